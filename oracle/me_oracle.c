@@ -1,0 +1,656 @@
+/*
+ * me_oracle.c -- plain, slow, FP64 CPU oracle for tree-level matrix elements |M|^2.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may link or call this file:
+ * only the tests, the smoke check and the CPU-baseline leg of the benchmark use it.
+ * It shares no code, header, table or generator with the CUDA path.
+ *
+ * What it computes (the quantity the paper offloads, Section 2, Eq.-free text of
+ * the abstract and Section 3: "matrix elements" for a batch of events):
+ *
+ *     me(p) = (1/IDEN) * sum_{all helicities h} sum_{all colours} |M(p, h, colours)|^2
+ *
+ * with IDEN = (initial spin states) x (initial colour states) x (identical final
+ * gluons)!.  The paper gives no formulas; the physics follows published textbook
+ * methods, each named where it is used:
+ *
+ *   * helicity spinors / polarisation vectors: the helicity basis of the HELAS
+ *     library (Murayama, Watanabe, Hagiwara, KEK Report 91-11), written here in the
+ *     chiral (Weyl) representation of Peskin & Schroeder (eqs. 3.25, 3.50-3.62);
+ *   * Feynman rules in Feynman gauge (Peskin & Schroeder Fig. 16.7 with g -> -g);
+ *   * colour decomposition of q qbar + n gluons into colour-ordered amplitudes
+ *     (Mangano & Parke, Phys. Rep. 200 (1991) 301), evaluated here with the
+ *     Berends-Giele recursion (Nucl. Phys. B306 (1988) 759);
+ *   * colour matrix C_{st} = Tr(T^s (T^t)^dagger), evaluated exactly in rationals by
+ *     the Fierz identity sum_a T^a_ij T^a_kl = (d_il d_kj - d_ij d_kl / N)/2.
+ *
+ * For e+ e- -> mu+ mu- the two s-channel diagrams (photon, Z) are written out with
+ * explicit 4x4 gamma matrices.
+ *
+ * Conventions shared with the product only through their published definitions:
+ *   * momenta [nevt][npar][4] = (E, px, py, pz); particle order of the process string;
+ *   * helicity index h in [0, 2^npar): particle i has helicity +1 if bit
+ *     (npar-1-i) of h is set, else -1 (physical helicity of that particle);
+ *   * colour-flow index: the lexicographic rank of the gluon permutation s in the
+ *     string (T^{a_s1} ... T^{a_sn})_{i_t j_tbar}, gluons named by particle index;
+ *   * selection: first index whose running sum exceeds r * total (strict);
+ *     helicity weights |M_h|^2, colour weights w_i = sum_h |A_{h,i}|^2.
+ *
+ * Compile with -ffp-contract=off so that no FMA contraction changes the rounding.
+ */
+#define _USE_MATH_DEFINES
+#include <complex.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef double complex cx;
+
+#define NPROC 5
+#define MAXPAR 7
+#define MAXG 5
+#define MAXCOL 120
+
+typedef struct {
+  double mZ, wZ, mt, wt, aEWM1, Gf, alphas;
+  int zero_width_tchan;
+} oracle_params;
+
+/* roles of external particles */
+enum { R_EBAR_IN, R_E_IN, R_MUBAR_OUT, R_MU_OUT, R_G_IN, R_G_OUT, R_T_OUT, R_TBAR_OUT };
+
+typedef struct {
+  const char* name;
+  int npar;
+  int ngluon;
+  int iden;
+  int role[MAXPAR];
+} proc_def;
+
+static const proc_def PROCS[NPROC] = {
+    {"e+ e- > mu+ mu-", 4, 0, 4, {R_EBAR_IN, R_E_IN, R_MUBAR_OUT, R_MU_OUT}},
+    {"g g > t t~", 4, 2, 256, {R_G_IN, R_G_IN, R_T_OUT, R_TBAR_OUT}},
+    {"g g > t t~ g", 5, 3, 256, {R_G_IN, R_G_IN, R_T_OUT, R_TBAR_OUT, R_G_OUT}},
+    {"g g > t t~ g g", 6, 4, 512, {R_G_IN, R_G_IN, R_T_OUT, R_TBAR_OUT, R_G_OUT, R_G_OUT}},
+    {"g g > t t~ g g g", 7, 5, 1536,
+     {R_G_IN, R_G_IN, R_T_OUT, R_TBAR_OUT, R_G_OUT, R_G_OUT, R_G_OUT}},
+};
+
+static int factorial(int n) { return n <= 1 ? 1 : n * factorial(n - 1); }
+
+int oracle_nproc(void) { return NPROC; }
+
+int oracle_process_id(const char* name) {
+  for (int i = 0; i < NPROC; ++i)
+    if (strcmp(name, PROCS[i].name) == 0) return i;
+  return -1;
+}
+
+int oracle_info(int proc, int* npar, int* ncomb, int* ncol, int* iden) {
+  if (proc < 0 || proc >= NPROC) return -1;
+  *npar = PROCS[proc].npar;
+  *ncomb = 1 << PROCS[proc].npar;
+  *ncol = PROCS[proc].ngluon ? factorial(PROCS[proc].ngluon) : 1;
+  *iden = PROCS[proc].iden;
+  return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Exact rationals for the colour algebra                                     */
+/* ------------------------------------------------------------------------- */
+typedef struct { int64_t n, d; } rat;
+
+static int64_t gcd64(int64_t a, int64_t b) {
+  if (a < 0) a = -a;
+  if (b < 0) b = -b;
+  while (b) { int64_t t = a % b; a = b; b = t; }
+  return a;
+}
+static rat rnorm(rat r) {
+  if (r.n == 0) { r.d = 1; return r; }
+  int64_t g = gcd64(r.n, r.d);
+  r.n /= g; r.d /= g;
+  if (r.d < 0) { r.n = -r.n; r.d = -r.d; }
+  return r;
+}
+static rat radd(rat a, rat b) { rat r = {a.n * b.d + b.n * a.d, a.d * b.d}; return rnorm(r); }
+static rat rmul(rat a, rat b) { rat r = {a.n * b.n, a.d * b.d}; return rnorm(r); }
+
+#define NC 3
+#define MAXWORDS 8
+#define MAXLEN (2 * MAXG)
+
+/* A product of traces Tr(w_0) Tr(w_1) ...; each word lists adjoint labels, and
+ * every label occurs exactly twice in the whole product (summed over). */
+typedef struct {
+  int nw;
+  int len[MAXWORDS];
+  int a[MAXWORDS][MAXLEN];
+} tprod;
+
+static rat trace_value(const tprod* t) {
+  /* a trace of a single generator vanishes */
+  for (int w = 0; w < t->nw; ++w)
+    if (t->len[w] == 1) { rat z = {0, 1}; return z; }
+  int w0 = -1;
+  for (int w = 0; w < t->nw; ++w)
+    if (t->len[w] > 0) { w0 = w; break; }
+  if (w0 < 0) { /* every trace is Tr(1) = N */
+    rat r = {1, 1};
+    for (int w = 0; w < t->nw; ++w) { rat n = {NC, 1}; r = rmul(r, n); }
+    return r;
+  }
+  int lab = t->a[w0][0];
+  /* partner occurrence */
+  int pw = -1, pi = -1;
+  for (int i = 1; i < t->len[w0]; ++i)
+    if (t->a[w0][i] == lab) { pw = w0; pi = i; break; }
+  if (pw < 0) {
+    for (int w = w0 + 1; w < t->nw && pw < 0; ++w)
+      for (int i = 0; i < t->len[w]; ++i)
+        if (t->a[w][i] == lab) { pw = w; pi = i; break; }
+  }
+  rat half = {1, 2}, mhalfn = {-1, 2 * NC};
+  tprod t1, t2;
+  if (pw == w0) {
+    /* Tr(T^a B T^a C) = 1/2 [Tr(C) Tr(B) - Tr(B C)/N], A empty since a is first */
+    int lenB = pi - 1, lenC = t->len[w0] - pi - 1;
+    const int* B = &t->a[w0][1];
+    const int* Cc = &t->a[w0][pi + 1];
+    t1 = *t;
+    t1.len[w0] = lenC;
+    memcpy(t1.a[w0], Cc, sizeof(int) * lenC);
+    t1.len[t1.nw] = lenB;
+    memcpy(t1.a[t1.nw], B, sizeof(int) * lenB);
+    t1.nw += 1;
+    t2 = *t;
+    t2.len[w0] = lenB + lenC;
+    memcpy(t2.a[w0], B, sizeof(int) * lenB);
+    memcpy(t2.a[w0] + lenB, Cc, sizeof(int) * lenC);
+  } else {
+    /* Tr(T^a X) Tr(T^a Y) = 1/2 [Tr(X Y) - Tr(X) Tr(Y)/N], with X = rest of w0 and
+     * Y = rest of pw read cyclically after the label */
+    int X[MAXLEN], Y[MAXLEN], lx = t->len[w0] - 1, ly = t->len[pw] - 1;
+    memcpy(X, &t->a[w0][1], sizeof(int) * lx);
+    for (int k = 0; k < ly; ++k) Y[k] = t->a[pw][(pi + 1 + k) % t->len[pw]];
+    /* term 1: merge into w0, delete pw */
+    t1 = *t;
+    t1.len[w0] = lx + ly;
+    memcpy(t1.a[w0], X, sizeof(int) * lx);
+    memcpy(t1.a[w0] + lx, Y, sizeof(int) * ly);
+    for (int w = pw; w + 1 < t1.nw; ++w) {
+      t1.len[w] = t1.len[w + 1];
+      memcpy(t1.a[w], t1.a[w + 1], sizeof(int) * MAXLEN);
+    }
+    t1.nw -= 1;
+    t2 = *t;
+    t2.len[w0] = lx;
+    memcpy(t2.a[w0], X, sizeof(int) * lx);
+    t2.len[pw] = ly;
+    memcpy(t2.a[pw], Y, sizeof(int) * ly);
+  }
+  return radd(rmul(half, trace_value(&t1)), rmul(mhalfn, trace_value(&t2)));
+}
+
+/* permutation of {0..n-1} with lexicographic rank r */
+static void perm_unrank(int n, int r, int* out) {
+  int pool[MAXG];
+  for (int i = 0; i < n; ++i) pool[i] = i;
+  for (int i = 0; i < n; ++i) {
+    int f = factorial(n - 1 - i);
+    int k = r / f;
+    r %= f;
+    out[i] = pool[k];
+    for (int j = k; j < n - 1 - i; ++j) pool[j] = pool[j + 1];
+  }
+}
+
+/* C_{st} = Tr(T^{s_1}...T^{s_n} T^{t_n}...T^{t_1}) as num[ncol*ncol] / den[ncol*ncol]. */
+int oracle_colour_matrix_exact(int proc, int64_t* num, int64_t* den) {
+  if (proc < 0 || proc >= NPROC) return -1;
+  int n = PROCS[proc].ngluon;
+  if (n == 0) { num[0] = 1; den[0] = 1; return 0; }
+  int ncol = factorial(n);
+  for (int s = 0; s < ncol; ++s) {
+    int ps[MAXG];
+    perm_unrank(n, s, ps);
+    for (int t = 0; t < ncol; ++t) {
+      int pt[MAXG];
+      perm_unrank(n, t, pt);
+      tprod tp;
+      memset(&tp, 0, sizeof tp);
+      tp.nw = 1;
+      tp.len[0] = 2 * n;
+      for (int i = 0; i < n; ++i) {
+        tp.a[0][i] = ps[i];
+        tp.a[0][2 * n - 1 - i] = pt[i];
+      }
+      rat v = trace_value(&tp);
+      num[s * ncol + t] = v.n;
+      den[s * ncol + t] = v.d;
+    }
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Dirac algebra (chiral representation)                                     */
+/* ------------------------------------------------------------------------- */
+static cx GAM[4][4][4]; /* GAM[mu][row][col] = gamma^mu */
+static int gam_ready = 0;
+
+static void gamma_init(void) {
+  if (gam_ready) return;
+  memset(GAM, 0, sizeof GAM);
+  /* gamma^mu = [[0, sigma^mu], [sigmabar^mu, 0]], sigma = (1, s1, s2, s3),
+   * sigmabar = (1, -s1, -s2, -s3) */
+  cx pauli[4][2][2] = {{{1, 0}, {0, 1}},
+                       {{0, 1}, {1, 0}},
+                       {{0, -I}, {I, 0}},
+                       {{1, 0}, {0, -1}}};
+  for (int mu = 0; mu < 4; ++mu)
+    for (int i = 0; i < 2; ++i)
+      for (int j = 0; j < 2; ++j) {
+        GAM[mu][i][2 + j] = pauli[mu][i][j];
+        GAM[mu][2 + i][j] = (mu == 0 ? 1.0 : -1.0) * pauli[mu][i][j];
+      }
+  gam_ready = 1;
+}
+
+static cx mdot_c(const cx* a, const cx* b) { return a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3]; }
+static double mdot_r(const double* a, const double* b) { return a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3]; }
+
+/* slash(a) = gamma^mu a_mu = gamma^0 a^0 - gamma^k a^k */
+static void slash(const cx* a, cx M[4][4]) {
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j)
+      M[i][j] = GAM[0][i][j] * a[0] - GAM[1][i][j] * a[1] - GAM[2][i][j] * a[2] - GAM[3][i][j] * a[3];
+}
+
+/* row vector times matrix */
+static void bra_mat(const cx* b, cx M[4][4], cx* out) {
+  for (int j = 0; j < 4; ++j) {
+    cx s = 0;
+    for (int i = 0; i < 4; ++i) s += b[i] * M[i][j];
+    out[j] = s;
+  }
+}
+static cx bra_ket(const cx* b, const cx* k) { return b[0] * k[0] + b[1] * k[1] + b[2] * k[2] + b[3] * k[3]; }
+
+/* Two-component helicity eigenvectors of sigma.p_hat with eigenvalue lam. */
+static void xi_hel(const double* p, int lam, cx* xi) {
+  double px = p[1], py = p[2], pz = p[3];
+  double ap = sqrt(px * px + py * py + pz * pz);
+  if (ap == 0.0) {
+    xi[0] = lam > 0 ? 1 : 0;
+    xi[1] = lam > 0 ? 0 : 1;
+    return;
+  }
+  if (pz >= 0) {
+    double nrm = 1.0 / sqrt(2.0 * ap * (ap + pz));
+    if (lam > 0) { xi[0] = (ap + pz) * nrm; xi[1] = (px + I * py) * nrm; }
+    else { xi[0] = (-px + I * py) * nrm; xi[1] = (ap + pz) * nrm; }
+  } else {
+    double nrm = 1.0 / sqrt(2.0 * ap * (ap - pz));
+    if (lam > 0) { xi[0] = (px - I * py) * nrm; xi[1] = (ap - pz) * nrm; }
+    else { xi[0] = (pz - ap) * nrm; xi[1] = (px + I * py) * nrm; }
+  }
+}
+
+/* sqrt(E - lam|p|) and sqrt(E + lam|p|) without cancellation */
+static void omega(const double* p, double m, int lam, double* wminus, double* wplus) {
+  double ap = sqrt(p[1] * p[1] + p[2] * p[2] + p[3] * p[3]);
+  double E = p[0];
+  double big = sqrt(E + ap);
+  double small = (m == 0.0) ? 0.0 : m / big; /* sqrt(E-|p|) = m / sqrt(E+|p|) */
+  if (lam > 0) { *wminus = small; *wplus = big; }
+  else { *wminus = big; *wplus = small; }
+}
+
+/* u(p, lam) = (sqrt(p.sigma) xi, sqrt(p.sigmabar) xi) with xi the helicity state */
+static void spinor_u(const double* p, double m, int lam, cx* u) {
+  cx xi[2];
+  double wm, wp;
+  xi_hel(p, lam, xi);
+  omega(p, m, lam, &wm, &wp);
+  u[0] = wm * xi[0]; u[1] = wm * xi[1];
+  u[2] = wp * xi[0]; u[3] = wp * xi[1];
+}
+
+/* v(p, lam) for an antiparticle of physical helicity lam:
+ * (sqrt(p.sigma) eta, -sqrt(p.sigmabar) eta), eta = xi_{-lam} */
+static void spinor_v(const double* p, double m, int lam, cx* v) {
+  cx eta[2];
+  double wm, wp; /* sqrt(E - (-lam)|p|), sqrt(E + (-lam)|p|) */
+  xi_hel(p, -lam, eta);
+  omega(p, m, -lam, &wm, &wp);
+  v[0] = wm * eta[0]; v[1] = wm * eta[1];
+  v[2] = -wp * eta[0]; v[3] = -wp * eta[1];
+}
+
+/* psibar = psi^dagger gamma^0 */
+static void dirac_bar(const cx* s, cx* b) {
+  b[0] = conj(s[2]); b[1] = conj(s[3]); b[2] = conj(s[0]); b[3] = conj(s[1]);
+}
+
+/* helicity polarisation vector eps^mu(k, lam) = (-lam e1 - i e2)/sqrt(2) with
+ * e1 = (0, cos th cos ph, cos th sin ph, -sin th), e2 = (0, -sin ph, cos ph, 0) */
+static void polvec(const double* k, int lam, cx* e) {
+  double px = k[1], py = k[2], pz = k[3];
+  double ap = sqrt(px * px + py * py + pz * pz);
+  double pt = sqrt(px * px + py * py);
+  double e1[4], e2[4];
+  if (pt > 0.0) {
+    double ct = pz / ap, st = pt / ap, cp = px / pt, sp = py / pt;
+    e1[0] = 0; e1[1] = ct * cp; e1[2] = ct * sp; e1[3] = -st;
+    e2[0] = 0; e2[1] = -sp; e2[2] = cp; e2[3] = 0;
+  } else {
+    double ct = pz >= 0 ? 1.0 : -1.0;
+    e1[0] = 0; e1[1] = ct; e1[2] = 0; e1[3] = 0;
+    e2[0] = 0; e2[1] = 0; e2[2] = 1; e2[3] = 0;
+  }
+  for (int mu = 0; mu < 4; ++mu) e[mu] = (-lam * e1[mu] - I * e2[mu]) / sqrt(2.0);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Standard-model parameters                                                  */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+  double ee;           /* electric charge e = sqrt(4 pi alpha) */
+  double sw2, sw, cw, mW;
+  double gZ_L, gZ_R;   /* Z couplings of charged leptons in units of e */
+} sm_derived;
+
+static void sm_derive(const oracle_params* p, sm_derived* d) {
+  double alpha = 1.0 / p->aEWM1;
+  d->ee = sqrt(4.0 * M_PI * alpha);
+  /* W mass from (alpha, G_F, m_Z): m_W^2 = mZ^2/2 + sqrt(mZ^4/4 - pi alpha mZ^2/(sqrt2 G_F)) */
+  double mz2 = p->mZ * p->mZ;
+  d->mW = sqrt(mz2 / 2.0 + sqrt(mz2 * mz2 / 4.0 - M_PI * alpha * mz2 / (sqrt(2.0) * p->Gf)));
+  d->sw2 = 1.0 - d->mW * d->mW / mz2;
+  d->sw = sqrt(d->sw2);
+  d->cw = sqrt(1.0 - d->sw2);
+  /* g = (T3 - Q sw^2)/(sw cw) for the left-handed, -Q sw^2/(sw cw) for the right-handed */
+  double T3 = -0.5, Q = -1.0;
+  d->gZ_L = (T3 - Q * d->sw2) / (d->sw * d->cw);
+  d->gZ_R = (-Q * d->sw2) / (d->sw * d->cw);
+}
+
+int oracle_sm_derived(const oracle_params* p, double* out5) {
+  sm_derived d;
+  sm_derive(p, &d);
+  out5[0] = d.ee; out5[1] = d.sw2; out5[2] = d.mW; out5[3] = d.gZ_L; out5[4] = d.gZ_R;
+  return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* e+ e- -> mu+ mu- : photon and Z in the s channel                           */
+/* ------------------------------------------------------------------------- */
+/* current b gamma^mu (cL P_L + cR P_R) k, with P_L = diag(1,1,0,0) here */
+static void vector_current(const cx* b, const cx* k, cx cL, cx cR, cx* j) {
+  cx kc[4] = {cL * k[0], cL * k[1], cR * k[2], cR * k[3]};
+  for (int mu = 0; mu < 4; ++mu) {
+    cx s = 0;
+    for (int r = 0; r < 4; ++r)
+      for (int c = 0; c < 4; ++c) s += b[r] * GAM[mu][r][c] * kc[c];
+    j[mu] = s;
+  }
+}
+
+static cx amp_eemumu(const double* mom, const int* lam, const oracle_params* par, const sm_derived* sm) {
+  const double *p1 = mom, *p2 = mom + 4, *p3 = mom + 8, *p4 = mom + 12;
+  cx v1[4], b1[4], u2[4], v3[4], u4[4], b4[4];
+  spinor_v(p1, 0.0, lam[0], v1);  dirac_bar(v1, b1); /* incoming e+ : vbar */
+  spinor_u(p2, 0.0, lam[1], u2);                       /* incoming e- : u    */
+  spinor_v(p3, 0.0, lam[2], v3);                       /* outgoing mu+: v    */
+  spinor_u(p4, 0.0, lam[3], u4);  dirac_bar(u4, b4);   /* outgoing mu-: ubar */
+  double P[4] = {p1[0] + p2[0], p1[1] + p2[1], p1[2] + p2[2], p1[3] + p2[3]};
+  double s = mdot_r(P, P);
+  cx ee = sm->ee;
+  cx total = 0;
+  /* photon: vertex -i e Q gamma^mu, Q = -1 for e and mu; propagator -i g_{mu nu}/s */
+  {
+    cx je[4], jm[4];
+    vector_current(b1, u2, -1.0, -1.0, je);
+    vector_current(b4, v3, -1.0, -1.0, jm);
+    total += (-I * ee) * (-I * ee) * (-I / s) * mdot_c(je, jm);
+  }
+  /* Z: vertex -i e gamma^mu (gL P_L + gR P_R); propagator -i g_{mu nu}/(s - mZ^2 + i mZ wZ)
+   * (the k_mu k_nu part vanishes against the massless currents) */
+  {
+    cx je[4], jm[4];
+    vector_current(b1, u2, sm->gZ_L, sm->gZ_R, je);
+    vector_current(b4, v3, sm->gZ_L, sm->gZ_R, jm);
+    cx den = s - par->mZ * par->mZ + I * par->mZ * par->wZ;
+    total += (-I * ee) * (-I * ee) * (-I / den) * mdot_c(je, jm);
+  }
+  return total;
+}
+
+/* ------------------------------------------------------------------------- */
+/* g g -> t t~ + n gluons : Berends-Giele colour-ordered recursion            */
+/* ------------------------------------------------------------------------- */
+/* colour-ordered three-gluon vertex contracted with two currents (legs in order
+ * 1, 2; all momenta incoming, third momentum q = -(k1 + k2)):
+ *   V^rho = (J1.J2)(k1-k2)^rho + J2^rho (k2-q).J1 + J1^rho (q-k1).J2
+ * which is g^{mu nu}(k-p)^rho + g^{nu rho}(p-q)^mu + g^{rho mu}(q-k)^nu
+ * contracted with J1_mu J2_nu. */
+static void v3(const double* k1, const cx* J1, const double* k2, const cx* J2, cx* out) {
+  double q[4], d12[4], a[4], b[4];
+  for (int m = 0; m < 4; ++m) {
+    q[m] = -(k1[m] + k2[m]);
+    d12[m] = k1[m] - k2[m];
+    a[m] = k2[m] - q[m];
+    b[m] = q[m] - k1[m];
+  }
+  cx j12 = mdot_c(J1, J2);
+  cx aj1 = a[0] * J1[0] - a[1] * J1[1] - a[2] * J1[2] - a[3] * J1[3];
+  cx bj2 = b[0] * J2[0] - b[1] * J2[1] - b[2] * J2[2] - b[3] * J2[3];
+  for (int m = 0; m < 4; ++m) out[m] = j12 * d12[m] + J2[m] * aj1 + J1[m] * bj2;
+}
+
+/* colour-ordered four-gluon vertex [2 g^{mu rho} g^{nu sigma} - g^{mu nu} g^{rho sigma}
+ * - g^{mu sigma} g^{nu rho}] contracted with J1_mu J2_nu J3_rho */
+static void v4(const cx* J1, const cx* J2, const cx* J3, cx* out) {
+  cx d13 = mdot_c(J1, J3), d12 = mdot_c(J1, J2), d23 = mdot_c(J2, J3);
+  for (int m = 0; m < 4; ++m) out[m] = 2.0 * d13 * J2[m] - d12 * J3[m] - d23 * J1[m];
+}
+
+/* Is the propagator whose momentum is the sum over 'mask' (bit i = particle i) in the
+ * t channel, i.e. does it separate the two incoming particles (0 and 1)? */
+static int is_tchannel(unsigned mask) {
+  int a = (mask >> 0) & 1, b = (mask >> 1) & 1;
+  return a != b;
+}
+
+typedef struct {
+  cx eps[MAXG][4];   /* gluon polarisation (incoming: eps, outgoing: eps*) */
+  double kin[MAXG][4];/* incoming momentum of each gluon */
+  int pidx[MAXG];    /* particle index of each gluon */
+  cx ubar_t[4];      /* outgoing top: ubar(p_t) */
+  cx v_tb[4];        /* outgoing antitop: v(p_tbar) */
+  double pt[4];      /* top momentum */
+  int it;            /* particle index of the top */
+} qcd_ext;
+
+/* colour-ordered amplitude A(sigma) for gluons in the order sigma (gluon slots) */
+static cx amp_ordered(const qcd_ext* x, int n, const int* sigma, double gs, double mt, double wt, int zwt) {
+  cx J[MAXG][MAXG][4];
+  double K[MAXG][MAXG][4];
+  unsigned M[MAXG][MAXG];
+  for (int len = 1; len <= n; ++len) {
+    for (int i = 0; i + len - 1 < n; ++i) {
+      int j = i + len - 1;
+      if (len == 1) {
+        for (int m = 0; m < 4; ++m) { J[i][i][m] = x->eps[sigma[i]][m]; K[i][i][m] = x->kin[sigma[i]][m]; }
+        M[i][i] = 1u << x->pidx[sigma[i]];
+        continue;
+      }
+      for (int m = 0; m < 4; ++m) K[i][j][m] = K[i][i][m] + K[i + 1][j][m];
+      M[i][j] = M[i][i] | M[i + 1][j];
+      cx cur[4] = {0, 0, 0, 0}, t[4];
+      for (int k = i; k < j; ++k) {
+        v3(K[i][k], J[i][k], K[k + 1][j], J[k + 1][j], t);
+        for (int m = 0; m < 4; ++m) cur[m] += I * gs * t[m];
+      }
+      for (int k = i; k < j; ++k)
+        for (int l = k + 1; l < j; ++l) {
+          v4(J[i][k], J[k + 1][l], J[l + 1][j], t);
+          for (int m = 0; m < 4; ++m) cur[m] += I * gs * gs * t[m];
+        }
+      double P2 = mdot_r(K[i][j], K[i][j]);
+      for (int m = 0; m < 4; ++m) J[i][j][m] = (-I / P2) * cur[m];
+    }
+  }
+  /* quark line: ubar(t) [-i gs J(B1)-slash] S [-i gs J(B2)-slash] ... v(tbar) */
+  cx U[MAXG][4];
+  for (int m = 0; m < 4; ++m) U[0][m] = x->ubar_t[m];
+  cx A = 0;
+  for (int j = 1; j <= n; ++j) {
+    cx acc[4] = {0, 0, 0, 0};
+    for (int i = 0; i < j; ++i) {
+      cx G[4][4], tmp[4], Jv[4];
+      for (int m = 0; m < 4; ++m) Jv[m] = -I * gs * J[i][j - 1][m];
+      slash(Jv, G);
+      bra_mat(U[i], G, tmp);
+      for (int m = 0; m < 4; ++m) acc[m] += tmp[m];
+    }
+    if (j == n) {
+      A = bra_ket(acc, x->v_tb);
+    } else {
+      /* propagator i(q-slash + m)/(q^2 - m^2 + i m w) with q = p_t - K(first j gluons) */
+      double q[4];
+      for (int m = 0; m < 4; ++m) q[m] = x->pt[m] - K[0][j - 1][m];
+      unsigned mask = M[0][j - 1] | (1u << x->it);
+      double w = (zwt && is_tchannel(mask)) ? 0.0 : wt;
+      cx den = mdot_r(q, q) - mt * mt + I * mt * w;
+      cx qc[4] = {q[0], q[1], q[2], q[3]}, S[4][4];
+      slash(qc, S);
+      for (int r = 0; r < 4; ++r) S[r][r] += mt;
+      cx tmp[4];
+      bra_mat(acc, S, tmp);
+      for (int m = 0; m < 4; ++m) U[j][m] = (I / den) * tmp[m];
+    }
+  }
+  return A;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Driver                                                                     */
+/* ------------------------------------------------------------------------- */
+static int select_first_exceeding(const double* w, int n, double r) {
+  double total = 0;
+  for (int i = 0; i < n; ++i) total += w[i];
+  if (!(total > 0)) return 0;
+  double target = r * total, run = 0;
+  for (int i = 0; i < n; ++i) {
+    run += w[i];
+    if (run > target) return i;
+  }
+  for (int i = n - 1; i >= 0; --i) if (w[i] > 0) return i;
+  return 0;
+}
+
+/*
+ * oracle_me: evaluate nevt events of process 'proc'.
+ *   mom      [nevt][npar][4] FP64
+ *   alphas   [nevt] or NULL (then par->alphas)
+ *   rnd_hel, rnd_col [nevt] in (0,1) or NULL (then no selection is written)
+ *   me       [nevt]                          (output, required)
+ *   me_hel   [nevt][ncomb] or NULL           |M_h|^2 (before 1/IDEN)
+ *   jamp     [nevt][ncomb][ncol][2] or NULL  colour-ordered amplitudes
+ *   colw     [nevt][ncol] or NULL            w_i = sum_h |A_{h,i}|^2
+ *   sel_hel, sel_col [nevt] or NULL
+ *   gauge_leg: -1 normally; otherwise the particle index of one gluon whose
+ *              polarisation is replaced by k/E (gauge check).
+ * Returns 0, or -1 for a bad argument.
+ */
+int oracle_me(int proc, const oracle_params* par, int64_t nevt, const double* mom, const double* alphas,
+              const double* rnd_hel, const double* rnd_col, double* me, double* me_hel, double* jamp,
+              double* colw, int32_t* sel_hel, int32_t* sel_col, int gauge_leg) {
+  if (proc < 0 || proc >= NPROC || nevt < 0 || !par || (nevt > 0 && (!mom || !me))) return -1;
+  gamma_init();
+  const proc_def* pd = &PROCS[proc];
+  int npar = pd->npar, ncomb = 1 << npar, n = pd->ngluon;
+  int ncol = n ? factorial(n) : 1;
+  sm_derived sm;
+  sm_derive(par, &sm);
+  double* Cm = (double*)malloc(sizeof(double) * ncol * ncol);
+  int64_t* cn = (int64_t*)malloc(sizeof(int64_t) * ncol * ncol);
+  int64_t* cd = (int64_t*)malloc(sizeof(int64_t) * ncol * ncol);
+  oracle_colour_matrix_exact(proc, cn, cd);
+  for (int i = 0; i < ncol * ncol; ++i) Cm[i] = (double)cn[i] / (double)cd[i];
+  free(cn);
+  free(cd);
+  int perms[MAXCOL][MAXG];
+  for (int s = 0; s < ncol && n; ++s) perm_unrank(n, s, perms[s]);
+
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t e = 0; e < nevt; ++e) {
+    const double* p = mom + e * npar * 4;
+    double mh[1 << MAXPAR];
+    double w[MAXCOL];
+    for (int i = 0; i < ncol; ++i) w[i] = 0;
+    double total = 0;
+    double as = alphas ? alphas[e] : par->alphas;
+    double gs = sqrt(4.0 * M_PI * as);
+    for (int h = 0; h < ncomb; ++h) {
+      int lam[MAXPAR];
+      for (int i = 0; i < npar; ++i) lam[i] = ((h >> (npar - 1 - i)) & 1) ? 1 : -1;
+      cx A[MAXCOL];
+      if (proc == 0) {
+        A[0] = amp_eemumu(p, lam, par, &sm);
+      } else {
+        qcd_ext x;
+        int g = 0;
+        for (int i = 0; i < npar; ++i) {
+          const double* pi = p + 4 * i;
+          int r = pd->role[i];
+          if (r == R_G_IN || r == R_G_OUT) {
+            cx e4[4];
+            polvec(pi, lam[i], e4);
+            for (int m = 0; m < 4; ++m) {
+              x.eps[g][m] = (r == R_G_IN) ? e4[m] : conj(e4[m]);
+              x.kin[g][m] = (r == R_G_IN) ? pi[m] : -pi[m];
+            }
+            if (i == gauge_leg)
+              for (int m = 0; m < 4; ++m) x.eps[g][m] = pi[m] / pi[0];
+            x.pidx[g] = i;
+            ++g;
+          } else if (r == R_T_OUT) {
+            cx u[4];
+            spinor_u(pi, par->mt, lam[i], u);
+            dirac_bar(u, x.ubar_t);
+            for (int m = 0; m < 4; ++m) x.pt[m] = pi[m];
+            x.it = i;
+          } else if (r == R_TBAR_OUT) {
+            spinor_v(pi, par->mt, lam[i], x.v_tb);
+          }
+        }
+        for (int s = 0; s < ncol; ++s)
+          A[s] = amp_ordered(&x, n, perms[s], gs, par->mt, par->wt, par->zero_width_tchan);
+      }
+      double m2 = 0;
+      for (int s = 0; s < ncol; ++s)
+        for (int t = 0; t < ncol; ++t) m2 += Cm[s * ncol + t] * creal(conj(A[s]) * A[t]);
+      mh[h] = m2;
+      total += m2;
+      for (int s = 0; s < ncol; ++s) w[s] += creal(A[s]) * creal(A[s]) + cimag(A[s]) * cimag(A[s]);
+      if (jamp)
+        for (int s = 0; s < ncol; ++s) {
+          jamp[((e * ncomb + h) * ncol + s) * 2 + 0] = creal(A[s]);
+          jamp[((e * ncomb + h) * ncol + s) * 2 + 1] = cimag(A[s]);
+        }
+    }
+    me[e] = total / pd->iden;
+    if (me_hel)
+      for (int h = 0; h < ncomb; ++h) me_hel[e * ncomb + h] = mh[h];
+    if (colw)
+      for (int s = 0; s < ncol; ++s) colw[e * ncol + s] = w[s];
+    if (sel_hel && rnd_hel) sel_hel[e] = select_first_exceeding(mh, ncomb, rnd_hel[e]);
+    if (sel_col && rnd_col) sel_col[e] = select_first_exceeding(w, ncol, rnd_col[e]);
+  }
+  free(Cm);
+  return 0;
+}
