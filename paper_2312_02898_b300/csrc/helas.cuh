@@ -1,0 +1,319 @@
+// helas.cuh -- HELAS-style helicity wavefunctions and vertex currents for the
+// event-parallel matrix-element kernels (one event per thread).
+//
+// Conventions (the physics of the HELAS library, Murayama/Watanabe/Hagiwara KEK 91-11,
+// re-derived here in the chiral representation):
+//   * gamma^mu = [[0, sigma^mu], [sigmabar^mu, 0]], sigma = (1, s), sigmabar = (1, -s);
+//     a Dirac spinor is (psi_L ; psi_R), P_L keeps the upper two components;
+//   * a "bra" wavefunction is a row spinor already multiplied by gamma^0 (ubar, vbar);
+//     a "ket" is a column spinor (u, v); a vector wavefunction holds contravariant
+//     components W^mu;
+//   * momenta are "incoming": incoming particles carry +p, outgoing ones -p; a fermion
+//     current carries the momentum that flows along the fermion arrow.
+//
+// Every routine computes a *raw* value: no coupling constant and no factor of i; the
+// generator folds g_s (one power per external gluon) and the phases of vertices and
+// propagators into the colour-flow coefficients, so the device code multiplies by no
+// constants.  Propagator denominators arrive precomputed in FP64 (once per event,
+// outside the helicity loop) and converted to the working precision R.
+#pragma once
+
+#include <cmath>
+#include <cstdint>
+
+#if defined(__CUDACC__)
+#define HD __host__ __device__ __forceinline__
+#else
+#define HD inline
+#endif
+
+namespace meb300 {
+
+template <class R>
+struct alignas(2 * sizeof(R)) cx {
+  R r, i;
+};
+
+template <class R> HD cx<R> mk(R r, R i) { cx<R> z; z.r = r; z.i = i; return z; }
+template <class R> HD cx<R> operator+(cx<R> a, cx<R> b) { return mk<R>(a.r + b.r, a.i + b.i); }
+template <class R> HD cx<R> operator-(cx<R> a, cx<R> b) { return mk<R>(a.r - b.r, a.i - b.i); }
+template <class R> HD cx<R> operator-(cx<R> a) { return mk<R>(-a.r, -a.i); }
+template <class R> HD cx<R> operator*(cx<R> a, cx<R> b) { return mk<R>(a.r * b.r - a.i * b.i, a.r * b.i + a.i * b.r); }
+template <class R> HD cx<R> operator*(R s, cx<R> a) { return mk<R>(s * a.r, s * a.i); }
+template <class R> HD cx<R> conjg(cx<R> a) { return mk<R>(a.r, -a.i); }
+template <class R> HD cx<R> times_i(cx<R> a) { return mk<R>(-a.i, a.r); }
+template <class R> HD void operator+=(cx<R>& a, cx<R> b) { a.r += b.r; a.i += b.i; }
+template <class R> HD void operator-=(cx<R>& a, cx<R> b) { a.r -= b.r; a.i -= b.i; }
+
+template <class R> HD void copy4(cx<R>* dst, const cx<R>* src) {
+#pragma unroll
+  for (int m = 0; m < 4; ++m) dst[m] = src[m];
+}
+
+// Minkowski product of two complex 4-vectors (bilinear, no conjugation)
+template <class R> HD cx<R> mdot(const cx<R>* a, const cx<R>* b) {
+  return a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
+}
+// Minkowski product of a real and a complex 4-vector
+template <class R> HD cx<R> mdot(const R* k, const cx<R>* a) {
+  return mk<R>(k[0] * a[0].r - k[1] * a[1].r - k[2] * a[2].r - k[3] * a[3].r,
+               k[0] * a[0].i - k[1] * a[1].i - k[2] * a[2].i - k[3] * a[3].i);
+}
+
+// ---------------------------------------------------------------------------
+// external wavefunctions
+// ---------------------------------------------------------------------------
+// Two-component helicity eigenvector chi_lam of sigma.p_hat.  Phase convention:
+// chi_+ = (cos th/2, e^{i ph} sin th/2), chi_- = (-e^{-i ph} sin th/2, cos th/2), in
+// the forward hemisphere; in the backward hemisphere both are multiplied by e^{-i ph}
+// (resp. e^{+i ph}) so that no component is computed as a small difference.
+template <class R>
+HD void helicity_chi(const R* p, int lam, cx<R>* chi) {
+  const R px = p[1], py = p[2], pz = p[3];
+  const R ap = sqrt(px * px + py * py + pz * pz);
+  if (pz >= R(0)) {
+    const R s = ap + pz;
+    const R nrm = R(1) / sqrt(R(2) * ap * s);
+    if (lam > 0) { chi[0] = mk<R>(s * nrm, R(0)); chi[1] = mk<R>(px * nrm, py * nrm); }
+    else         { chi[0] = mk<R>(-px * nrm, py * nrm); chi[1] = mk<R>(s * nrm, R(0)); }
+  } else {
+    const R d = ap - pz;
+    const R nrm = R(1) / sqrt(R(2) * ap * d);
+    if (lam > 0) { chi[0] = mk<R>(px * nrm, -py * nrm); chi[1] = mk<R>(d * nrm, R(0)); }
+    else         { chi[0] = mk<R>(-d * nrm, R(0));      chi[1] = mk<R>(px * nrm, py * nrm); }
+  }
+}
+
+// sqrt(E + |p|) and sqrt(E - |p|) = m / sqrt(E + |p|), free of cancellation
+template <class R>
+HD void omegas(const R* p, R m, R& wp, R& wm) {
+  const R ap = sqrt(p[1] * p[1] + p[2] * p[2] + p[3] * p[3]);
+  wp = sqrt(p[0] + ap);
+  wm = (m == R(0)) ? R(0) : m / wp;
+}
+
+// u(p, lam) = (sqrt(E - lam|p|) chi_lam ; sqrt(E + lam|p|) chi_lam)   [ket]
+template <class R>
+HD void ext_u(const R* p, R m, int lam, cx<R>* w) {
+  cx<R> chi[2];
+  R wp, wm;
+  helicity_chi(p, lam, chi);
+  omegas(p, m, wp, wm);
+  const R lo = lam > 0 ? wm : wp, hi = lam > 0 ? wp : wm;
+  w[0] = lo * chi[0]; w[1] = lo * chi[1]; w[2] = hi * chi[0]; w[3] = hi * chi[1];
+}
+
+// v(p, lam) for an antiparticle of helicity lam:
+// (sqrt(E + lam|p|) chi_{-lam} ; -sqrt(E - lam|p|) chi_{-lam})   [ket]
+template <class R>
+HD void ext_v(const R* p, R m, int lam, cx<R>* w) {
+  cx<R> chi[2];
+  R wp, wm;
+  helicity_chi(p, -lam, chi);
+  omegas(p, m, wp, wm);
+  const R up = lam > 0 ? wp : wm, dn = lam > 0 ? wm : wp;
+  w[0] = up * chi[0]; w[1] = up * chi[1]; w[2] = (-dn) * chi[0]; w[3] = (-dn) * chi[1];
+}
+
+// bar(psi) = psi^dagger gamma^0: swap the chiral halves and conjugate
+template <class R>
+HD void dirac_bar(const cx<R>* s, cx<R>* b) {
+  b[0] = conjg(s[2]); b[1] = conjg(s[3]); b[2] = conjg(s[0]); b[3] = conjg(s[1]);
+}
+
+template <class R> HD void ext_ubar(const R* p, R m, int lam, cx<R>* w) { cx<R> t[4]; ext_u(p, m, lam, t); dirac_bar(t, w); }
+template <class R> HD void ext_vbar(const R* p, R m, int lam, cx<R>* w) { cx<R> t[4]; ext_v(p, m, lam, t); dirac_bar(t, w); }
+
+// Helicity polarisation vector eps(k, lam) = (-lam e1 - i e2)/sqrt2,
+// e1 = (0, cos th cos ph, cos th sin ph, -sin th), e2 = (0, -sin ph, cos ph, 0);
+// an outgoing gluon takes the complex conjugate.
+template <class R>
+HD void ext_eps(const R* k, int lam, bool outgoing, cx<R>* w) {
+  const R px = k[1], py = k[2], pz = k[3];
+  const R pt2 = px * px + py * py;
+  const R ap = sqrt(pt2 + pz * pz);
+  const R rt2 = R(0.70710678118654752440);
+  R e1[3], e2[3];
+  if (pt2 > R(0)) {
+    const R pt = sqrt(pt2);
+    const R ct = pz / ap, st = pt / ap, cp = px / pt, sp = py / pt;
+    e1[0] = ct * cp; e1[1] = ct * sp; e1[2] = -st;
+    e2[0] = -sp; e2[1] = cp; e2[2] = R(0);
+  } else {
+    e1[0] = pz >= R(0) ? R(1) : R(-1); e1[1] = R(0); e1[2] = R(0);
+    e2[0] = R(0); e2[1] = R(1); e2[2] = R(0);
+  }
+  const R sgn = outgoing ? R(1) : R(-1);  // imaginary part flips for eps*
+  w[0] = mk<R>(R(0), R(0));
+  for (int j = 0; j < 3; ++j) w[j + 1] = mk<R>(-R(lam) * rt2 * e1[j], sgn * rt2 * e2[j]);
+}
+
+// ---------------------------------------------------------------------------
+// vertices (raw: no couplings, no factors of i)
+// ---------------------------------------------------------------------------
+// three-gluon vertex contracted with two currents X (momentum kx) and Y (ky):
+//   V3^rho = (X.Y)(kx - ky)^rho + Y^rho (kx + 2 ky).X - X^rho (2 kx + ky).Y
+// (all momenta incoming; the third leg carries q = -(kx + ky)).
+template <class R>
+HD void v3_raw(const cx<R>* X, const R* kx, const cx<R>* Y, const R* ky, cx<R>* out) {
+  R a[4], b[4], d[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    d[m] = kx[m] - ky[m];
+    a[m] = kx[m] + R(2) * ky[m];
+    b[m] = R(2) * kx[m] + ky[m];
+  }
+  const cx<R> xy = mdot(X, Y), ax = mdot(a, X), by = mdot(b, Y);
+#pragma unroll
+  for (int m = 0; m < 4; ++m) out[m] = d[m] * xy + Y[m] * ax - X[m] * by;
+}
+
+// off-shell gluon from a three-gluon vertex: V3 / K^2   (phase i)
+template <class R>
+HD void g3_current(const cx<R>* X, const R* kx, const cx<R>* Y, const R* ky, R invK2, cx<R>* out) {
+  v3_raw(X, kx, Y, ky, out);
+#pragma unroll
+  for (int m = 0; m < 4; ++m) out[m] = invK2 * out[m];
+}
+
+// Lorentz structure s of the four-gluon vertex contracted with X, Y, Z (legs a, b, c):
+//   s=1 (f^abe f^cde): (X.Z) Y - (Y.Z) X
+//   s=2 (f^ace f^bde): (X.Y) Z - (Y.Z) X
+//   s=3 (f^ade f^bce): (X.Y) Z - (X.Z) Y
+template <int S, class R>
+HD void v4_raw(const cx<R>* X, const cx<R>* Y, const cx<R>* Z, cx<R>* out) {
+  if (S == 1) {
+    const cx<R> xz = mdot(X, Z), yz = mdot(Y, Z);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) out[m] = xz * Y[m] - yz * X[m];
+  } else if (S == 2) {
+    const cx<R> xy = mdot(X, Y), yz = mdot(Y, Z);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) out[m] = xy * Z[m] - yz * X[m];
+  } else {
+    const cx<R> xy = mdot(X, Y), xz = mdot(X, Z);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) out[m] = xy * Z[m] - xz * Y[m];
+  }
+}
+
+// off-shell gluon from a four-gluon structure: V4_s / K^2   (phase -1)
+template <int S, class R>
+HD void g4_current(const cx<R>* X, const cx<R>* Y, const cx<R>* Z, R invK2, cx<R>* out) {
+  v4_raw<S>(X, Y, Z, out);
+#pragma unroll
+  for (int m = 0; m < 4; ++m) out[m] = invK2 * out[m];
+}
+
+// row spinor (a | b) times gamma.G, G contravariant:
+//   (a|b) [[0, G.sigma], [G.sigmabar, 0]] = (b (G.sigmabar) | a (G.sigma))
+template <class R>
+HD void bra_gslash(const cx<R>* f, const cx<R>* G, cx<R>* o) {
+  const cx<R> p03 = G[0] + G[3], m03 = G[0] - G[3];
+  const cx<R> p12 = G[1] + times_i(G[2]), m12 = G[1] - times_i(G[2]);  // G1 +- i G2
+  // G.sigmabar = [[G0+G3, G1-iG2], [G1+iG2, G0-G3]], G.sigma = [[G0-G3, -(G1-iG2)], [-(G1+iG2), G0+G3]]
+  o[0] = f[2] * p03 + f[3] * p12;
+  o[1] = f[2] * m12 + f[3] * m03;
+  o[2] = f[0] * m03 - f[1] * p12;
+  o[3] = f[1] * p03 - f[0] * m12;
+}
+
+// gamma.G times column spinor (l ; r) = (G.sigma r ; G.sigmabar l)
+template <class R>
+HD void gslash_ket(const cx<R>* G, const cx<R>* f, cx<R>* o) {
+  const cx<R> p03 = G[0] + G[3], m03 = G[0] - G[3];
+  const cx<R> p12 = G[1] + times_i(G[2]), m12 = G[1] - times_i(G[2]);
+  o[0] = m03 * f[2] - m12 * f[3];
+  o[1] = p03 * f[3] - p12 * f[2];
+  o[2] = p03 * f[0] + m12 * f[1];
+  o[3] = p12 * f[0] + m03 * f[1];
+}
+
+// row spinor times (qslash + m), q real
+template <class R>
+HD void bra_prop(const cx<R>* c, const R* q, R m, cx<R>* o) {
+  // (c|d) [[m, q.sigma], [q.sigmabar, m]] = (m c + d q.sigmabar | c q.sigma + m d)
+  const R p03 = q[0] + q[3], m03 = q[0] - q[3];
+  const cx<R> p12 = mk<R>(q[1], q[2]), m12 = mk<R>(q[1], -q[2]);
+  o[0] = m * c[0] + p03 * c[2] + c[3] * p12;
+  o[1] = m * c[1] + c[2] * m12 + m03 * c[3];
+  o[2] = m03 * c[0] - c[1] * p12 + m * c[2];
+  o[3] = p03 * c[1] - c[0] * m12 + m * c[3];
+}
+
+// (qslash + m) times column spinor, q real
+template <class R>
+HD void prop_ket(const R* q, R m, const cx<R>* c, cx<R>* o) {
+  // [[m, q.sigma], [q.sigmabar, m]] (l ; r) = (m l + q.sigma r ; q.sigmabar l + m r)
+  const R p03 = q[0] + q[3], m03 = q[0] - q[3];
+  const cx<R> p12 = mk<R>(q[1], q[2]), m12 = mk<R>(q[1], -q[2]);
+  o[0] = m * c[0] + m03 * c[2] - m12 * c[3];
+  o[1] = m * c[1] + p03 * c[3] - p12 * c[2];
+  o[2] = p03 * c[0] + m12 * c[1] + m * c[2];
+  o[3] = p12 * c[0] + m03 * c[1] + m * c[3];
+}
+
+// bra chain step: F (gamma.G) (qslash + m) / D       (phase +1)
+template <class R>
+HD void bra_step(const cx<R>* F, const cx<R>* G, const R* q, R m, cx<R> invD, cx<R>* out) {
+  cx<R> t[4], u[4];
+  bra_gslash(F, G, t);
+  bra_prop(t, q, m, u);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) out[j] = u[j] * invD;
+}
+
+// ket chain step: (qslash + m) (gamma.G) F / D       (phase +1)
+template <class R>
+HD void ket_step(const cx<R>* G, const cx<R>* F, const R* q, R m, cx<R> invD, cx<R>* out) {
+  cx<R> t[4], u[4];
+  gslash_ket(G, F, t);
+  prop_ket(q, m, t, u);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) out[j] = u[j] * invD;
+}
+
+// fermion-pair vector current j^mu = B gamma^mu K = a sigma^mu r + b sigmabar^mu l,
+// B = (a|b), K = (l;r)
+template <class R>
+HD void pair_current(const cx<R>* B, const cx<R>* K, cx<R>* j) {
+  const cx<R> a1r1 = B[0] * K[2], a2r2 = B[1] * K[3], a1r2 = B[0] * K[3], a2r1 = B[1] * K[2];
+  const cx<R> b1l1 = B[2] * K[0], b2l2 = B[3] * K[1], b1l2 = B[2] * K[1], b2l1 = B[3] * K[0];
+  j[0] = (a1r1 + a2r2) + (b1l1 + b2l2);
+  j[1] = (a1r2 + a2r1) - (b1l2 + b2l1);
+  j[2] = times_i((a2r1 - a1r2) - (b2l1 - b1l2));
+  j[3] = (a1r1 - a2r2) - (b1l1 - b2l2);
+}
+
+// chiral couplings: j^mu = B gamma^mu (cL P_L + cR P_R) K = cR a sigma^mu r + cL b sigmabar^mu l
+template <class R>
+HD void pair_current_lr(const cx<R>* B, const cx<R>* K, R cL, R cR, cx<R>* j) {
+  const cx<R> a1r1 = B[0] * K[2], a2r2 = B[1] * K[3], a1r2 = B[0] * K[3], a2r1 = B[1] * K[2];
+  const cx<R> b1l1 = B[2] * K[0], b2l2 = B[3] * K[1], b1l2 = B[2] * K[1], b2l1 = B[3] * K[0];
+  j[0] = cR * (a1r1 + a2r2) + cL * (b1l1 + b2l2);
+  j[1] = cR * (a1r2 + a2r1) - cL * (b1l2 + b2l1);
+  j[2] = times_i(cR * (a2r1 - a1r2) - cL * (b2l1 - b1l2));
+  j[3] = cR * (a1r1 - a2r2) - cL * (b1l1 - b2l2);
+}
+
+// closing kinds: PJ . G,  PJ . V3(X, Y) / K^2,  PJ . V4_s(X, Y, Z) / K^2
+// (the in-place forms evaluate the block's root vertex and the gluon propagator that
+// joins it to the quark line without storing the block current)
+template <class R>
+HD cx<R> close_dot(const cx<R>* PJ, const cx<R>* G) { return mdot(PJ, G); }
+
+template <class R>
+HD cx<R> close_v3(const cx<R>* PJ, const cx<R>* X, const R* kx, const cx<R>* Y, const R* ky, R invK2) {
+  cx<R> v[4];
+  v3_raw(X, kx, Y, ky, v);
+  return invK2 * mdot(PJ, v);
+}
+
+template <int S, class R>
+HD cx<R> close_v4(const cx<R>* PJ, const cx<R>* X, const cx<R>* Y, const cx<R>* Z, R invK2) {
+  if (S == 1) return invK2 * (mdot(X, Z) * mdot(Y, PJ) - mdot(Y, Z) * mdot(X, PJ));
+  if (S == 2) return invK2 * (mdot(X, Y) * mdot(Z, PJ) - mdot(Y, Z) * mdot(X, PJ));
+  return invK2 * (mdot(X, Y) * mdot(Z, PJ) - mdot(X, Z) * mdot(Y, PJ));
+}
+
+}  // namespace meb300

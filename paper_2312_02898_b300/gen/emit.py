@@ -1,0 +1,476 @@
+"""Emit the per-process device code (straight-line CUDA over the helas.cuh routines).
+
+Build-time generator code.  For each process it writes ``proc_<tag>.cuh`` holding a
+struct ``proc_<tag>`` with
+
+  * constants: NPAR, NCOMB, NCOL, NDIAG (Feynman diagrams, four-gluon vertices counted
+    once), NAMP (diagram terms: a four-gluon vertex gives three), NNODE (off-shell
+    currents per helicity), IDEN, NGLUON, the number of gluon / top propagator
+    denominators, the colour-matrix denominator and the flop counts of one helicity;
+  * denominators<R>(): every distinct propagator denominator, evaluated in FP64 from
+    the FP64 momenta once per event (1/K^2 for gluons, 1/(q^2 - m^2 + i m w) for tops)
+    and stored in the working precision R;
+  * jamps<R>(): for one helicity, the external wavefunctions, the off-shell currents
+    and the diagram terms, each added to its colour flows with a coefficient in
+    {+-1, +-i} (no multiplications);
+  * colour_sum<R>(): sum_ij CF_ij Re(J_i^* J_j) using the symmetry of CF;
+
+plus the integer colour matrix proc_<tag>_CF.
+"""
+from __future__ import annotations
+
+import math
+import os
+
+from . import colour as colmod
+from . import diagrams as dg
+from . import schedule as sc
+
+# Processes: particle roles in the order of the process string.
+PROCESSES = {
+    "e+ e- > mu+ mu-": dict(tag="eemumu", roles=("ebar_in", "e_in", "mubar_out", "mu_out")),
+    "g g > t t~": dict(tag="ggtt", roles=("g_in", "g_in", "t", "tb")),
+    "g g > t t~ g": dict(tag="ggttg", roles=("g_in", "g_in", "t", "tb", "g_out")),
+    "g g > t t~ g g": dict(tag="ggttgg", roles=("g_in", "g_in", "t", "tb", "g_out", "g_out")),
+    "g g > t t~ g g g": dict(tag="ggttggg", roles=("g_in", "g_in", "t", "tb", "g_out", "g_out", "g_out")),
+}
+
+# register budgets of the emitted jamps variants (None: every current in registers)
+BUDGETS = {"ggtt": (None,), "ggttg": (None,), "ggttgg": (None, 20, 10), "ggttggg": (24, 12)}
+
+# real-flop counts of the helas.cuh routines (complex multiply 6, complex add 2,
+# real x complex 2); counted from the formulas as written
+FLOPS = {
+    "ext_eps": 30, "ext_ubar": 40, "ext_v": 40, "ext_u": 40, "ext_vbar": 40,
+    "g3": 24 + 30 + 14 + 14 + 4 * (4 + 6 + 6 + 4) + 8,      # 170
+    "g4": 2 * 30 + 4 * (6 + 6 + 2) + 8,                     # 124
+    "bra": 8 * 6 + 4 * 2 + 4 * (2 + 2 * 6 + 4) + 8 + 4 * 6,  # 160
+    "ket": 8 * 6 + 4 * 2 + 4 * (2 + 2 * 6 + 4) + 8 + 4 * 6,  # 160
+    "pj": 8 * 6 + 12 * 2,                                    # 72
+    "dot": 4 * 6 + 3 * 2,                                    # 30
+    "v3": 24 + 30 + 14 + 14 + 4 * (4 + 6 + 6 + 4) + 30 + 2,  # 194
+    "v4": 4 * 30 + 2 * 6 + 2 + 2,                           # 136
+    "add": 2,
+}
+
+
+def _lit(x):
+    return f"R({float(x)!r})"
+
+
+def allocate_storage(seq, deps_of, externals, budget):
+    """Decide where each current lives: registers while at most ``budget`` values are
+    register-resident, otherwise a slot of the per-thread slot buffer.  Belady's rule:
+    when a new value needs a register and none is free, the resident value whose next
+    use is furthest away moves to a slot (a copy at that point), unless the new value's
+    own next use is further still, in which case it is written to a slot directly.
+
+    Returns (plan, nslot): plan[k] = (evictions [(value, slot)], output location) for
+    step k of seq, location ("R",) or ("S", slot); externals are defined before step 0.
+    budget None keeps everything in registers.
+    """
+    uses = {}
+    for k, (t, x) in enumerate(seq):
+        for d in deps_of(t, x):
+            uses.setdefault(d, []).append(k)
+    last = {v: u[-1] for v, u in uses.items()}
+    ptr = {v: 0 for v in uses}
+
+    def next_use(v, k):
+        u = uses.get(v, [])
+        i = ptr.get(v, 0)
+        while i < len(u) and u[i] <= k:
+            i += 1
+        ptr[v] = i
+        return u[i] if i < len(u) else float("inf")
+
+    regs, slots_of = set(externals), {}
+    free, nslot = [], 0
+    plan = []
+
+    def take_slot():
+        nonlocal nslot
+        if free:
+            free.sort()
+            return free.pop(0)
+        nslot += 1
+        return nslot - 1
+
+    for k, (t, x) in enumerate(seq):
+        ev, loc = [], ("R",)
+        if t == "N" and budget is not None:
+            live_regs = [v for v in regs if last.get(v, -1) >= k]
+            if len(live_regs) >= budget:
+                nu_new = next_use(x, k)
+                far = max(live_regs, key=lambda v: next_use(v, k - 1))
+                if next_use(far, k - 1) > nu_new:
+                    sl = take_slot()
+                    ev.append((far, sl))
+                    regs.discard(far)
+                    slots_of[far] = sl
+                    regs.add(x)
+                else:
+                    sl = take_slot()
+                    slots_of[x] = sl
+                    loc = ("S", sl)
+            else:
+                regs.add(x)
+        elif t == "N":
+            regs.add(x)
+        plan.append((ev, loc))
+        # release values whose last use is this step
+        for d in deps_of(t, x):
+            if last.get(d) == k:
+                regs.discard(d)
+                if d in slots_of:
+                    free.append(slots_of.pop(d))
+        if t == "N" and x not in uses:
+            regs.discard(x)
+            if x in slots_of:
+                free.append(slots_of.pop(x))
+    return plan, nslot
+
+
+class Emitter:
+    def __init__(self, process: str):
+        self.process = process
+        self.spec = PROCESSES[process]
+        self.roles = self.spec["roles"]
+        self.tag = self.spec["tag"]
+        self.npar = len(self.roles)
+        self.gluons = tuple(i for i, r in enumerate(self.roles) if r in ("g_in", "g_out"))
+
+    def mask_of_leaves(self, leaves):
+        m = 0
+        for i in leaves:
+            m |= 1 << i
+        return m
+
+    def kin_terms(self, mask):
+        """signed external momenta whose sum is the incoming momentum of 'mask'
+        (incoming particles +p, outgoing -p)"""
+        terms = []
+        for i in range(self.npar):
+            if mask >> i & 1:
+                r = self.roles[i]
+                terms.append(("+" if r.endswith("_in") else "-", i))
+        return terms
+
+    @staticmethod
+    def _sum_expr(parts, mu, arr="p"):
+        e = " ".join(f"{s} {arr}[{i}][{mu}]" for s, i in parts)
+        return e[2:] if e.startswith("+ ") else e
+
+    # ------------------------------------------------------------------ QCD
+    def emit_qcd(self, budgets=(None,)):
+        it = self.roles.index("t")
+        itb = self.roles.index("tb")
+        gl = self.gluons
+        n = len(gl)
+        sched = sc.build_qcd_schedule(gl, it, itb, restarts=8 if n >= 5 else 24)
+        ndiag = len(dg.qcd_diagrams(gl, split4=False))
+        ncol = math.factorial(n)
+        cf, cden = colmod.colour_matrix(n)
+        iden = 4 * 64 * math.factorial(sum(1 for r in self.roles if r == "g_out"))
+
+        base_name = {("EXT", i): f"x{i}" for i in range(self.npar)}
+        for k, node in enumerate(sched.nodes):
+            base_name[node] = f"w{k}"
+        name = dict(base_name)
+
+        gmask_idx, tmask_idx = {}, {}
+
+        def gmask_of_tree(tree):
+            m = self.mask_of_leaves(dg.leaves(tree))
+            if m not in gmask_idx:
+                gmask_idx[m] = len(gmask_idx)
+            return gmask_idx[m]
+
+        def tmask(node):
+            m = 1 << (it if node[0] == "BRA" else itb)
+            for b in node[1]:
+                m |= self.mask_of_leaves(dg.leaves(b))
+            if m not in tmask_idx:
+                tmask_idx[m] = len(tmask_idx)
+            return m, tmask_idx[m]
+
+        kvars = {}
+        body = []
+
+        def fermion_parts(mask):
+            # momentum along the fermion arrow: top side q = p_t - K(gluons);
+            # antitop side q = -p_tb + K(gluons)
+            if mask >> it & 1:
+                return [("+", it)] + [("-" if s == "+" else "+", i) for s, i in self.kin_terms(mask & ~(1 << it))]
+            return [("-", itb)] + self.kin_terms(mask & ~(1 << itb))
+
+        def kvar(mask, fermion=False):
+            key = (mask, fermion)
+            if key not in kvars:
+                v = f"k{len(kvars)}"
+                kvars[key] = v
+                parts = fermion_parts(mask) if fermion else self.kin_terms(mask)
+                comps = ", ".join(self._sum_expr(parts, mu) for mu in range(4))
+                body.append(f"  const R {v}[4] = {{{comps}}};")
+            return kvars[key]
+
+        fl = {"amp": 0}
+
+        def flop(kind):
+            fl["amp"] += FLOPS[kind]
+
+        for i, r in enumerate(self.roles):
+            if r in ("g_in", "g_out"):
+                body.append(f"  cx<R> x{i}[4]; ext_eps<R>(p[{i}], lam[{i}], {'true' if r == 'g_out' else 'false'}, x{i});")
+                flop("ext_eps")
+            elif r == "t":
+                body.append(f"  cx<R> x{i}[4]; ext_ubar<R>(p[{i}], mt, lam[{i}], x{i});")
+                flop("ext_ubar")
+            elif r == "tb":
+                body.append(f"  cx<R> x{i}[4]; ext_v<R>(p[{i}], mt, lam[{i}], x{i});")
+                flop("ext_v")
+
+        def gk(node):
+            if node[0] == "EXT":
+                return kvar(1 << node[1])
+            return kvar(self.mask_of_leaves(dg.leaves(node[1])))
+
+        pair_count = 0
+
+        def emit_amp(a):
+            nonlocal pair_count
+            nm = [name[x] for x in a.inputs]
+            if a.kind == "DOT":
+                body.append(f"  {{ const cx<R> a = close_dot<R>({nm[0]}, {nm[1]});")
+                flop("dot")
+            else:
+                blk = tuple(x[1] if x[0] == "G" else ("L", x[1]) for x in a.inputs[1:])
+                ig = gmask_of_tree(("3",) + blk) if a.kind == "V3" else gmask_of_tree(("4", a.struct) + blk)
+                if a.kind == "V3":
+                    body.append(f"  {{ const cx<R> a = close_v3<R>({nm[0]}, {nm[1]}, {gk(a.inputs[1])}, "
+                                f"{nm[2]}, {gk(a.inputs[2])}, dg[{ig}]);")
+                    flop("v3")
+                else:
+                    body.append(f"  {{ const cx<R> a = close_v4<{a.struct}, R>({nm[0]}, {nm[1]}, {nm[2]}, "
+                                f"{nm[3]}, dg[{ig}]);")
+                    flop("v4")
+            ops = []
+            for c, v in sorted(a.colour.items()):
+                v = complex(v)
+                if abs(v - 1) < 1e-12:
+                    ops.append(f"J[{c}] += a;")
+                elif abs(v + 1) < 1e-12:
+                    ops.append(f"J[{c}] -= a;")
+                elif abs(v - 1j) < 1e-12:
+                    ops.append(f"J[{c}] += times_i(a);")
+                elif abs(v + 1j) < 1e-12:
+                    ops.append(f"J[{c}] -= times_i(a);")
+                else:
+                    raise ValueError(f"unexpected colour coefficient {v}")
+                flop("add")
+                pair_count += 1
+            body.append("    " + " ".join(ops) + " }")
+
+        def emit_node(node, loc):
+            v = base_name[node]
+            if loc[0] == "S":
+                decl = f"  cx<R>* {v} = ws + {loc[1]} * wss;"
+            else:
+                decl = f"  cx<R> {v}[4];"
+            name[node] = v
+            kind = node[0]
+            if kind == "G":
+                t = node[1]
+                kids = sc.deps(node, it, itb)
+                ig = gmask_of_tree(t)
+                if t[0] == "3":
+                    body.append(f"{decl} g3_current<R>({name[kids[0]]}, {gk(kids[0])}, "
+                                f"{name[kids[1]]}, {gk(kids[1])}, dg[{ig}], {v});")
+                    flop("g3")
+                else:
+                    body.append(f"{decl} g4_current<{t[1]}, R>({name[kids[0]]}, {name[kids[1]]}, "
+                                f"{name[kids[2]]}, dg[{ig}], {v});")
+                    flop("g4")
+            elif kind == "BRA":
+                prev, g = sc.deps(node, it, itb)
+                m, idx = tmask(node)
+                body.append(f"{decl} bra_step<R>({name[prev]}, {name[g]}, {kvar(m, True)}, mt, dt[{idx}], {v});")
+                flop("bra")
+            elif kind == "KET":
+                g, prev = sc.deps(node, it, itb)
+                m, idx = tmask(node)
+                body.append(f"{decl} ket_step<R>({name[g]}, {name[prev]}, {kvar(m, True)}, mt, dt[{idx}], {v});")
+                flop("ket")
+            elif kind == "PJ":
+                b, k = sc.deps(node, it, itb)
+                body.append(f"{decl} pair_current<R>({name[b]}, {name[k]}, {v});")
+                flop("pj")
+
+        def deps_of(t, x):
+            return sc.deps(x, it, itb) if t == "N" else sched.amps[x].inputs
+
+        externals = [("EXT", i) for i in range(self.npar)]
+        ext_lines = list(body)
+        variants = []
+        for vi, budget in enumerate(budgets):
+            plan, nslot = allocate_storage(sched.seq, deps_of, externals, budget)
+            body[:] = list(ext_lines)
+            name.clear()
+            name.update(base_name)
+            kvars.clear()
+            fl["amp"] = sum(FLOPS["ext_eps"] if r.startswith("g") else FLOPS["ext_ubar"] for r in self.roles)
+            pair_count = 0
+            for (t, x), (ev, loc) in zip(sched.seq, plan):
+                for u, sl in ev:
+                    body.append(f"  cx<R>* {base_name[u]}s = ws + {sl} * wss; copy4<R>({base_name[u]}s, {name[u]});")
+                    name[u] = base_name[u] + "s"
+                if t == "N":
+                    emit_node(x, loc)
+                else:
+                    emit_amp(sched.amps[x])
+            variants.append((budget, nslot, list(body)))
+
+        den = ["  double q[4];"]
+        for m, idx in sorted(gmask_idx.items(), key=lambda t: t[1]):
+            parts = self.kin_terms(m)
+            for mu in range(4):
+                den.append(f"  q[{mu}] = {self._sum_expr(parts, mu)};")
+            den.append(f"  dg[{idx}] = R(1.0 / (q[0] * q[0] - q[1] * q[1] - q[2] * q[2] - q[3] * q[3]));")
+        for m, idx in sorted(tmask_idx.items(), key=lambda t: t[1]):
+            parts = fermion_parts(m)
+            tchan = (m & 1) != ((m >> 1) & 1)  # separates the two incoming particles
+            for mu in range(4):
+                den.append(f"  q[{mu}] = {self._sum_expr(parts, mu)};")
+            den.append(f"  {{ const double w = {'(zwt ? 0.0 : wt)' if tchan else 'wt'};")
+            den.append("    const double re = q[0] * q[0] - q[1] * q[1] - q[2] * q[2] - q[3] * q[3] - mt * mt;")
+            den.append("    const double im = mt * w, inv = 1.0 / (re * re + im * im);")
+            den.append(f"    dt[{idx}] = mk<R>(R(re * inv), R(-im * inv)); }}")
+
+        cs = []
+        csflops = 0
+        for i in range(ncol):
+            tr, ti = [], []
+            for j in range(i, ncol):
+                c = int(cf[i, j]) * (1 if j == i else 2)
+                if c == 0:
+                    continue
+                tr.append(f"{_lit(c)} * J[{j}].r")
+                ti.append(f"{_lit(c)} * J[{j}].i")
+                csflops += 4
+            cs.append(f"  {{ const R tr = {' + '.join(tr)}; const R ti = {' + '.join(ti)};")
+            cs.append(f"    s += J[{i}].r * tr + J[{i}].i * ti; }}")
+            csflops += 4
+
+        ngden, ntden = max(1, len(gmask_idx)), max(1, len(tmask_idx))
+        tag = self.tag
+        out = [f"// Generated by paper_2312_02898_b300/gen/emit.py for '{self.process}'. Do not edit.",
+               "#pragma once", '#include "../helas.cuh"', "namespace meb300 {", f"struct proc_{tag} {{",
+               f'static constexpr const char* NAME = "{self.process}";',
+               f"static constexpr int NPAR = {self.npar}, NCOMB = {1 << self.npar}, NCOL = {ncol}, NDIAG = {ndiag};",
+               f"static constexpr int NAMP = {len(sched.amps)}, NNODE = {len(sched.nodes)}, IDEN = {iden}, NGLUON = {n};",
+               f"static constexpr int NDEN_G = {ngden}, NDEN_T = {ntden}, COL_DEN = {cden}, NCOLPAIR = {pair_count};",
+               f"static constexpr long FLOPS_AMP = {fl['amp']}, FLOPS_COL = {csflops};  // per helicity, real flops",
+               f"static constexpr int MAX_LIVE = {sc.max_live(sched, it, itb)};  // currents alive at once",
+               "static constexpr bool QCD = true;", "",
+               "template <class R, class DG, class DT>",
+               "static HD void denominators(const double (*p)[4], double mt, double wt, int zwt, DG& dg, DT& dt) {"]
+        out += den
+        out.append("}")
+        out.append(f"// jamps variants: register budget (currents kept in registers; None = all) and")
+        out.append(f"// slots needed in the per-thread slot buffer ws (slot s at ws + s * wss)")
+        out.append(f"static constexpr int NVARIANT = {len(variants)};")
+        out.append("static constexpr int NSLOT[NVARIANT] = {" + ", ".join(str(v[1]) for v in variants) + "};")
+        out.append("static constexpr int BUDGET[NVARIANT] = {" + ", ".join(str(-1 if v[0] is None else v[0]) for v in variants) + "};")
+        for vi, (budget, nslot, vbody) in enumerate(variants):
+            out += ["", "template <class R, class DG, class DT, class JA>",
+                    f"static HD void jamps_v{vi}(const R (*p)[4], const int* lam, R mt, const DG& dg, const DT& dt, JA& J,"
+                    f" cx<R>* ws, int wss) {{"]
+            out += vbody
+            out.append("}")
+        out += ["", "template <int V, class R, class DG, class DT, class JA>",
+                "static HD void jamps(const R (*p)[4], const int* lam, R mt, const DG& dg, const DT& dt, JA& J,"
+                " cx<R>* ws = nullptr, int wss = 0) {"]
+        for vi in range(len(variants)):
+            out.append(f"  {'if' if vi == 0 else 'else if'} constexpr (V == {vi}) jamps_v{vi}<R>(p, lam, mt, dg, dt, J, ws, wss);")
+        out += ["}"]
+        out += ["", "template <class R, class JA>", "static HD R colour_sum(JA& J) {", "  R s = R(0);"]
+        out += cs
+        out += ["  return s;", "}", "};",
+                f"constexpr int proc_{tag}_CF[{ncol} * {ncol}] = {{{', '.join(str(int(x)) for x in cf.flatten())}}};",
+                "}  // namespace meb300"]
+        stats = dict(ndiag=ndiag, namp=len(sched.amps), nnode=len(sched.nodes), ncol=ncol, pairs=pair_count,
+                     flops_amp=fl["amp"], flops_col=csflops, nden_g=ngden, nden_t=ntden, col_den=cden,
+                     max_live=sc.max_live(sched, it, itb), schedule=sc.summary(sched),
+                     variants=[(b, ns) for b, ns, _ in variants])
+        return "\n".join(out) + "\n", stats
+
+    # ------------------------------------------------------------------ e+e- -> mu+mu-
+    def emit_eemumu(self):
+        fa = 4 * FLOPS["ext_u"] + 4 * FLOPS["pj"] + 2 * FLOPS["dot"] + 6 + 6 + 2
+        out = [f"// Generated by paper_2312_02898_b300/gen/emit.py for '{self.process}'. Do not edit.",
+               "#pragma once", '#include "../helas.cuh"', "namespace meb300 {", "struct proc_eemumu {",
+               f'static constexpr const char* NAME = "{self.process}";',
+               "static constexpr int NPAR = 4, NCOMB = 16, NCOL = 1, NDIAG = 2, NAMP = 2, NNODE = 2, IDEN = 4, NGLUON = 0;",
+               "static constexpr int NDEN_G = 1, NDEN_T = 1, COL_DEN = 1, NCOLPAIR = 2, MAX_LIVE = 2;",
+               f"static constexpr long FLOPS_AMP = {fa}, FLOPS_COL = 4;",
+               "static constexpr bool QCD = false;",
+               "// Photon and Z in the s channel.  dg[0] = 1/s;  dt[0] = 1/(s - mZ^2 + i mZ wZ).",
+               "template <class R, class DG, class DT>",
+               "static HD void denominators(const double (*p)[4], double mZ, double wZ, int, DG& dg, DT& dt) {",
+               "  double q[4];",
+               "  for (int m = 0; m < 4; ++m) q[m] = p[0][m] + p[1][m];",
+               "  const double s = q[0] * q[0] - q[1] * q[1] - q[2] * q[2] - q[3] * q[3];",
+               "  dg[0] = R(1.0 / s);",
+               "  const double re = s - mZ * mZ, im = mZ * wZ, inv = 1.0 / (re * re + im * im);",
+               "  dt[0] = mk<R>(R(re * inv), R(-im * inv));",
+               "}",
+               "// J = i [ (j_e . j_mu)_photon / s + (j_e . j_mu)_Z / D_Z ] in units of e^2: the photon",
+               "// couples with Q_e Q_mu = 1 overall, the Z with (gL, gR) = zc[0..1] on each current.",
+               "static constexpr int NVARIANT = 1;",
+               "static constexpr int NSLOT[1] = {0};",
+               "static constexpr int BUDGET[1] = {-1};",
+               "template <int V, class R, class DG, class DT, class JA>",
+               "static HD void jamps(const R (*p)[4], const int* lam, const R* zc, const DG& dg, const DT& dt, JA& J,",
+               "                     cx<R>* = nullptr, int = 0) {",
+               "  cx<R> x0[4], x1[4], x2[4], x3[4];",
+               "  ext_vbar<R>(p[0], R(0), lam[0], x0);   // incoming e+",
+               "  ext_u<R>(p[1], R(0), lam[1], x1);      // incoming e-",
+               "  ext_v<R>(p[2], R(0), lam[2], x2);      // outgoing mu+",
+               "  ext_ubar<R>(p[3], R(0), lam[3], x3);   // outgoing mu-",
+               "  cx<R> je[4], jm[4];",
+               "  pair_current<R>(x0, x1, je); pair_current<R>(x3, x2, jm);",
+               "  const cx<R> aa = dg[0] * mdot(je, jm);",
+               "  pair_current_lr<R>(x0, x1, zc[0], zc[1], je); pair_current_lr<R>(x3, x2, zc[0], zc[1], jm);",
+               "  const cx<R> az = mdot(je, jm) * dt[0];",
+               "  J[0] += times_i(aa + az);",
+               "}",
+               "template <class R, class JA>",
+               "static HD R colour_sum(JA& J) { return J[0].r * J[0].r + J[0].i * J[0].i; }",
+               "};",
+               "constexpr int proc_eemumu_CF[1] = {1};",
+               "}  // namespace meb300"]
+        stats = dict(ndiag=2, namp=2, nnode=2, ncol=1, pairs=2, flops_amp=fa, flops_col=4, nden_g=1, nden_t=1,
+                     col_den=1, max_live=2)
+        return "\n".join(out) + "\n", stats
+
+    def emit(self):
+        if self.tag == "eemumu":
+            return self.emit_eemumu()
+        return self.emit_qcd(budgets=BUDGETS.get(self.tag, (None,)))
+
+
+def generate_all(outdir: str, processes=None, verbose=False):
+    """Write proc_<tag>.cuh for every process (only when the text changes)."""
+    os.makedirs(outdir, exist_ok=True)
+    stats = {}
+    for proc in (processes or PROCESSES):
+        text, st = Emitter(proc).emit()
+        path = os.path.join(outdir, f"proc_{PROCESSES[proc]['tag']}.cuh")
+        old = open(path).read() if os.path.exists(path) else None
+        if old != text:
+            with open(path, "w") as f:
+                f.write(text)
+        stats[proc] = st
+        if verbose:
+            print(proc, st)
+    return stats
