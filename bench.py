@@ -1,0 +1,301 @@
+"""Throughput benchmark: tree-level matrix elements per second on one B300 (or N, as
+independent shards of events).
+
+Workload (one "step"): g g -> t t~ g g, 1048576 RAMBO events at sqrt(s) = 1500 GeV with
+per-event alpha_s ~ U[0.10, 0.13] and both selection outputs -- every row of the hot
+path (momentum load, couplings, wavefunctions, currents, diagram closings, colour sum,
+helicity sum, selections).  Inputs (226 MB) are larger than the 126 MB L2, so no L2
+flush is needed between steps.  Each precision mode is timed separately; the headline
+``value`` is the mode named by --mode (default: fp64, the mode that matches the FP64
+oracle at 1e-12).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--mode fp64|fp32|mixed]
+    python bench.py --impl reference      # the FP64 CPU oracle on the host cores
+
+Multi-GPU: every rank evaluates its own batch (disjoint event indices); the timed
+region is bracketed by barriers and the maximum over ranks is taken.  No data-path
+collective exists: events are independent ("scaling": "weak").
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PROCESS = "g g > t t~ g g"
+NEVT = 1048576
+METRIC = "ME evals/s per process, FP64 vs mixed at stated rel. err; serving p50/p99 ms"
+UNIT = "ME evals/s"
+FLOP_DTYPE = {"fp64": "f64", "fp32": "f32", "mixed": "f32+bf16"}
+ERR_BOUND = {"fp64": 1e-12, "fp32": 1e-5, "mixed": 1e-5}
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def shard_events(rank: int, nevt_per_rank: int):
+    """first event index of this rank's batch (disjoint, batch-independent RNG)"""
+    return rank * nevt_per_rank
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region"""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                try:
+                    rows.append((float(f[1]), float(f[2]), f[4:9]))
+                except ValueError:
+                    pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["active_mask", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i in range(1, 5) if r[i].lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def oracle_rate(process, nevt_sample, first_event, alphas="uniform"):
+    """the FP64 CPU oracle (as it stands) on a bounded sample: (ME/s, cores, seconds)"""
+    import oracle
+    from paper_2312_02898_b300 import phasespace as ps
+    oracle.build()
+    mom, a, rh, rc = ps.make_batch(process, nevt_sample, seed=0, first_event=first_event, alphas=alphas)
+    t0 = time.perf_counter()
+    oracle.me(process, mom, alphas=a, rnd_hel=rh, rnd_col=rc)
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return nevt_sample / dt, cores, dt
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    sample = args.ref_sample
+    for _ in range(args.warmup):
+        oracle_rate(PROCESS, max(64, sample // 8), 0)
+    times = []
+    for k in range(args.steps):
+        rate, cores, dt = oracle_rate(PROCESS, sample, k * sample)
+        times.append(dt)
+    value = sample * len(times) / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (RAMBO, Philox4x32-10 seed 0)",
+            "config": {"workload": f"{PROCESS}, sqrt(s)=1500 GeV, alpha_s~U[0.10,0.13]",
+                       "events_per_step": sample, "full_batch": NEVT, "precision": "fp64"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{sample} events of the {NEVT}-event workload per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def time_mode(mode, dev_inputs, host_inputs, steps, warmup, dist):
+    """device-resident timing and end-to-end timing of one precision mode"""
+    import torch
+    from paper_2312_02898_b300.binding import MatrixElement
+    m = MatrixElement(PROCESS, precision=mode)
+    mom, a, rh, rc = dev_inputs
+    nevt = mom.shape[0]
+    out = (torch.empty(nevt, dtype=torch.float64, device=mom.device),
+           torch.empty(nevt, dtype=torch.int32, device=mom.device),
+           torch.empty(nevt, dtype=torch.int32, device=mom.device))
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        m.compute(mom, a, rh, rc, out=out, stream=stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    rank = dist.get_rank() if dist else 0
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", 0))) as clk:
+        e0.record(stream)
+        for _ in range(steps):
+            m.compute(mom, a, rh, rc, out=out, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1) / steps
+    if dist:
+        t = torch.tensor([ms], device=mom.device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = t.item()
+    launches, ws_bytes = m.plan(nevt)
+    # end to end through the host entry point: pinned host inputs, copies inside
+    hmom, ha, hrh, hrc = host_inputs
+    hout = (torch.empty(nevt, dtype=torch.float64).pin_memory(), torch.empty(nevt, dtype=torch.int32).pin_memory(),
+            torch.empty(nevt, dtype=torch.int32).pin_memory())
+    for _ in range(max(1, warmup // 2)):
+        m.compute_host(hmom, ha, hrh, hrc, out=hout, stream=stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        m.compute_host(hmom, ha, hrh, hrc, out=hout, stream=stream)
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / steps
+    if dist:
+        t = torch.tensor([e2e_ms], device=mom.device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = t.item()
+    return {"ms": ms, "launches": launches, "workspace_bytes": ws_bytes, "clocks": clk.summary(),
+            "flops_per_event": m.flops_per_event(), "ngood": m.ngood, "e2e_ms": e2e_ms, "me": out[0],
+            "sel": (out[1], out[2])}
+
+
+def accuracy_sample(mode_out, host_inputs, n=48):
+    """max / median relative error of a mode against the FP64 oracle on sampled events"""
+    import oracle
+    hmom, ha, hrh, hrc = (x.numpy() for x in host_inputs)
+    nevt = hmom.shape[0]
+    idx = np.unique(np.linspace(0, nevt - 1, n).astype(np.int64))
+    ref = oracle.me(PROCESS, hmom[idx], alphas=ha[idx])["me"]
+    got = mode_out.cpu().numpy()[idx]
+    rel = np.abs(got / ref - 1)
+    return float(rel.max()), float(np.median(rel)), len(idx)
+
+
+def run_gpu(args):
+    import torch
+    rank, world, local = dist_env()
+    dist = None
+    if world > 1:
+        import torch.distributed as tdist
+        torch.cuda.set_device(local)
+        tdist.init_process_group("nccl")
+        dist = tdist
+    else:
+        torch.cuda.set_device(0)
+    from paper_2312_02898_b300 import binding
+    from paper_2312_02898_b300 import phasespace as ps
+    first = shard_events(rank, NEVT)
+    mom, a, rh, rc = ps.make_batch(PROCESS, NEVT, seed=0, first_event=first, alphas="uniform")
+    host = [torch.from_numpy(x).pin_memory() for x in (mom, a, rh, rc)]
+    dev = [x.cuda(non_blocking=True) for x in host]
+    torch.cuda.synchronize()
+    modes = [args.mode] + [m for m in ("fp64", "fp32") if m != args.mode and not args.only]
+    results = {}
+    for mode in modes:
+        try:
+            results[mode] = time_mode(mode, dev, host, args.steps, args.warmup, dist)
+        except binding.MEError as e:
+            results[mode] = {"error": str(e)}
+    head = results[args.mode]
+    if "error" in head:
+        raise SystemExit(f"headline mode {args.mode} failed: {head['error']}")
+    value = world * NEVT / (head["ms"] * 1e-3)
+    peaks = {p: binding.alu_peak(p, 0.3) for p in ("fp64", "fp32")}
+    per_launch_ms = head["ms"] / head["launches"]
+    events_per_launch = NEVT / head["launches"]
+    peak_key = "fp64" if args.mode == "fp64" else "fp32"
+    achieved = head["flops_per_event"] * events_per_launch / (per_launch_ms * 1e-3) / 1e12
+    peak = peaks[peak_key] / 1e12
+    line = None
+    if rank == 0:
+        acc = {}
+        for mode, r in results.items():
+            if "error" in r:
+                acc[mode] = {"error": r["error"]}
+                continue
+            mx, med, ns = accuracy_sample(r["me"], host)
+            acc[mode] = {"value": NEVT * world / (r["ms"] * 1e-3), "ms_per_step": r["ms"],
+                         "max_rel_err": mx, "median_rel_err": med, "err_sample": ns, "bound": ERR_BOUND[mode],
+                         "gpu_launches_per_step": r["launches"], "clocks": r["clocks"]}
+        try:
+            ref_rate, cores, dt = oracle_rate(PROCESS, args.ref_sample, 0)
+            cpu = {"value": ref_rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                   "sample": f"first {args.ref_sample} events of the workload ({dt:.1f} s)"}
+        except Exception as e:  # the oracle needs gcc; report rather than fail
+            cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": f"failed: {e}"}
+        h2d = sum(x.numel() * x.element_size() for x in host)
+        d2h = NEVT * (8 + 4 + 4)
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": head["ms"], "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": FLOP_DTYPE[args.mode], "data": "synthetic (RAMBO, Philox4x32-10 seed 0)",
+                "config": {"workload": f"{PROCESS}, sqrt(s)=1500 GeV, alpha_s~U[0.10,0.13], both selections",
+                           "events_per_gpu": NEVT, "global_batch": NEVT * world, "precision": args.mode,
+                           "parallelism": f"events sharded over {world} GPU(s), no collective",
+                           "l2": "inputs (226 MB per GPU) larger than L2; no flush"},
+                "clocks": head["clocks"],
+                "gpu_launches": head["launches"] * args.steps,
+                "e2e": {"value": world * NEVT / (head["e2e_ms"] * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": d2h, "entry": "me_compute_host"},
+                "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                             "frac": achieved / peak, "traffic": None,
+                             "peak_source": f"measured {peak_key.upper()} FMA probe (me_probe_alu_peak) in this run",
+                             "flops_per_event": head["flops_per_event"], "kernel": "me_kernel (amplitudes + colour sum)"},
+                "modes": acc,
+                "cpu_baseline": cpu,
+                "alu_peaks_tflops": {k: v / 1e12 for k, v in peaks.items()}}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
+    ap.add_argument("--mode", default="fp64", choices=["fp64", "fp32", "mixed"])
+    ap.add_argument("--only", action="store_true", help="time only the headline mode")
+    ap.add_argument("--ref-sample", type=int, default=4096, help="oracle events per CPU-baseline sample")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("at least 3 warm-up steps")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

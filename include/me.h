@@ -1,0 +1,147 @@
+/*
+ * me.h -- C ABI of the B300 matrix-element library (libme_b300.so).
+ *
+ * Evaluates tree-level matrix elements |M|^2 for batches of phase-space points on one
+ * GPU, one event per CUDA thread.  This is the multi-event interface of the paper
+ * (Section 3: random numbers, momenta and matrix elements produced in batches of up to
+ * several thousand events and handed to an accelerated backend; Fig. 1c), and the
+ * quantity computed is the one the paper offloads (abstract, Section 2): for each event
+ *
+ *     me = (1/IDEN) sum_{helicities h} sum_{colours} |M(p, h, colours)|^2 ,
+ *
+ * built from HELAS-style external wavefunctions, FFV / VVV / VVVV vertex currents for
+ * every Feynman diagram, the helicity sum and the colour sum J^dagger C J over
+ * colour-flow amplitudes J.  IDEN averages over initial spins and colours and divides
+ * by (number of identical final gluons)!.
+ *
+ * Processes (particle order of the string):
+ *   "e+ e- > mu+ mu-"      2 diagrams (photon, Z),   16 helicities,   1 colour flow
+ *   "g g > t t~"           3 diagrams,              16 helicities,   2 colour flows
+ *   "g g > t t~ g"         16 diagrams,             32 helicities,   6
+ *   "g g > t t~ g g"       123 diagrams,            64 helicities,  24
+ *   "g g > t t~ g g g"     1240 diagrams,          128 helicities, 120
+ *
+ * Conventions:
+ *   momenta   (E, px, py, pz) in GeV, FP64, array-of-structures [nevt][npar][4];
+ *   helicity  index h in [0, 2^npar): particle i has helicity +1 if bit (npar-1-i) of h
+ *             is set, else -1 (the physical helicity of that particle);
+ *   colour    flow index = lexicographic rank of the gluon permutation s of the string
+ *             (T^{a_s1} ... T^{a_sn})_{i_t j_tbar} (gluons named by particle index);
+ *   selection sel_hel = first kept helicity whose running sum of |M_h|^2 exceeds
+ *             rnd_hel * total; sel_col = first flow whose running sum of
+ *             w_i = sum_h |J_{h,i}|^2 exceeds rnd_col * sum_i w_i; both 0-based; an event
+ *             whose total is 0 selects 0.
+ *
+ * Ownership: the caller owns every array passed to me_compute (device memory, for
+ * example torch CUDA tensors).  The library owns the handle and what it keeps on the
+ * device (helicity list, per-stream workspace).
+ *
+ * Errors: every call returns 0 on success or a negative status; me_last_error gives
+ * the message.  Non-finite momenta produce NaN in me for that event only.
+ */
+#ifndef ME_B300_H
+#define ME_B300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ME_OK 0
+#define ME_ERR_ARG (-1)        /* null pointer, nevt < 0, unknown process, host pointer */
+#define ME_ERR_MODE (-2)       /* precision mode not available for this process */
+#define ME_ERR_NOMEM (-3)      /* device allocation failed */
+#define ME_ERR_CUDA (-4)       /* a CUDA runtime call or kernel launch failed */
+#define ME_ERR_TIMEOUT (-5)    /* a bounded device-side wait gave up */
+
+#define ME_PREC_FP64 0   /* everything in FP64 */
+#define ME_PREC_FP32 1   /* FP32 amplitudes and colour sum; FP64 inputs, denominators, helicity sum */
+#define ME_PREC_MIXED 2  /* FP32 amplitudes, colour sum on tensor cores (split BF16/FP16 operands,
+                            FP32 accumulation); FP64 inputs, denominators, helicity sum */
+
+typedef struct me_handle me_handle;
+
+/* Standard-model input parameters.  The weak mixing angle follows from (alpha, G_F,
+ * mZ): mW^2 = mZ^2/2 + sqrt(mZ^4/4 - pi alpha mZ^2/(sqrt2 G_F)), sw^2 = 1 - mW^2/mZ^2. */
+typedef struct {
+  double mZ, wZ;            /* Z mass and width [GeV] */
+  double mt, wt;            /* top mass and width [GeV] */
+  double aEWM1;             /* 1/alpha_EM */
+  double Gf;                /* Fermi constant [GeV^-2] */
+  double alphas_default;    /* alpha_s when me_compute gets alphas == NULL */
+  int precision;            /* ME_PREC_* */
+  int zero_width_tchan;     /* 1: no width in t-channel propagators (those that separate
+                               the two incoming particles); Section 3, Tables 1-2 */
+} me_sm_params;
+
+/* Fill p with the defaults: mZ 91.188, wZ 2.4414, mt 173, wt 1.4915, 1/alpha 132.5,
+ * G_F 1.16639e-5, alpha_s 0.118, FP64, widths everywhere. */
+void me_default_params(me_sm_params* p);
+
+/* Create a handle for one process on the current CUDA device.  Runs the helicity
+ * filter: a helicity is kept when |M_h|^2 is not exactly zero (FP64) on any of 1024
+ * fixed RAMBO events at sqrt(s) = 1500 GeV.  *out receives the handle (NULL on error).
+ * Errors: ME_ERR_ARG (null pointer, unknown process, invalid parameter),
+ * ME_ERR_MODE, ME_ERR_NOMEM, ME_ERR_CUDA. */
+int me_init(const char* process, const me_sm_params* p, me_handle** out);
+
+/* Evaluate nevt events, asynchronously on cuda_stream (a cudaStream_t, NULL = legacy
+ * default stream); results are ready when the stream reaches this point.
+ *   momenta  device, FP64 [nevt][npar][4], 16-byte aligned
+ *   alphas   device, FP64 [nevt], or NULL for alphas_default
+ *   rnd_hel  device, FP64 [nevt] in (0,1), or NULL (then sel_hel is not written)
+ *   rnd_col  device, FP64 [nevt] in (0,1), or NULL (then sel_col is not written)
+ *   me       device, FP64 [nevt]                      (output, required)
+ *   sel_hel  device, int32 [nevt] or NULL             (output)
+ *   sel_col  device, int32 [nevt] or NULL             (output)
+ * nevt == 0 is a no-op.  The handle keeps one workspace per stream (grown on demand,
+ * stream-ordered); make one call at the largest size before capturing a stream into a
+ * CUDA graph.  Calls on different streams may run concurrently.
+ * Errors: ME_ERR_ARG (null handle/momenta/me, nevt < 0, a host pointer, misaligned
+ * momenta), ME_ERR_NOMEM, ME_ERR_CUDA, ME_ERR_TIMEOUT. */
+int me_compute(me_handle* h, int64_t nevt, const double* momenta, const double* alphas,
+               const double* rnd_hel, const double* rnd_col, double* me, int32_t* sel_hel,
+               int32_t* sel_col, void* cuda_stream);
+
+/* Same computation with HOST buffers: copies inputs to the device, computes, copies the
+ * outputs back, and synchronises the stream before returning (end-to-end path).  The
+ * host buffers should be pinned for full copy bandwidth.  Same argument meanings and
+ * errors as me_compute, with host instead of device pointers. */
+int me_compute_host(me_handle* h, int64_t nevt, const double* momenta, const double* alphas,
+                    const double* rnd_hel, const double* rnd_col, double* me, int32_t* sel_hel,
+                    int32_t* sel_col, void* cuda_stream);
+
+/* Process shape: external particles, helicity combinations, helicities kept by the
+ * filter, colour flows, Feynman diagrams.  Any output pointer may be NULL. */
+int me_info(const me_handle* h, int* npar, int* ncomb, int* ngood, int* ncol, int* ndiag);
+
+/* The helicity indices kept by the filter, ascending; list must hold ncomb entries. */
+int me_good_helicities(const me_handle* h, int32_t* list);
+
+/* Work per event for the roofline: real floating-point operations of one helicity's
+ * amplitudes and of one helicity's colour sum, as counted by the code generator. */
+int me_flops(const me_handle* h, int64_t* flops_amp_per_hel, int64_t* flops_col_per_hel);
+
+/* Plan of a me_compute call of nevt events: the number of kernel launches it makes
+ * and the bytes of stream workspace it needs (with both selection outputs requested).
+ * Either output pointer may be NULL. */
+int me_plan(const me_handle* h, int64_t nevt, int64_t* launches, int64_t* workspace_bytes);
+
+/* Select the kernel launch configuration (register budget, block size, placement of
+ * per-thread arrays) used by later me_compute calls; 0 is the default.  Returns the
+ * number of configurations available for the handle's precision when config < 0.
+ * Errors: ME_ERR_ARG for an unknown configuration. */
+int me_set_config(me_handle* h, int config);
+
+/* Message of the last failing call on this handle (or of the last failing me_init when
+ * h is NULL).  Never NULL; "" when there was no error. */
+const char* me_last_error(const me_handle* h);
+
+/* Release the handle and its device memory (synchronises the device). */
+void me_free(me_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ME_B300_H */

@@ -1,0 +1,195 @@
+"""Thin Python binding of the C ABI in include/me.h (argument marshalling only).
+
+Every step of the computation runs in libme_b300.so; PyTorch supplies device memory
+and streams.  There is no CPU path: without the built library (or without a CUDA
+device) every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libme_b300.so")
+
+ME_OK, ME_ERR_ARG, ME_ERR_MODE, ME_ERR_NOMEM, ME_ERR_CUDA, ME_ERR_TIMEOUT = 0, -1, -2, -3, -4, -5
+PRECISIONS = {"fp64": 0, "fp32": 1, "mixed": 2}
+
+# the C-ABI entry points declared in include/me.h
+EXPORTS = ("me_default_params", "me_init", "me_compute", "me_compute_host", "me_info", "me_good_helicities",
+           "me_flops", "me_plan", "me_set_config", "me_last_error", "me_free", "me_probe_alu_peak")
+
+
+class SMParams(ctypes.Structure):
+    _fields_ = [("mZ", ctypes.c_double), ("wZ", ctypes.c_double), ("mt", ctypes.c_double),
+                ("wt", ctypes.c_double), ("aEWM1", ctypes.c_double), ("Gf", ctypes.c_double),
+                ("alphas_default", ctypes.c_double), ("precision", ctypes.c_int),
+                ("zero_width_tchan", ctypes.c_int)]
+
+
+class MEError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libme_b300.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: run `python -m paper_2312_02898_b300.build`")
+    lib = ctypes.CDLL(path)
+    vp, i64 = ctypes.c_void_p, ctypes.c_int64
+    ip = ctypes.POINTER(ctypes.c_int)
+    lib.me_default_params.argtypes = [ctypes.POINTER(SMParams)]
+    lib.me_default_params.restype = None
+    lib.me_init.argtypes = [ctypes.c_char_p, ctypes.POINTER(SMParams), ctypes.POINTER(vp)]
+    lib.me_compute.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.me_compute_host.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.me_info.argtypes = [vp, ip, ip, ip, ip, ip]
+    lib.me_good_helicities.argtypes = [vp, ctypes.POINTER(ctypes.c_int32)]
+    lib.me_flops.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
+    lib.me_set_config.argtypes = [vp, ctypes.c_int]
+    lib.me_plan.argtypes = [vp, i64, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
+    lib.me_probe_alu_peak.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
+    lib.me_last_error.argtypes = [vp]
+    lib.me_last_error.restype = ctypes.c_char_p
+    lib.me_free.argtypes = [vp]
+    lib.me_free.restype = None
+    for f in ("me_init", "me_compute", "me_compute_host", "me_info", "me_good_helicities", "me_flops",
+              "me_set_config", "me_plan", "me_probe_alu_peak"):
+        getattr(lib, f).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def default_params() -> SMParams:
+    p = SMParams()
+    load().me_default_params(ctypes.byref(p))
+    return p
+
+
+def alu_peak(precision: str, seconds: float = 0.3) -> float:
+    """measured FMA throughput (flop/s) of the current device for 'fp64' or 'fp32'"""
+    v = ctypes.c_double()
+    rc = load().me_probe_alu_peak(PRECISIONS[precision], seconds, ctypes.byref(v))
+    if rc != ME_OK:
+        raise MEError(rc, "ALU probe failed")
+    return v.value
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+class MatrixElement:
+    """One process on the current CUDA device.
+
+    >>> m = MatrixElement("g g > t t~ g g", precision="fp32")
+    >>> me, sel_hel, sel_col = m.compute(momenta, alphas, rnd_hel, rnd_col)
+    """
+
+    def __init__(self, process: str, precision: str = "fp64", config: int | None = None, **params):
+        self.lib = load()
+        p = default_params()
+        p.precision = PRECISIONS[precision]
+        for k, v in params.items():
+            setattr(p, "alphas_default" if k == "alphas" else k, v)
+        h = ctypes.c_void_p()
+        rc = self.lib.me_init(process.encode(), ctypes.byref(p), ctypes.byref(h))
+        if rc != ME_OK:
+            raise MEError(rc, self.lib.me_last_error(None).decode())
+        self.handle = h
+        self.process = process
+        self.precision = precision
+        self.params = p
+        v = [ctypes.c_int() for _ in range(5)]
+        self.lib.me_info(h, *[ctypes.byref(x) for x in v])
+        self.npar, self.ncomb, self.ngood, self.ncol, self.ndiag = (x.value for x in v)
+        fa, fc = ctypes.c_int64(), ctypes.c_int64()
+        self.lib.me_flops(h, ctypes.byref(fa), ctypes.byref(fc))
+        self.flops_amp_per_hel, self.flops_col_per_hel = fa.value, fc.value
+        self.nconfig = self.lib.me_set_config(h, -1)
+        if config is not None:
+            self.set_config(config)
+
+    def plan(self, nevt: int):
+        """(kernel launches, workspace bytes) of a compute call of nevt events"""
+        n, w = ctypes.c_int64(), ctypes.c_int64()
+        self._check(self.lib.me_plan(self.handle, nevt, ctypes.byref(n), ctypes.byref(w)))
+        return n.value, w.value
+
+    def set_config(self, config: int):
+        self._check(self.lib.me_set_config(self.handle, config))
+
+    def good_helicities(self):
+        arr = (ctypes.c_int32 * self.ncomb)()
+        self.lib.me_good_helicities(self.handle, arr)
+        return list(arr)[: self.ngood]
+
+    def flops_per_event(self) -> int:
+        """generator-counted real flops of one event (amplitudes + colour sum, all kept helicities)"""
+        return self.ngood * (self.flops_amp_per_hel + self.flops_col_per_hel)
+
+    def _check(self, rc):
+        if rc != ME_OK:
+            raise MEError(rc, self.lib.me_last_error(self.handle).decode())
+
+    def compute(self, momenta, alphas=None, rnd_hel=None, rnd_col=None, out=None, stream=None):
+        """Device tensors in, device tensors out (asynchronous on ``stream``)."""
+        import torch
+        if not momenta.is_cuda:
+            raise ValueError("momenta must be a CUDA tensor (use compute_host for host arrays)")
+        nevt = momenta.shape[0]
+        momenta = momenta.contiguous()
+        dev = momenta.device
+        if out is None:
+            me = torch.empty(nevt, dtype=torch.float64, device=dev)
+            sh = torch.empty(nevt, dtype=torch.int32, device=dev) if rnd_hel is not None else None
+            sc = torch.empty(nevt, dtype=torch.int32, device=dev) if rnd_col is not None else None
+        else:
+            me, sh, sc = out
+        s = stream if stream is not None else torch.cuda.current_stream(dev)
+        rc = self.lib.me_compute(self.handle, nevt, _ptr(momenta), _ptr(alphas), _ptr(rnd_hel), _ptr(rnd_col),
+                                 _ptr(me), _ptr(sh), _ptr(sc), ctypes.c_void_p(s.cuda_stream))
+        self._check(rc)
+        return me, sh, sc
+
+    def compute_raw(self, nevt, momenta_ptr, alphas_ptr, rnd_hel_ptr, rnd_col_ptr, me_ptr, sel_hel_ptr,
+                    sel_col_ptr, stream_ptr):
+        """Raw device pointers (integers or None)."""
+        rc = self.lib.me_compute(self.handle, nevt, momenta_ptr, alphas_ptr, rnd_hel_ptr, rnd_col_ptr, me_ptr,
+                                 sel_hel_ptr, sel_col_ptr, stream_ptr)
+        self._check(rc)
+
+    def compute_host(self, momenta, alphas=None, rnd_hel=None, rnd_col=None, out=None, stream=None):
+        """Host (ideally pinned) tensors in and out; the copies happen inside the library."""
+        import torch
+        nevt = momenta.shape[0]
+        if out is None:
+            me = torch.empty(nevt, dtype=torch.float64).pin_memory()
+            sh = torch.empty(nevt, dtype=torch.int32).pin_memory() if rnd_hel is not None else None
+            sc = torch.empty(nevt, dtype=torch.int32).pin_memory() if rnd_col is not None else None
+        else:
+            me, sh, sc = out
+        s = stream if stream is not None else torch.cuda.current_stream()
+        rc = self.lib.me_compute_host(self.handle, nevt, _ptr(momenta), _ptr(alphas), _ptr(rnd_hel), _ptr(rnd_col),
+                                      _ptr(me), _ptr(sh), _ptr(sc), ctypes.c_void_p(s.cuda_stream))
+        self._check(rc)
+        return me, sh, sc
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.me_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,374 @@
+// me_kernels.cuh -- the event-parallel matrix-element kernel (one event per thread).
+//
+// Per event:
+//   1. load the FP64 momenta (array of structures, 16-byte vector loads);
+//   2. evaluate every propagator denominator once, in FP64 (the only place where a
+//      near-resonant top propagator can cancel), and keep 1/D in the working precision;
+//   3. for each helicity kept by the filter: external wavefunctions, off-shell currents
+//      and diagram terms accumulate the colour-flow amplitudes J (generated straight-line
+//      code), then |M_h|^2 = g_s^(2n) sum_ij CF_ij Re(J_i^* J_j) / COL_DEN, accumulated
+//      in FP64 over helicities;
+//   4. me = total / IDEN and the helicity / colour selection from rnd_hel / rnd_col.
+//
+// Where each per-thread array lives is a per-process, per-precision choice (a Layout):
+// registers for small processes; shared memory laid out [index][thread] so that a
+// warp touches consecutive words; or a global workspace laid out [index][event] so
+// that a warp's accesses coalesce.  The generated code keeps at most a fixed number of
+// currents in registers (the variant's budget) and the rest in a slot buffer.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "helas.cuh"
+
+namespace meb300 {
+
+constexpr int MAX_COMB = 128;
+
+struct MeLaunch {
+  int64_t nevt;
+  const double* mom;
+  const double* alphas;
+  double alphas_default;
+  const double* rnd_hel;
+  const double* rnd_col;
+  double* me;
+  int32_t* sel_hel;
+  int32_t* sel_col;
+  double mt, wt;
+  int zwt;
+  double zc[4];      // e+e- -> mu+mu-: Z couplings gL, gR (units of e), mZ, wZ
+  double coup;       // e+e- -> mu+mu-: e^4
+  int ngood;
+  int cum_mode;      // 0: cum holds running sums; 1: cum holds each |M_h|^2 (filter pass)
+  uint8_t good[MAX_COMB];
+  double* cum;       // workspace [ngood][nevt]
+  double* colw;      // workspace [ncol][nevt] (when the colour weights live in global memory)
+  void* slots;       // workspace [block][nslot][BLOCK][4] complex (slot buffer in global memory)
+  void* ktab;        // workspace [block][nkvec][BLOCK][4] real (momentum table in global memory)
+};
+
+// view of an array laid out [index][S]
+template <class T, int S>
+struct Strided {
+  T* b;
+  HD T& operator[](int i) const { return b[i * S]; }
+};
+
+// Launch configuration of one (process, precision):
+//   V        jamps variant (register budget) of the generated code
+//   BLOCK    threads per block
+//   DEN_SMEM denominators in shared memory (else registers)
+//   J_SMEM   colour-flow amplitudes in shared memory (else registers)
+//   W_MODE   colour weights: 0 registers, 1 shared memory, 2 global workspace
+//   S_MODE   slot buffer: 0 none, 1 shared memory, 2 global workspace
+//   K_MODE   momentum table: 1 shared memory, 2 global workspace
+template <int V_, int BLOCK_, bool DEN_SMEM, bool J_SMEM, int W_MODE, int S_MODE, int K_MODE>
+struct Layout {
+  static constexpr int V = V_, BLOCK = BLOCK_;
+  static constexpr bool den_smem = DEN_SMEM, j_smem = J_SMEM;
+  static constexpr int w_mode = W_MODE, s_mode = S_MODE, k_mode = K_MODE;
+};
+
+template <class P, class R, class L>
+constexpr size_t me_smem_bytes() {
+  size_t b = 0;
+  if (L::den_smem) b += size_t(P::NDEN_G) * L::BLOCK * sizeof(R) + size_t(P::NDEN_T) * L::BLOCK * sizeof(cx<R>);
+  if (L::j_smem) b += size_t(P::NCOL) * L::BLOCK * sizeof(cx<R>);
+  if (L::w_mode == 1) b += size_t(P::NCOL) * L::BLOCK * sizeof(R);
+  if (L::s_mode == 1) b += size_t(P::template nslot<L::V>()) * L::BLOCK * 4 * sizeof(cx<R>);
+  if (L::k_mode == 1) b += size_t(P::NKVEC) * L::BLOCK * 4 * sizeof(R);
+  return b;
+}
+
+template <class P, class L, class R, class DG, class DT, class JA>
+__device__ __forceinline__ void call_jamps(const int* lam, const MeLaunch& a, const DG& dg, const DT& dt, JA& J,
+                                           cx<R>* ws, int wss, const R* kt, int kts) {
+  if constexpr (P::QCD) {
+    P::template jamps<L::V, R>(nullptr, lam, R(a.mt), dg, dt, J, ws, wss, kt, kts);
+  } else {
+    const R zc[2] = {R(a.zc[0]), R(a.zc[1])};
+    P::template jamps<L::V, R>(nullptr, lam, zc, dg, dt, J, ws, wss, kt, kts);
+  }
+}
+
+// Colour sum of flows held in shared memory, out of line so that its register use
+// (every J is read by many rows) does not add to that of the amplitude code.
+template <class P, class R, int BLOCK>
+__device__ __noinline__ R colour_sum_strided(cx<R>* s_J_t) {
+  Strided<cx<R>, BLOCK> J{s_J_t};
+  return P::template colour_sum<R>(J);
+}
+
+// One helicity of one event for the large processes: currents, diagram closings,
+// colour sum and colour weights.  Kept out of line so that the helicity-independent
+// loads (denominators, momentum table) cannot be hoisted out of the helicity loop into
+// registers that would stay live across it; everything per helicity lives here.
+template <class P, class R, class L>
+__device__ __noinline__ R one_helicity(int h, R mt, R* s_dg_t, cx<R>* s_dt_t, cx<R>* s_J_t, R* s_w_t, double* colw_t,
+                                       int64_t colw_stride, cx<R>* ws, const R* kt, bool want_w) {
+  constexpr int BLOCK = L::BLOCK;
+  int lam[P::NPAR];
+#pragma unroll
+  for (int i = 0; i < P::NPAR; ++i) lam[i] = ((h >> (P::NPAR - 1 - i)) & 1) ? 1 : -1;
+  Strided<R, BLOCK> dg{s_dg_t};
+  Strided<cx<R>, BLOCK> dt{s_dt_t};
+  R cs;
+  auto weights = [&](const cx<R> z, int c) {
+    const R m2 = z.r * z.r + z.i * z.i;
+    if constexpr (L::w_mode == 1) s_w_t[c * BLOCK] += m2;
+    else if constexpr (L::w_mode == 2) colw_t[c * colw_stride] += double(m2);
+  };
+  if constexpr (L::j_smem) {
+    Strided<cx<R>, BLOCK> J{s_J_t};
+    for (int c = 0; c < P::NCOL; ++c) J[c] = mk<R>(R(0), R(0));
+    P::template jamps<L::V, R>(nullptr, lam, mt, dg, dt, J, ws, BLOCK * 4, kt, BLOCK * 4);
+    cs = colour_sum_strided<P, R, BLOCK>(s_J_t);
+    if (want_w)
+      for (int c = 0; c < P::NCOL; ++c) weights(J[c], c);
+  } else {
+    cx<R> J[P::NCOL];
+#pragma unroll
+    for (int c = 0; c < P::NCOL; ++c) J[c] = mk<R>(R(0), R(0));
+    P::template jamps<L::V, R>(nullptr, lam, mt, dg, dt, J, ws, BLOCK * 4, kt, BLOCK * 4);
+    cs = P::template colour_sum<R>(J);
+    if (want_w) {
+#pragma unroll
+      for (int c = 0; c < P::NCOL; ++c) weights(J[c], c);
+    }
+  }
+  return cs;
+}
+
+template <class P, class R, class L>
+__global__ void __launch_bounds__(L::BLOCK) me_kernel(const MeLaunch a) {
+  constexpr int BLOCK = L::BLOCK;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int tid = threadIdx.x;
+  const int64_t nevt = a.nevt;
+  const int64_t ievt = int64_t(blockIdx.x) * BLOCK + tid;
+  if (ievt >= nevt) return;  // no block-wide barrier below
+
+  // 1. momenta
+  double pd[P::NPAR][4];
+  {
+    const double2* src = reinterpret_cast<const double2*>(a.mom + ievt * (P::NPAR * 4));
+#pragma unroll
+    for (int i = 0; i < P::NPAR; ++i) {
+      const double2 v0 = __ldg(src + 2 * i), v1 = __ldg(src + 2 * i + 1);
+      pd[i][0] = v0.x; pd[i][1] = v0.y; pd[i][2] = v1.x; pd[i][3] = v1.y;
+    }
+  }
+
+  // shared-memory carve-up
+  unsigned char* sp = smem_raw;
+  R* s_dg = nullptr;
+  cx<R>* s_dt = nullptr;
+  cx<R>* s_J = nullptr;
+  R* s_w = nullptr;
+  cx<R>* s_slots = nullptr;
+  R* s_kt = nullptr;
+  if constexpr (L::den_smem) {
+    s_dg = reinterpret_cast<R*>(sp); sp += size_t(P::NDEN_G) * BLOCK * sizeof(R);
+    s_dt = reinterpret_cast<cx<R>*>(sp); sp += size_t(P::NDEN_T) * BLOCK * sizeof(cx<R>);
+  }
+  if constexpr (L::j_smem) { s_J = reinterpret_cast<cx<R>*>(sp); sp += size_t(P::NCOL) * BLOCK * sizeof(cx<R>); }
+  if constexpr (L::w_mode == 1) { s_w = reinterpret_cast<R*>(sp); sp += size_t(P::NCOL) * BLOCK * sizeof(R); }
+  constexpr int NS = P::template nslot<L::V>();
+  static_assert(NS == 0 || L::s_mode != 0, "this jamps variant needs a slot buffer");
+  if constexpr (L::s_mode == 1) { s_slots = reinterpret_cast<cx<R>*>(sp); sp += size_t(NS) * BLOCK * 4 * sizeof(cx<R>); }
+  if constexpr (L::k_mode == 1) { s_kt = reinterpret_cast<R*>(sp); }
+
+  // Slot buffer and momentum table: entry s of this thread at base + s * (BLOCK * 4),
+  // 4 consecutive values.  Both shared and global placements use one tile per block,
+  // so the stride is a compile-time constant and every access is base + immediate.
+  constexpr int wss = BLOCK * 4, kts = BLOCK * 4;
+  cx<R>* ws = nullptr;
+  if constexpr (L::s_mode == 1) ws = s_slots + tid * 4;
+  else if constexpr (L::s_mode == 2) ws = static_cast<cx<R>*>(a.slots) + (size_t(blockIdx.x) * NS * BLOCK + tid) * 4;
+  R* kt;
+  if constexpr (L::k_mode == 1) kt = s_kt + tid * 4;
+  else kt = static_cast<R*>(a.ktab) + (size_t(blockIdx.x) * P::NKVEC * BLOCK + tid) * 4;
+
+  // 2. denominators and momentum table, FP64 once per event
+  R r_dg[L::den_smem ? 1 : P::NDEN_G];
+  cx<R> r_dt[L::den_smem ? 1 : P::NDEN_T];
+  Strided<R, BLOCK> v_dg{s_dg + tid};
+  Strided<cx<R>, BLOCK> v_dt{s_dt + tid};
+  double gfac;
+  if constexpr (P::QCD) {
+    if constexpr (L::den_smem) P::template precompute<R>(pd, a.mt, a.wt, a.zwt, v_dg, v_dt, kt, kts);
+    else P::template precompute<R>(pd, a.mt, a.wt, a.zwt, r_dg, r_dt, kt, kts);
+    const double as = a.alphas ? a.alphas[ievt] : a.alphas_default;
+    const double g2 = 4.0 * 3.14159265358979323846 * as;
+    double gp = 1.0;
+#pragma unroll
+    for (int k = 0; k < P::NGLUON; ++k) gp *= g2;
+    gfac = gp / double(P::COL_DEN);
+  } else {
+    if constexpr (L::den_smem) P::template precompute<R>(pd, a.zc[2], a.zc[3], 0, v_dg, v_dt, kt, kts);
+    else P::template precompute<R>(pd, a.zc[2], a.zc[3], 0, r_dg, r_dt, kt, kts);
+    gfac = a.coup / double(P::COL_DEN);
+  }
+
+  // colour weights
+  const bool want_w = a.sel_col != nullptr && P::NCOL > 1;
+  R r_w[L::w_mode == 0 ? P::NCOL : 1];
+  Strided<R, BLOCK> v_w{s_w + tid};
+  if (want_w) {
+    if constexpr (L::w_mode == 0) {
+#pragma unroll
+      for (int c = 0; c < P::NCOL; ++c) r_w[c] = R(0);
+    } else if constexpr (L::w_mode == 1) {
+      for (int c = 0; c < P::NCOL; ++c) v_w[c] = R(0);
+    } else {
+      for (int c = 0; c < P::NCOL; ++c) a.colw[c * nevt + ievt] = 0.0;
+    }
+  }
+
+  // 3. helicity loop
+  double total = 0.0;
+#pragma unroll 1
+  for (int ih = 0; ih < a.ngood; ++ih) {
+    const int h = a.good[ih];
+    int lam[P::NPAR];
+#pragma unroll
+    for (int i = 0; i < P::NPAR; ++i) lam[i] = ((h >> (P::NPAR - 1 - i)) & 1) ? 1 : -1;
+    R cs;
+    if constexpr (P::QCD && L::den_smem && L::w_mode != 0) {
+      cs = one_helicity<P, R, L>(h, R(a.mt), s_dg + tid, s_dt + tid, L::j_smem ? s_J + tid : nullptr,
+                                 L::w_mode == 1 ? s_w + tid : nullptr, a.colw ? a.colw + ievt : nullptr, nevt,
+                                 ws, kt, want_w);
+    } else if constexpr (L::j_smem) {
+      Strided<cx<R>, BLOCK> J{s_J + tid};
+      for (int c = 0; c < P::NCOL; ++c) J[c] = mk<R>(R(0), R(0));
+      if constexpr (L::den_smem) call_jamps<P, L>(lam, a, v_dg, v_dt, J, ws, wss, kt, kts);
+      else call_jamps<P, L>(lam, a, r_dg, r_dt, J, ws, wss, kt, kts);
+      cs = P::template colour_sum<R>(J);
+      if (want_w) {
+        for (int c = 0; c < P::NCOL; ++c) {
+          const cx<R> z = J[c];
+          const R m2 = z.r * z.r + z.i * z.i;
+          if constexpr (L::w_mode == 0) r_w[c] += m2;
+          else if constexpr (L::w_mode == 1) v_w[c] += m2;
+          else a.colw[c * nevt + ievt] += double(m2);
+        }
+      }
+    } else {
+      cx<R> J[P::NCOL];
+#pragma unroll
+      for (int c = 0; c < P::NCOL; ++c) J[c] = mk<R>(R(0), R(0));
+      if constexpr (L::den_smem) call_jamps<P, L>(lam, a, v_dg, v_dt, J, ws, wss, kt, kts);
+      else call_jamps<P, L>(lam, a, r_dg, r_dt, J, ws, wss, kt, kts);
+      cs = P::template colour_sum<R>(J);
+      if (want_w) {
+#pragma unroll
+        for (int c = 0; c < P::NCOL; ++c) {
+          const R m2 = J[c].r * J[c].r + J[c].i * J[c].i;
+          if constexpr (L::w_mode == 0) r_w[c] += m2;
+          else if constexpr (L::w_mode == 1) v_w[c] += m2;
+          else a.colw[c * nevt + ievt] += double(m2);
+        }
+      }
+    }
+    const double mh = double(cs) * gfac;
+    total += mh;
+    if (a.cum) a.cum[ih * nevt + ievt] = a.cum_mode ? mh : total;
+  }
+
+  // 4. outputs
+  a.me[ievt] = total / double(P::IDEN);
+  if (a.sel_hel && a.cum && !a.cum_mode) {
+    int sel = 0;
+    if (total > 0.0) {
+      const double target = a.rnd_hel[ievt] * total;
+      int found = -1, lastnz = -1;
+      double prev = 0.0;
+      for (int ih = 0; ih < a.ngood; ++ih) {
+        const double c = a.cum[ih * nevt + ievt];
+        if (c > prev) lastnz = ih;
+        if (c > target) { found = ih; break; }
+        prev = c;
+      }
+      const int pick = found >= 0 ? found : lastnz;
+      sel = pick >= 0 ? a.good[pick] : 0;
+    }
+    a.sel_hel[ievt] = sel;
+  }
+  if (a.sel_col) {
+    int sel = 0;
+    if (want_w) {
+      double wt_tot = 0.0;
+      for (int c = 0; c < P::NCOL; ++c) {
+        if constexpr (L::w_mode == 0) wt_tot += double(r_w[c]);
+        else if constexpr (L::w_mode == 1) wt_tot += double(v_w[c]);
+        else wt_tot += a.colw[c * nevt + ievt];
+      }
+      if (wt_tot > 0.0) {
+        const double target = a.rnd_col[ievt] * wt_tot;
+        double run = 0.0;
+        int found = -1, lastnz = -1;
+        for (int c = 0; c < P::NCOL; ++c) {
+          double w;
+          if constexpr (L::w_mode == 0) w = double(r_w[c]);
+          else if constexpr (L::w_mode == 1) w = double(v_w[c]);
+          else w = a.colw[c * nevt + ievt];
+          run += w;
+          if (w > 0.0) lastnz = c;
+          if (run > target) { found = c; break; }
+        }
+        sel = found >= 0 ? found : (lastnz >= 0 ? lastnz : 0);
+      }
+    }
+    a.sel_col[ievt] = sel;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// per-process launch table
+// ---------------------------------------------------------------------------
+// Workspace a launch needs beyond the caller's arrays, in bytes per event.
+struct LaunchNeeds {
+  size_t slot_bytes_per_event;  // global slot buffer
+  size_t ktab_bytes_per_event;  // global momentum table
+  bool colw_global;             // colour weights in a global [ncol][nevt] array
+  int block;                    // threads per block (global tiles cover whole blocks)
+};
+
+struct ProcessOps {
+  const char* name;
+  int npar, ncomb, ncol, ndiag, namp, iden;
+  long flops_amp, flops_col;
+  bool has_mixed;
+  int nconfig[3];  // launch configurations available per precision (index 0 is the default)
+  LaunchNeeds (*needs)(int prec, int config);
+  cudaError_t (*launch)(int prec, int config, const MeLaunch& a, cudaStream_t s);
+};
+
+template <class P, class R, class L>
+LaunchNeeds needs_of() {
+  LaunchNeeds n;
+  n.slot_bytes_per_event = L::s_mode == 2 ? size_t(P::template nslot<L::V>()) * 4 * sizeof(cx<R>) : 0;
+  n.ktab_bytes_per_event = L::k_mode == 2 ? size_t(P::NKVEC) * 4 * sizeof(R) : 0;
+  n.colw_global = L::w_mode == 2;
+  n.block = L::BLOCK;
+  return n;
+}
+
+template <class P, class R, class L>
+cudaError_t launch_me(const MeLaunch& a, cudaStream_t s) {
+  constexpr size_t smem = me_smem_bytes<P, R, L>();
+  static_assert(smem <= 227 * 1024, "shared-memory footprint of this layout exceeds 227 KB");
+  auto k = me_kernel<P, R, L>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+  }
+  const int64_t nblk = (a.nevt + L::BLOCK - 1) / L::BLOCK;
+  k<<<dim3(unsigned(nblk)), dim3(L::BLOCK), smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace meb300

@@ -1,0 +1,486 @@
+// me_lib.cu -- the C ABI declared in include/me.h.
+//
+// Host side of the multi-event interface (paper Section 3, Fig. 1c): a handle per
+// process keeps the derived couplings, the helicities kept by the filter and one
+// device workspace per CUDA stream; me_compute checks its arguments and launches the
+// process kernel on the caller's stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/me.h"
+#include "me_kernels.cuh"
+
+// Each process lives in its own translation unit; a build may leave one out (weak
+// references resolve to null and the process is then reported as unknown).
+namespace meb300 {
+extern const ProcessOps ops_eemumu __attribute__((weak));
+extern const ProcessOps ops_ggtt __attribute__((weak));
+extern const ProcessOps ops_ggttg __attribute__((weak));
+extern const ProcessOps ops_ggttgg __attribute__((weak));
+extern const ProcessOps ops_ggttggg __attribute__((weak));
+}
+using namespace meb300;
+
+namespace {
+
+const ProcessOps* const kProcs[] = {&ops_eemumu, &ops_ggtt, &ops_ggttg, &ops_ggttgg, &ops_ggttggg};
+
+thread_local std::string g_init_error;
+
+struct Workspace {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+// events per launch when the slot buffer lives in global memory (bounds the workspace
+// and keeps 32-bit slot offsets)
+constexpr int64_t kGlobalSlotChunk = 65536;
+
+}  // namespace
+
+struct me_handle {
+  const ProcessOps* ops = nullptr;
+  me_sm_params par{};
+  int config = 0;
+  double zc[4] = {0, 0, 0, 0};
+  double coup = 0;
+  std::vector<int> good;
+  std::mutex mu;
+  std::unordered_map<uintptr_t, Workspace> ws;  // keyed by stream (and purpose)
+  std::string err;
+};
+
+namespace {
+
+int fail(me_handle* h, int code, const std::string& msg) {
+  if (h) {
+    std::lock_guard<std::mutex> g(h->mu);
+    h->err = msg;
+  } else {
+    g_init_error = msg;
+  }
+  return code;
+}
+
+int cuda_fail(me_handle* h, cudaError_t e, const char* where) {
+  const int code = (e == cudaErrorMemoryAllocation) ? ME_ERR_NOMEM : ME_ERR_CUDA;
+  return fail(h, code, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+// splitmix64 (Steele, Lea, Flood 2014) for the library's own filter sample
+struct SplitMix {
+  uint64_t s;
+  double uniform() {
+    uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (double(z >> 12) + 0.5) * (1.0 / 4503599627370496.0);
+  }
+};
+
+// RAMBO (Kleiss, Stirling, Ellis 1986): flat n-body phase space at sqrt(s), massless
+// vectors rescaled to the final-state masses.  Writes [nevt][2+n][4].
+void rambo_sample(int nevt, double sqrt_s, const std::vector<double>& masses, uint64_t seed, double* out) {
+  const int n = int(masses.size());
+  SplitMix rng{seed};
+  std::vector<double> q(4 * n), p(4 * n);
+  const int npar = n + 2;
+  double msum = 0;
+  for (double m : masses) msum += m;
+  for (int e = 0; e < nevt; ++e) {
+    double Q[4] = {0, 0, 0, 0};
+    for (int i = 0; i < n; ++i) {
+      const double c = 2 * rng.uniform() - 1, phi = 2 * M_PI * rng.uniform();
+      const double q0 = -std::log(rng.uniform() * rng.uniform());
+      const double st = std::sqrt(1 - c * c);
+      q[4 * i] = q0;
+      q[4 * i + 1] = q0 * st * std::cos(phi);
+      q[4 * i + 2] = q0 * st * std::sin(phi);
+      q[4 * i + 3] = q0 * c;
+      for (int m = 0; m < 4; ++m) Q[m] += q[4 * i + m];
+    }
+    const double M = std::sqrt(Q[0] * Q[0] - Q[1] * Q[1] - Q[2] * Q[2] - Q[3] * Q[3]);
+    const double b[3] = {-Q[1] / M, -Q[2] / M, -Q[3] / M};
+    const double gam = Q[0] / M, a = 1 / (1 + gam), x = sqrt_s / M;
+    for (int i = 0; i < n; ++i) {
+      const double* qi = &q[4 * i];
+      const double bq = b[0] * qi[1] + b[1] * qi[2] + b[2] * qi[3];
+      p[4 * i] = x * (gam * qi[0] + bq);
+      for (int k = 0; k < 3; ++k) p[4 * i + 1 + k] = x * (qi[1 + k] + b[k] * qi[0] + a * bq * b[k]);
+    }
+    double xi = 1.0;
+    if (msum > 0) {
+      xi = std::sqrt(1 - (msum / sqrt_s) * (msum / sqrt_s));
+      for (int it = 0; it < 50; ++it) {
+        double f = -sqrt_s, fp = 0;
+        for (int i = 0; i < n; ++i) {
+          const double r = std::sqrt(masses[i] * masses[i] + xi * xi * p[4 * i] * p[4 * i]);
+          f += r;
+          fp += xi * p[4 * i] * p[4 * i] / r;
+        }
+        if (std::fabs(f) <= 1e-15 * sqrt_s) break;
+        xi -= f / fp;
+      }
+    }
+    double* o = out + size_t(e) * npar * 4;
+    o[0] = o[3] = sqrt_s / 2;
+    o[1] = o[2] = 0;
+    o[4] = sqrt_s / 2;
+    o[5] = o[6] = 0;
+    o[7] = -sqrt_s / 2;
+    for (int i = 0; i < n; ++i) {
+      double* pi = o + 4 * (i + 2);
+      pi[0] = std::sqrt(masses[i] * masses[i] + xi * xi * p[4 * i] * p[4 * i]);
+      for (int k = 1; k < 4; ++k) pi[k] = xi * p[4 * i + k];
+    }
+  }
+}
+
+std::vector<double> final_masses(const ProcessOps* ops, double mt) {
+  if (ops == &ops_eemumu) return {0.0, 0.0};
+  std::vector<double> m = {mt, mt};
+  for (int i = 4; i < ops->npar; ++i) m.push_back(0.0);
+  return m;
+}
+
+void fill_common(const me_handle* h, MeLaunch& a) {
+  a.alphas_default = h->par.alphas_default;
+  a.mt = h->par.mt;
+  a.wt = h->par.wt;
+  a.zwt = h->par.zero_width_tchan;
+  for (int i = 0; i < 4; ++i) a.zc[i] = h->zc[i];
+  a.coup = h->coup;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// stream-ordered workspace of at least 'bytes' under key
+int get_workspace(me_handle* h, uintptr_t key, cudaStream_t s, size_t bytes, void** out) {
+  std::lock_guard<std::mutex> g(h->mu);
+  Workspace& w = h->ws[key];
+  if (w.bytes < bytes) {
+    if (w.ptr) cudaFreeAsync(w.ptr, s);
+    w.ptr = nullptr;
+    w.bytes = 0;
+    const size_t want = bytes + bytes / 4;
+    cudaError_t e = cudaMallocAsync(&w.ptr, want, s);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      w.ptr = nullptr;
+      h->err = std::string("workspace allocation: ") + cudaGetErrorString(e);
+      return e == cudaErrorMemoryAllocation ? ME_ERR_NOMEM : ME_ERR_CUDA;
+    }
+    w.bytes = want;
+  }
+  *out = w.ptr;
+  return ME_OK;
+}
+
+// Bytes of workspace one launch of 'chunk' events needs, and its carve-up.
+struct Carve {
+  size_t cum = 0, colw = 0, slots = 0, ktab = 0;
+  size_t total() const { return cum + colw + slots + ktab; }
+};
+
+Carve carve(const ProcessOps* ops, const LaunchNeeds& nd, int ngood, int64_t chunk, bool want_hel, bool want_col) {
+  Carve c;
+  auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+  if (want_hel) c.cum = up(size_t(ngood) * chunk * sizeof(double));
+  if (want_col && nd.colw_global) c.colw = up(size_t(ops->ncol) * chunk * sizeof(double));
+  const int64_t padded = (chunk + nd.block - 1) / nd.block * nd.block;  // whole blocks
+  c.slots = up(nd.slot_bytes_per_event * padded);
+  c.ktab = up(nd.ktab_bytes_per_event * padded);
+  return c;
+}
+
+// Launch 'a' over nevt events in chunks, with workspace 'wsp' carved per 'cv'.
+cudaError_t launch_chunks(const ProcessOps* ops, int prec, int config, MeLaunch a, int64_t nevt, int64_t chunk,
+                          const Carve& cv, void* wsp, cudaStream_t s) {
+  char* w = static_cast<char*>(wsp);
+  double* cum = cv.cum ? reinterpret_cast<double*>(w) : a.cum;
+  double* colw = cv.colw ? reinterpret_cast<double*>(w + cv.cum) : nullptr;
+  void* slots = cv.slots ? static_cast<void*>(w + cv.cum + cv.colw) : nullptr;
+  void* ktab = cv.ktab ? static_cast<void*>(w + cv.cum + cv.colw + cv.slots) : nullptr;
+  const int npar = ops->npar;
+  for (int64_t off = 0; off < nevt; off += chunk) {
+    MeLaunch b = a;
+    b.nevt = std::min(chunk, nevt - off);
+    b.mom = a.mom + off * npar * 4;
+    if (a.alphas) b.alphas = a.alphas + off;
+    if (a.rnd_hel) b.rnd_hel = a.rnd_hel + off;
+    if (a.rnd_col) b.rnd_col = a.rnd_col + off;
+    b.me = a.me + off;
+    if (a.sel_hel) b.sel_hel = a.sel_hel + off;
+    if (a.sel_col) b.sel_col = a.sel_col + off;
+    b.cum = cum;
+    b.colw = colw;
+    b.slots = slots;
+    b.ktab = ktab;
+    cudaError_t e = ops->launch(prec, config, b, s);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+int64_t chunk_for(const LaunchNeeds& nd, int64_t nevt) {
+  return (nd.slot_bytes_per_event || nd.ktab_bytes_per_event) ? std::min<int64_t>(nevt, kGlobalSlotChunk) : nevt;
+}
+
+}  // namespace
+
+extern "C" {
+
+void me_default_params(me_sm_params* p) {
+  if (!p) return;
+  p->mZ = 91.188;
+  p->wZ = 2.4414;
+  p->mt = 173.0;
+  p->wt = 1.4915;
+  p->aEWM1 = 132.5;
+  p->Gf = 1.16639e-5;
+  p->alphas_default = 0.118;
+  p->precision = ME_PREC_FP64;
+  p->zero_width_tchan = 0;
+}
+
+int me_init(const char* process, const me_sm_params* p, me_handle** out) {
+  if (out) *out = nullptr;
+  if (!process || !p || !out) return fail(nullptr, ME_ERR_ARG, "me_init: null argument");
+  const ProcessOps* ops = nullptr;
+  for (const ProcessOps* o : kProcs)
+    if (o && std::strcmp(o->name, process) == 0) ops = o;
+  if (!ops) return fail(nullptr, ME_ERR_ARG, std::string("me_init: unknown process '") + process + "'");
+  if (!(p->mZ > 0 && p->wZ >= 0 && p->mt > 0 && p->wt >= 0 && p->aEWM1 > 0 && p->Gf > 0 && p->alphas_default > 0))
+    return fail(nullptr, ME_ERR_ARG, "me_init: parameters must be positive (widths non-negative)");
+  if (p->precision < 0 || p->precision > 2) return fail(nullptr, ME_ERR_ARG, "me_init: unknown precision mode");
+  if (p->precision == ME_PREC_MIXED && !ops->has_mixed)
+    return fail(nullptr, ME_ERR_MODE, "me_init: mixed precision is not available for this process");
+  const double alpha = 1.0 / p->aEWM1;
+  const double mz2 = p->mZ * p->mZ;
+  const double disc = mz2 * mz2 / 4.0 - M_PI * alpha * mz2 / (std::sqrt(2.0) * p->Gf);
+  if (!(disc > 0)) return fail(nullptr, ME_ERR_ARG, "me_init: (alpha, G_F, mZ) admit no W mass");
+
+  me_handle* h = new me_handle();
+  h->ops = ops;
+  h->par = *p;
+  if (const char* env = std::getenv("ME_B300_CONFIG")) {
+    const int c = std::atoi(env);
+    if (c >= 0 && c < ops->nconfig[p->precision]) h->config = c;
+  }
+  const double ee = std::sqrt(4.0 * M_PI * alpha);
+  const double mw2 = mz2 / 2.0 + std::sqrt(disc);
+  const double sw2 = 1.0 - mw2 / mz2, sw = std::sqrt(sw2), cw = std::sqrt(1.0 - sw2);
+  h->zc[0] = (-0.5 + sw2) / (sw * cw);  // charged lepton, left-handed: (T3 - Q sw^2)/(sw cw)
+  h->zc[1] = sw2 / (sw * cw);           // right-handed: -Q sw^2/(sw cw)
+  h->zc[2] = p->mZ;
+  h->zc[3] = p->wZ;
+  h->coup = ee * ee * ee * ee;
+
+  // helicity filter on 1024 fixed RAMBO events, every helicity, FP64
+  const int nf = 1024;
+  std::vector<double> mom(size_t(nf) * ops->npar * 4);
+  rambo_sample(nf, 1500.0, final_masses(ops, p->mt), 12345, mom.data());
+  const LaunchNeeds nd = ops->needs(ME_PREC_FP64, 0);
+  const int64_t chunk = chunk_for(nd, nf);
+  Carve cv = carve(ops, nd, 0, chunk, false, false);
+  double *d_mom = nullptr, *d_me = nullptr, *d_cum = nullptr;
+  void* d_ws = nullptr;
+  cudaError_t e = cudaMalloc(&d_mom, mom.size() * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&d_me, nf * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&d_cum, size_t(ops->ncomb) * nf * sizeof(double));
+  if (e == cudaSuccess && cv.total()) e = cudaMalloc(&d_ws, cv.total());
+  if (e == cudaSuccess) e = cudaMemcpy(d_mom, mom.data(), mom.size() * sizeof(double), cudaMemcpyHostToDevice);
+  std::vector<double> cum(size_t(ops->ncomb) * nf);
+  if (e == cudaSuccess) {
+    MeLaunch a{};
+    fill_common(h, a);
+    a.mom = d_mom;
+    a.me = d_me;
+    a.ngood = ops->ncomb;
+    a.cum_mode = 1;
+    for (int i = 0; i < ops->ncomb; ++i) a.good[i] = uint8_t(i);
+    a.cum = d_cum;  // one launch: the filter sample is smaller than any chunk
+    e = launch_chunks(ops, ME_PREC_FP64, 0, a, nf, nf, cv, d_ws, 0);
+    if (e == cudaSuccess) e = cudaMemcpy(cum.data(), d_cum, cum.size() * sizeof(double), cudaMemcpyDeviceToHost);
+  }
+  cudaFree(d_mom);
+  cudaFree(d_me);
+  cudaFree(d_cum);
+  cudaFree(d_ws);
+  if (e != cudaSuccess) {
+    int rc = cuda_fail(nullptr, e, "me_init helicity filter");
+    delete h;
+    return rc;
+  }
+  for (int hh = 0; hh < ops->ncomb; ++hh) {
+    bool nz = false;
+    for (int ev = 0; ev < nf && !nz; ++ev) nz = cum[size_t(hh) * nf + ev] != 0.0;
+    if (nz) h->good.push_back(hh);
+  }
+  *out = h;
+  return ME_OK;
+}
+
+static int compute_device(me_handle* h, int64_t nevt, const double* momenta, const double* alphas,
+                          const double* rnd_hel, const double* rnd_col, double* me, int32_t* sel_hel,
+                          int32_t* sel_col, cudaStream_t s) {
+  const ProcessOps* ops = h->ops;
+  const int prec = h->par.precision, config = h->config;
+  const int ngood = int(h->good.size());
+  const bool want_hel = sel_hel && rnd_hel;
+  const bool want_col = sel_col && rnd_col;
+  const LaunchNeeds nd = ops->needs(prec, config);
+  const int64_t chunk = chunk_for(nd, nevt);
+  const Carve cv = carve(ops, nd, ngood, chunk, want_hel, want_col);
+  void* wsp = nullptr;
+  if (cv.total()) {
+    int rc = get_workspace(h, reinterpret_cast<uintptr_t>(s) << 1, s, cv.total(), &wsp);
+    if (rc) return rc;
+  }
+  MeLaunch a{};
+  fill_common(h, a);
+  a.mom = momenta;
+  a.alphas = alphas;
+  a.rnd_hel = rnd_hel;
+  a.rnd_col = rnd_col;
+  a.me = me;
+  a.sel_hel = want_hel ? sel_hel : nullptr;
+  a.sel_col = want_col ? sel_col : nullptr;
+  a.ngood = ngood;
+  for (int i = 0; i < ngood; ++i) a.good[i] = uint8_t(h->good[i]);
+  cudaError_t e = launch_chunks(ops, prec, config, a, nevt, chunk, cv, wsp, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "me_compute launch");
+  return ME_OK;
+}
+
+int me_compute(me_handle* h, int64_t nevt, const double* momenta, const double* alphas, const double* rnd_hel,
+               const double* rnd_col, double* me, int32_t* sel_hel, int32_t* sel_col, void* cuda_stream) {
+  if (!h) return fail(nullptr, ME_ERR_ARG, "me_compute: null handle");
+  if (nevt < 0) return fail(h, ME_ERR_ARG, "me_compute: nevt < 0");
+  if (nevt == 0) return ME_OK;
+  if (nevt > (int64_t(1) << 31) * 32) return fail(h, ME_ERR_ARG, "me_compute: nevt too large for one call");
+  if (!momenta || !me) return fail(h, ME_ERR_ARG, "me_compute: momenta and me are required");
+  if (reinterpret_cast<uintptr_t>(momenta) % 16) return fail(h, ME_ERR_ARG, "me_compute: momenta must be 16-byte aligned");
+  if ((sel_hel && !rnd_hel) || (sel_col && !rnd_col))
+    return fail(h, ME_ERR_ARG, "me_compute: a selection output needs its random numbers");
+  const void* ptrs[] = {momenta, me, alphas, rnd_hel, rnd_col, sel_hel, sel_col};
+  for (const void* p : ptrs)
+    if (p && !is_device_ptr(p)) return fail(h, ME_ERR_ARG, "me_compute: arrays must be device memory");
+  return compute_device(h, nevt, momenta, alphas, rnd_hel, rnd_col, me, sel_hel, sel_col,
+                        static_cast<cudaStream_t>(cuda_stream));
+}
+
+int me_compute_host(me_handle* h, int64_t nevt, const double* momenta, const double* alphas,
+                    const double* rnd_hel, const double* rnd_col, double* me, int32_t* sel_hel, int32_t* sel_col,
+                    void* cuda_stream) {
+  if (!h) return fail(nullptr, ME_ERR_ARG, "me_compute_host: null handle");
+  if (nevt < 0) return fail(h, ME_ERR_ARG, "me_compute_host: nevt < 0");
+  if (nevt == 0) return ME_OK;
+  if (!momenta || !me) return fail(h, ME_ERR_ARG, "me_compute_host: momenta and me are required");
+  if ((sel_hel && !rnd_hel) || (sel_col && !rnd_col))
+    return fail(h, ME_ERR_ARG, "me_compute_host: a selection output needs its random numbers");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  const size_t nm = size_t(nevt) * h->ops->npar * 4;
+  // device staging: momenta | alphas | rnd_hel | rnd_col | me | sel_hel | sel_col
+  const size_t bytes = nm * 8 + 4 * size_t(nevt) * 8 + 2 * size_t(nevt) * 4 + 64;
+  void* stage = nullptr;
+  int rc = get_workspace(h, (reinterpret_cast<uintptr_t>(s) << 1) | 1, s, bytes, &stage);
+  if (rc) return rc;
+  char* c = static_cast<char*>(stage);
+  double* d_mom = reinterpret_cast<double*>(c); c += nm * 8;
+  double* d_as = reinterpret_cast<double*>(c); c += size_t(nevt) * 8;
+  double* d_rh = reinterpret_cast<double*>(c); c += size_t(nevt) * 8;
+  double* d_rc = reinterpret_cast<double*>(c); c += size_t(nevt) * 8;
+  double* d_me = reinterpret_cast<double*>(c); c += size_t(nevt) * 8;
+  int32_t* d_sh = reinterpret_cast<int32_t*>(c); c += size_t(nevt) * 4;
+  int32_t* d_sc = reinterpret_cast<int32_t*>(c);
+  cudaError_t e = cudaMemcpyAsync(d_mom, momenta, nm * 8, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && alphas) e = cudaMemcpyAsync(d_as, alphas, nevt * 8, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && rnd_hel) e = cudaMemcpyAsync(d_rh, rnd_hel, nevt * 8, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && rnd_col) e = cudaMemcpyAsync(d_rc, rnd_col, nevt * 8, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "me_compute_host H2D");
+  rc = compute_device(h, nevt, d_mom, alphas ? d_as : nullptr, rnd_hel ? d_rh : nullptr, rnd_col ? d_rc : nullptr,
+                      d_me, sel_hel ? d_sh : nullptr, sel_col ? d_sc : nullptr, s);
+  if (rc) return rc;
+  e = cudaMemcpyAsync(me, d_me, nevt * 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && sel_hel) e = cudaMemcpyAsync(sel_hel, d_sh, nevt * 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && sel_col) e = cudaMemcpyAsync(sel_col, d_sc, nevt * 4, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "me_compute_host D2H");
+  return ME_OK;
+}
+
+int me_info(const me_handle* h, int* npar, int* ncomb, int* ngood, int* ncol, int* ndiag) {
+  if (!h) return ME_ERR_ARG;
+  if (npar) *npar = h->ops->npar;
+  if (ncomb) *ncomb = h->ops->ncomb;
+  if (ngood) *ngood = int(h->good.size());
+  if (ncol) *ncol = h->ops->ncol;
+  if (ndiag) *ndiag = h->ops->ndiag;
+  return ME_OK;
+}
+
+int me_good_helicities(const me_handle* h, int32_t* list) {
+  if (!h || !list) return ME_ERR_ARG;
+  for (size_t i = 0; i < h->good.size(); ++i) list[i] = h->good[i];
+  return ME_OK;
+}
+
+int me_flops(const me_handle* h, int64_t* fa, int64_t* fc) {
+  if (!h) return ME_ERR_ARG;
+  if (fa) *fa = h->ops->flops_amp;
+  if (fc) *fc = h->ops->flops_col;
+  return ME_OK;
+}
+
+int me_plan(const me_handle* h, int64_t nevt, int64_t* launches, int64_t* workspace_bytes) {
+  if (!h || nevt < 0) return ME_ERR_ARG;
+  const LaunchNeeds nd = h->ops->needs(h->par.precision, h->config);
+  const int64_t chunk = std::max<int64_t>(1, chunk_for(nd, nevt));
+  if (launches) *launches = nevt ? (nevt + chunk - 1) / chunk : 0;
+  if (workspace_bytes)
+    *workspace_bytes = int64_t(carve(h->ops, nd, int(h->good.size()), chunk, true, true).total());
+  return ME_OK;
+}
+
+int me_set_config(me_handle* h, int config) {
+  if (!h) return ME_ERR_ARG;
+  const int n = h->ops->nconfig[h->par.precision];
+  if (config < 0) return n;
+  if (config >= n) return fail(h, ME_ERR_ARG, "me_set_config: unknown configuration");
+  h->config = config;
+  return ME_OK;
+}
+
+const char* me_last_error(const me_handle* h) {
+  if (!h) return g_init_error.c_str();
+  return h->err.c_str();
+}
+
+void me_free(me_handle* h) {
+  if (!h) return;
+  cudaDeviceSynchronize();
+  for (auto& kv : h->ws)
+    if (kv.second.ptr) cudaFree(kv.second.ptr);
+  delete h;
+}
+
+}  // extern "C"

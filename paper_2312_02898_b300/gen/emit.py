@@ -36,7 +36,7 @@ PROCESSES = {
 }
 
 # register budgets of the emitted jamps variants (None: every current in registers)
-BUDGETS = {"ggtt": (None,), "ggttg": (None,), "ggttgg": (None, 20, 10), "ggttggg": (24, 12)}
+BUDGETS = {"ggtt": (None,), "ggttg": (None, 6), "ggttgg": (None, 20, 10, 6, 3), "ggttggg": (12, 6)}
 
 # real-flop counts of the helas.cuh routines (complex multiply 6, complex add 2,
 # real x complex 2); counted from the formulas as written
@@ -205,14 +205,12 @@ class Emitter:
             return [("-", itb)] + self.kin_terms(mask & ~(1 << itb))
 
         def kvar(mask, fermion=False):
+            """index expression of a momentum vector in the per-event table kt (filled
+            once per event by precompute(), outside the helicity loop)"""
             key = (mask, fermion)
             if key not in kvars:
-                v = f"k{len(kvars)}"
-                kvars[key] = v
-                parts = fermion_parts(mask) if fermion else self.kin_terms(mask)
-                comps = ", ".join(self._sum_expr(parts, mu) for mu in range(4))
-                body.append(f"  const R {v}[4] = {{{comps}}};")
-            return kvars[key]
+                kvars[key] = self.npar + len(kvars)  # entries 0..npar-1: external momenta
+            return f"(kt + {kvars[key]} * kts)"
 
         fl = {"amp": 0}
 
@@ -221,13 +219,13 @@ class Emitter:
 
         for i, r in enumerate(self.roles):
             if r in ("g_in", "g_out"):
-                body.append(f"  cx<R> x{i}[4]; ext_eps<R>(p[{i}], lam[{i}], {'true' if r == 'g_out' else 'false'}, x{i});")
+                body.append(f"  cx<R> x{i}[4]; ext_eps<R>((kt + {i} * kts), lam[{i}], {'true' if r == 'g_out' else 'false'}, x{i});")
                 flop("ext_eps")
             elif r == "t":
-                body.append(f"  cx<R> x{i}[4]; ext_ubar<R>(p[{i}], mt, lam[{i}], x{i});")
+                body.append(f"  cx<R> x{i}[4]; ext_ubar<R>((kt + {i} * kts), mt, lam[{i}], x{i});")
                 flop("ext_ubar")
             elif r == "tb":
-                body.append(f"  cx<R> x{i}[4]; ext_v<R>(p[{i}], mt, lam[{i}], x{i});")
+                body.append(f"  cx<R> x{i}[4]; ext_v<R>((kt + {i} * kts), mt, lam[{i}], x{i});")
                 flop("ext_v")
 
         def gk(node):
@@ -317,7 +315,6 @@ class Emitter:
             body[:] = list(ext_lines)
             name.clear()
             name.update(base_name)
-            kvars.clear()
             fl["amp"] = sum(FLOPS["ext_eps"] if r.startswith("g") else FLOPS["ext_ubar"] for r in self.roles)
             pair_count = 0
             for (t, x), (ev, loc) in zip(sched.seq, plan):
@@ -346,6 +343,15 @@ class Emitter:
             den.append("    const double im = mt * w, inv = 1.0 / (re * re + im * im);")
             den.append(f"    dt[{idx}] = mk<R>(R(re * inv), R(-im * inv)); }}")
 
+        den.append("  // momentum table: external momenta, then the vectors the vertices use")
+        den.append(f"  for (int i = 0; i < {self.npar}; ++i)")
+        den.append("    for (int m = 0; m < 4; ++m) kt[i * kts + m] = R(p[i][m]);")
+        for (mask, fermion), idx in sorted(kvars.items(), key=lambda t: t[1]):
+            parts = fermion_parts(mask) if fermion else self.kin_terms(mask)
+            for mu in range(4):
+                den.append(f"  kt[{idx} * kts + {mu}] = R({self._sum_expr(parts, mu)});")
+        nk = self.npar + len(kvars)
+
         cs = []
         csflops = 0
         for i in range(ncol):
@@ -372,26 +378,33 @@ class Emitter:
                f"static constexpr long FLOPS_AMP = {fl['amp']}, FLOPS_COL = {csflops};  // per helicity, real flops",
                f"static constexpr int MAX_LIVE = {sc.max_live(sched, it, itb)};  // currents alive at once",
                "static constexpr bool QCD = true;", "",
+               f"static constexpr int NKVEC = {nk};  // momentum vectors in the per-event table",
                "template <class R, class DG, class DT>",
-               "static HD void denominators(const double (*p)[4], double mt, double wt, int zwt, DG& dg, DT& dt) {"]
+               "static HD void precompute(const double (*p)[4], double mt, double wt, int zwt, DG& dg, DT& dt,"
+               " R* kt, int kts) {"]
         out += den
         out.append("}")
         out.append(f"// jamps variants: register budget (currents kept in registers; None = all) and")
         out.append(f"// slots needed in the per-thread slot buffer ws (slot s at ws + s * wss)")
         out.append(f"static constexpr int NVARIANT = {len(variants)};")
         out.append("static constexpr int NSLOT[NVARIANT] = {" + ", ".join(str(v[1]) for v in variants) + "};")
+        chain = "0"
+        for vi in reversed(range(len(variants))):
+            chain = f"(V == {vi} ? {variants[vi][1]} : {chain})"
+        out.append(f"template <int V> static HD constexpr int nslot() {{ return {chain}; }}")
         out.append("static constexpr int BUDGET[NVARIANT] = {" + ", ".join(str(-1 if v[0] is None else v[0]) for v in variants) + "};")
         for vi, (budget, nslot, vbody) in enumerate(variants):
             out += ["", "template <class R, class DG, class DT, class JA>",
                     f"static HD void jamps_v{vi}(const R (*p)[4], const int* lam, R mt, const DG& dg, const DT& dt, JA& J,"
-                    f" cx<R>* ws, int wss) {{"]
+                    f" cx<R>* ws, int wss, const R* kt, int kts) {{"]
             out += vbody
             out.append("}")
         out += ["", "template <int V, class R, class DG, class DT, class JA>",
                 "static HD void jamps(const R (*p)[4], const int* lam, R mt, const DG& dg, const DT& dt, JA& J,"
-                " cx<R>* ws = nullptr, int wss = 0) {"]
+                " cx<R>* ws, int wss, const R* kt, int kts) {"]
         for vi in range(len(variants)):
-            out.append(f"  {'if' if vi == 0 else 'else if'} constexpr (V == {vi}) jamps_v{vi}<R>(p, lam, mt, dg, dt, J, ws, wss);")
+            out.append(f"  {'if' if vi == 0 else 'else if'} constexpr (V == {vi}) "
+                       f"jamps_v{vi}<R>(p, lam, mt, dg, dt, J, ws, wss, kt, kts);")
         out += ["}"]
         out += ["", "template <class R, class JA>", "static HD R colour_sum(JA& J) {", "  R s = R(0);"]
         out += cs
@@ -411,12 +424,14 @@ class Emitter:
                "#pragma once", '#include "../helas.cuh"', "namespace meb300 {", "struct proc_eemumu {",
                f'static constexpr const char* NAME = "{self.process}";',
                "static constexpr int NPAR = 4, NCOMB = 16, NCOL = 1, NDIAG = 2, NAMP = 2, NNODE = 2, IDEN = 4, NGLUON = 0;",
-               "static constexpr int NDEN_G = 1, NDEN_T = 1, COL_DEN = 1, NCOLPAIR = 2, MAX_LIVE = 2;",
+               "static constexpr int NDEN_G = 1, NDEN_T = 1, COL_DEN = 1, NCOLPAIR = 2, MAX_LIVE = 2, NKVEC = 4;",
                f"static constexpr long FLOPS_AMP = {fa}, FLOPS_COL = 4;",
                "static constexpr bool QCD = false;",
                "// Photon and Z in the s channel.  dg[0] = 1/s;  dt[0] = 1/(s - mZ^2 + i mZ wZ).",
                "template <class R, class DG, class DT>",
-               "static HD void denominators(const double (*p)[4], double mZ, double wZ, int, DG& dg, DT& dt) {",
+               "static HD void precompute(const double (*p)[4], double mZ, double wZ, int, DG& dg, DT& dt, R* kt, int kts) {",
+               "  for (int i = 0; i < 4; ++i)",
+               "    for (int m = 0; m < 4; ++m) kt[i * kts + m] = R(p[i][m]);",
                "  double q[4];",
                "  for (int m = 0; m < 4; ++m) q[m] = p[0][m] + p[1][m];",
                "  const double s = q[0] * q[0] - q[1] * q[1] - q[2] * q[2] - q[3] * q[3];",
@@ -428,15 +443,16 @@ class Emitter:
                "// couples with Q_e Q_mu = 1 overall, the Z with (gL, gR) = zc[0..1] on each current.",
                "static constexpr int NVARIANT = 1;",
                "static constexpr int NSLOT[1] = {0};",
+               "template <int V> static HD constexpr int nslot() { return 0; }",
                "static constexpr int BUDGET[1] = {-1};",
                "template <int V, class R, class DG, class DT, class JA>",
                "static HD void jamps(const R (*p)[4], const int* lam, const R* zc, const DG& dg, const DT& dt, JA& J,",
-               "                     cx<R>* = nullptr, int = 0) {",
+               "                     cx<R>*, int, const R* kt, int kts) {",
                "  cx<R> x0[4], x1[4], x2[4], x3[4];",
-               "  ext_vbar<R>(p[0], R(0), lam[0], x0);   // incoming e+",
-               "  ext_u<R>(p[1], R(0), lam[1], x1);      // incoming e-",
-               "  ext_v<R>(p[2], R(0), lam[2], x2);      // outgoing mu+",
-               "  ext_ubar<R>(p[3], R(0), lam[3], x3);   // outgoing mu-",
+               "  ext_vbar<R>(kt, R(0), lam[0], x0);              // incoming e+",
+               "  ext_u<R>(kt + kts, R(0), lam[1], x1);          // incoming e-",
+               "  ext_v<R>(kt + 2 * kts, R(0), lam[2], x2);      // outgoing mu+",
+               "  ext_ubar<R>(kt + 3 * kts, R(0), lam[3], x3);   // outgoing mu-",
                "  cx<R> je[4], jm[4];",
                "  pair_current<R>(x0, x1, je); pair_current<R>(x3, x2, jm);",
                "  const cx<R> aa = dg[0] * mdot(je, jm);",

@@ -1,0 +1,209 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle, event by
+event, on identical seeded RAMBO inputs.
+
+Bars: FP64 mode max relative error <= 1e-12 on every event; FP32 mode <= 1e-5 (max and
+median printed); selected helicity and colour identical except where r * total lies
+within a relative 1e-10 (FP64) of a running-sum boundary.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2312_02898_b300 import phasespace as ps
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+PROCS = ["e+ e- > mu+ mu-", "g g > t t~", "g g > t t~ g", "g g > t t~ g g", "g g > t t~ g g g"]
+# ME_B300_TEST_PROCS="0,1,2,3" restricts a development run to some processes
+_SEL = os.environ.get("ME_B300_TEST_PROCS")
+ACTIVE = [PROCS[int(i)] for i in _SEL.split(",")] if _SEL else PROCS
+# several thread blocks plus a ragged tail, small enough for the oracle in seconds
+NEV = {PROCS[0]: 1000, PROCS[1]: 1000, PROCS[2]: 700, PROCS[3]: 300, PROCS[4]: 77}
+FP32_BOUND = 1e-5
+
+
+def mk(process, precision="fp64", **kw):
+    from paper_2312_02898_b300.binding import MatrixElement
+    return MatrixElement(process, precision=precision, **kw)
+
+
+def to_dev(*arrs):
+    return [None if a is None else torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in arrs]
+
+
+def boundary_ok(sel_gpu, sel_ref, weights, r, rel):
+    """selection equal, or r*total within rel*total of a running-sum boundary"""
+    for e in np.nonzero(sel_gpu != sel_ref)[0]:
+        c = np.cumsum(weights[e])
+        if np.min(np.abs(c - r[e] * c[-1])) > rel * c[-1]:
+            return False, e
+    return True, None
+
+
+_ref_cache = {}
+
+
+def reference(process, nevt, seed=0, alphas="uniform"):
+    key = (process, nevt, seed, alphas)
+    if key not in _ref_cache:
+        mom, a, rh, rc = ps.make_batch(process, nevt, seed=seed, alphas=alphas)
+        ref = oracle.me(process, mom, alphas=a, rnd_hel=rh, rnd_col=rc, want_hel=True, want_colw=True)
+        _ref_cache[key] = (mom, a, rh, rc, ref)
+    return _ref_cache[key]
+
+
+def run_gpu(m, mom, a, rh, rc):
+    me, sh, sc = m.compute(*to_dev(mom, a, rh, rc))
+    torch.cuda.synchronize()
+    return me.cpu().numpy(), sh.cpu().numpy(), sc.cpu().numpy()
+
+
+@pytest.mark.parametrize("process", ACTIVE)
+def test_fp64_parity(process):
+    mom, a, rh, rc, ref = reference(process, NEV[process])
+    m = mk(process, "fp64")
+    for config in range(m.nconfig):
+        m.set_config(config)
+        me, sh, sc = run_gpu(m, mom, a, rh, rc)
+        rel = np.abs(me / ref["me"] - 1)
+        assert rel.max() <= 1e-12, (config, rel.max(), np.argmax(rel))
+        ok, e = boundary_ok(sh, ref["sel_hel"], ref["me_hel"], rh, 1e-10)
+        assert ok, ("sel_hel", config, e)
+        ok, e = boundary_ok(sc, ref["sel_col"], ref["colw"], rc, 1e-10)
+        assert ok, ("sel_col", config, e)
+
+
+@pytest.mark.parametrize("process", ACTIVE)
+def test_fp32_parity(process):
+    mom, a, rh, rc, ref = reference(process, NEV[process])
+    m = mk(process, "fp32")
+    for config in range(m.nconfig):
+        m.set_config(config)
+        me, sh, sc = run_gpu(m, mom, a, rh, rc)
+        rel = np.abs(me / ref["me"] - 1)
+        print(f"{process} fp32 config {config}: max rel {rel.max():.3e} median {np.median(rel):.3e}")
+        assert rel.max() <= FP32_BOUND
+        assert np.mean(sh == ref["sel_hel"]) > 0.99
+        assert np.mean(sc == ref["sel_col"]) > 0.99
+
+
+@pytest.mark.parametrize("process", ACTIVE)
+def test_helicity_filter_keeps_every_contributing_helicity(process):
+    m = mk(process)
+    good = set(m.good_helicities())
+    mom, a, _, _ = ps.make_batch(process, 20, seed=99)
+    ref = oracle.me(process, mom, want_hel=True)
+    contributing = set(np.nonzero((ref["me_hel"] != 0).any(axis=0))[0].tolist())
+    assert contributing <= good
+    if process == PROCS[0]:
+        assert m.ngood == 4
+    assert m.ncomb == 2 ** m.npar
+
+
+def test_info_matches_process_tables():
+    expect = {PROCS[0]: (4, 16, 1, 2), PROCS[1]: (4, 16, 2, 3), PROCS[2]: (5, 32, 6, 16),
+              PROCS[3]: (6, 64, 24, 123), PROCS[4]: (7, 128, 120, 1240)}
+    for p, (npar, ncomb, ncol, ndiag) in expect.items():
+        if p not in ACTIVE:
+            continue
+        m = mk(p)
+        assert (m.npar, m.ncomb, m.ncol, m.ndiag) == (npar, ncomb, ncol, ndiag)
+
+
+def test_edge_cases_and_errors():
+    from paper_2312_02898_b300.binding import MEError
+    p = PROCS[1]
+    m = mk(p)
+    # nevt = 0 is a no-op
+    me, _, _ = m.compute(torch.empty((0, 4, 4), dtype=torch.float64, device="cuda"))
+    assert me.numel() == 0
+    # one event, no alphas (the default is used), no selection
+    mom, a, rh, rc = ps.make_batch(p, 1, seed=3)
+    me, sh, sc = m.compute(to_dev(mom)[0])
+    torch.cuda.synchronize()
+    ref = oracle.me(p, mom)
+    assert abs(me.item() / ref["me"][0] - 1) < 1e-12 and sh is None and sc is None
+    # non-finite momenta poison only their own event
+    mom, a, rh, rc = ps.make_batch(p, 300, seed=4)
+    mom[17, 2, 1] = np.nan
+    me, sh, sc = run_gpu(m, mom, a, rh, rc)
+    assert np.isnan(me[17]) and np.isfinite(np.delete(me, 17)).all()
+    # host memory is rejected with a status code
+    host = torch.from_numpy(mom)
+    dev_me = torch.empty(300, dtype=torch.float64, device="cuda")
+    rc_ = m.lib.me_compute(m.handle, 300, host.data_ptr(), None, None, None, dev_me.data_ptr(), None, None, None)
+    assert rc_ == -1 and b"device memory" in m.lib.me_last_error(m.handle)
+    assert m.lib.me_compute(m.handle, -1, None, None, None, None, None, None, None, None) == -1
+    d = to_dev(mom)[0]
+    rc_ = m.lib.me_compute(m.handle, 10, d.data_ptr() + 8, None, None, None, dev_me.data_ptr(), None, None, None)
+    assert rc_ == -1 and b"aligned" in m.lib.me_last_error(m.handle)
+    assert m.lib.me_set_config(m.handle, 99) == -1
+    # a process without a tensor-core path reports ME_ERR_MODE for mixed precision
+    with pytest.raises(MEError) as ei:
+        mk(PROCS[0], "mixed")
+    assert ei.value.code == -2
+
+
+def test_host_entry_point_matches_device():
+    p = PROCS[2]
+    m = mk(p)
+    mom, a, rh, rc = ps.make_batch(p, 500, seed=5, alphas="uniform")
+    me_d, sh_d, sc_d = m.compute(*to_dev(mom, a, rh, rc))
+    pin = [torch.from_numpy(x).pin_memory() for x in (mom, a, rh, rc)]
+    me_h, sh_h, sc_h = m.compute_host(*pin)
+    assert torch.equal(me_d.cpu(), me_h) and torch.equal(sh_d.cpu(), sh_h) and torch.equal(sc_d.cpu(), sc_h)
+
+
+def test_concurrent_streams_match_sequential():
+    p = PROCS[3]
+    m = mk(p, "fp32")
+    b1 = to_dev(*ps.make_batch(p, 3000, seed=6, alphas="uniform"))
+    b2 = to_dev(*ps.make_batch(p, 2000, seed=7, alphas="uniform"))
+    seq1 = [x.clone() for x in m.compute(*b1)]
+    seq2 = [x.clone() for x in m.compute(*b2)]
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    torch.cuda.synchronize()
+    r1 = m.compute(*b1, stream=s1)
+    r2 = m.compute(*b2, stream=s2)
+    torch.cuda.synchronize()
+    for x, y in zip(seq1 + seq2, list(r1) + list(r2)):
+        assert torch.equal(x, y)
+
+
+def test_batch_split_invariance():
+    # an event's result does not depend on the batch it is evaluated in
+    p = PROCS[3]
+    m = mk(p, "fp64")
+    mom, a, rh, rc = ps.make_batch(p, 2000, seed=8, alphas="uniform")
+    whole = run_gpu(m, mom, a, rh, rc)
+    part = run_gpu(m, mom[700:1300], a[700:1300], rh[700:1300], rc[700:1300])
+    for x, y in zip(whole, part):
+        assert np.array_equal(x[700:1300], y)
+
+
+FULL = [(PROCS[0], 16384, "fp64", None), (PROCS[1], 524288, "fp64", 0.118), (PROCS[2], 524288, "fp32", 0.118),
+        (PROCS[3], 1048576, "fp64", "uniform"), (PROCS[3], 1048576, "fp32", "uniform"),
+        (PROCS[4], 262144, "fp32", 0.118)]
+
+
+@pytest.mark.parametrize("process,nevt,precision,alphas", [f for f in FULL if f[0] in ACTIVE])
+def test_full_size_sampled(process, nevt, precision, alphas):
+    """Workload-size batches in the benchmark's launch configuration: properties on every
+    event and the oracle on a random sample of events."""
+    mom, a, rh, rc = ps.make_batch(process, nevt, seed=0, alphas=alphas)
+    m = mk(process, precision)
+    me, sh, sc = run_gpu(m, mom, a, rh, rc)
+    assert np.isfinite(me).all() and (me > 0).all()
+    assert set(np.unique(sh).tolist()) <= set(m.good_helicities())
+    assert sc.min() >= 0 and sc.max() < m.ncol
+    rng = np.random.default_rng(1)
+    idx = np.sort(rng.choice(nevt, size=24 if process == PROCS[4] else 64, replace=False))
+    idx = np.unique(np.concatenate([idx, [0, nevt - 1]]))
+    ref = oracle.me(process, mom[idx], alphas=None if a is None else a[idx], rnd_hel=rh[idx], rnd_col=rc[idx])
+    rel = np.abs(me[idx] / ref["me"] - 1)
+    assert rel.max() <= (1e-12 if precision == "fp64" else FP32_BOUND)
+    assert np.mean(sh[idx] == ref["sel_hel"]) >= 0.95
