@@ -474,20 +474,37 @@ typedef struct {
   int it;            /* particle index of the top */
 } qcd_ext;
 
+/* Minkowski square in x87 extended precision.  A propagator's momentum is a sum of
+ * external momenta; when that sum is nearly light-like (a gluon almost collinear
+ * with a beam or with another gluon) the plain FP64 square cancels most of its digits.
+ * The invariants are therefore summed and squared in long double and rounded once;
+ * every other operation of the oracle stays in FP64. */
+static long double mdot_l(const long double* a, const long double* b) {
+  return a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
+}
+
 /* colour-ordered amplitude A(sigma) for gluons in the order sigma (gluon slots) */
 static cx amp_ordered(const qcd_ext* x, int n, const int* sigma, double gs, double mt, double wt, int zwt) {
   cx J[MAXG][MAXG][4];
   double K[MAXG][MAXG][4];
+  long double KL[MAXG][MAXG][4]; /* the same sums in extended precision, for invariants */
   unsigned M[MAXG][MAXG];
   for (int len = 1; len <= n; ++len) {
     for (int i = 0; i + len - 1 < n; ++i) {
       int j = i + len - 1;
       if (len == 1) {
-        for (int m = 0; m < 4; ++m) { J[i][i][m] = x->eps[sigma[i]][m]; K[i][i][m] = x->kin[sigma[i]][m]; }
+        for (int m = 0; m < 4; ++m) {
+          J[i][i][m] = x->eps[sigma[i]][m];
+          K[i][i][m] = x->kin[sigma[i]][m];
+          KL[i][i][m] = x->kin[sigma[i]][m];
+        }
         M[i][i] = 1u << x->pidx[sigma[i]];
         continue;
       }
-      for (int m = 0; m < 4; ++m) K[i][j][m] = K[i][i][m] + K[i + 1][j][m];
+      for (int m = 0; m < 4; ++m) {
+        K[i][j][m] = K[i][i][m] + K[i + 1][j][m];
+        KL[i][j][m] = KL[i][i][m] + KL[i + 1][j][m];
+      }
       M[i][j] = M[i][i] | M[i + 1][j];
       cx cur[4] = {0, 0, 0, 0}, t[4];
       for (int k = i; k < j; ++k) {
@@ -499,7 +516,7 @@ static cx amp_ordered(const qcd_ext* x, int n, const int* sigma, double gs, doub
           v4(J[i][k], J[k + 1][l], J[l + 1][j], t);
           for (int m = 0; m < 4; ++m) cur[m] += I * gs * gs * t[m];
         }
-      double P2 = mdot_r(K[i][j], K[i][j]);
+      double P2 = (double)mdot_l(KL[i][j], KL[i][j]);
       for (int m = 0; m < 4; ++m) J[i][j][m] = (-I / P2) * cur[m];
     }
   }
@@ -521,10 +538,14 @@ static cx amp_ordered(const qcd_ext* x, int n, const int* sigma, double gs, doub
     } else {
       /* propagator i(q-slash + m)/(q^2 - m^2 + i m w) with q = p_t - K(first j gluons) */
       double q[4];
-      for (int m = 0; m < 4; ++m) q[m] = x->pt[m] - K[0][j - 1][m];
+      long double qL[4];
+      for (int m = 0; m < 4; ++m) {
+        q[m] = x->pt[m] - K[0][j - 1][m];
+        qL[m] = (long double)x->pt[m] - KL[0][j - 1][m];
+      }
       unsigned mask = M[0][j - 1] | (1u << x->it);
       double w = (zwt && is_tchannel(mask)) ? 0.0 : wt;
-      cx den = mdot_r(q, q) - mt * mt + I * mt * w;
+      cx den = (double)(mdot_l(qL, qL) - (long double)mt * mt) + I * mt * w;
       cx qc[4] = {q[0], q[1], q[2], q[3]}, S[4][4];
       slash(qc, S);
       for (int r = 0; r < 4; ++r) S[r][r] += mt;

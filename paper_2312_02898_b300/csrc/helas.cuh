@@ -61,6 +61,47 @@ template <class R> HD cx<R> mdot(const R* k, const cx<R>* a) {
 }
 
 // ---------------------------------------------------------------------------
+// Double-double arithmetic (Dekker 1971; Knuth TAOCP vol. 2, 4.2.2) for propagator
+// invariants: the Minkowski square of a nearly light-like sum of momenta cancels most
+// of its digits in plain FP64, so the sum and the square are formed without rounding
+// error (error-free sums, FMA-exact products) and rounded once at the end.
+// ---------------------------------------------------------------------------
+struct dd {
+  double hi, lo;
+};
+HD dd dd_two_sum(double a, double b) {
+  const double s = a + b, bb = s - a;
+  return dd{s, (a - (s - bb)) + (b - bb)};
+}
+HD dd dd_renorm(double hi, double lo) {
+  const double s = hi + lo;
+  return dd{s, lo - (s - hi)};
+}
+HD dd dd_add(dd x, dd y) {
+  const dd s = dd_two_sum(x.hi, y.hi);
+  return dd_renorm(s.hi, s.lo + (x.lo + y.lo));
+}
+HD dd dd_add(dd x, double y) {
+  const dd s = dd_two_sum(x.hi, y);
+  return dd_renorm(s.hi, s.lo + x.lo);
+}
+HD dd dd_sq(dd x) {
+  const double p = x.hi * x.hi;
+  const double e = fma(x.hi, x.hi, -p);
+  return dd_renorm(p, e + 2.0 * x.hi * x.lo);
+}
+HD dd dd_neg(dd x) { return dd{-x.hi, -x.lo}; }
+// q^2 - m^2 for q given as four double-double components
+HD double dd_invariant(const dd* q, double m) {
+  dd s = dd_sq(q[0]);
+  s = dd_add(s, dd_neg(dd_sq(q[1])));
+  s = dd_add(s, dd_neg(dd_sq(q[2])));
+  s = dd_add(s, dd_neg(dd_sq(q[3])));
+  s = dd_add(s, -m * m);
+  return s.hi + s.lo;
+}
+
+// ---------------------------------------------------------------------------
 // external wavefunctions
 // ---------------------------------------------------------------------------
 // Two-component helicity eigenvector chi_lam of sigma.p_hat.  Phase convention:

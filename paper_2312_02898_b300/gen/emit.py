@@ -327,22 +327,29 @@ class Emitter:
                     emit_amp(sched.amps[x])
             variants.append((budget, nslot, list(body)))
 
-        den = ["  double q[4];"]
+        den = ["  dd q[4];"]
+
+        def dd_sum(parts):
+            # exact sum of signed momenta, component by component
+            out = []
+            for mu in range(4):
+                s0, i0 = parts[0]
+                e = f"dd{{{'-' if s0 == '-' else ''}p[{i0}][{mu}], 0.0}}"
+                for sgn, i in parts[1:]:
+                    e = f"dd_add({e}, {'-' if sgn == '-' else ''}p[{i}][{mu}])"
+                out.append(f"  q[{mu}] = {e};")
+            return out
+
         for m, idx in sorted(gmask_idx.items(), key=lambda t: t[1]):
-            parts = self.kin_terms(m)
-            for mu in range(4):
-                den.append(f"  q[{mu}] = {self._sum_expr(parts, mu)};")
-            den.append(f"  dg[{idx}] = R(1.0 / (q[0] * q[0] - q[1] * q[1] - q[2] * q[2] - q[3] * q[3]));")
+            den += dd_sum(self.kin_terms(m))
+            den.append(f"  dg[{idx}] = R(1.0 / dd_invariant(q, 0.0));")
         for m, idx in sorted(tmask_idx.items(), key=lambda t: t[1]):
-            parts = fermion_parts(m)
             tchan = (m & 1) != ((m >> 1) & 1)  # separates the two incoming particles
-            for mu in range(4):
-                den.append(f"  q[{mu}] = {self._sum_expr(parts, mu)};")
+            den += dd_sum(fermion_parts(m))
             den.append(f"  {{ const double w = {'(zwt ? 0.0 : wt)' if tchan else 'wt'};")
-            den.append("    const double re = q[0] * q[0] - q[1] * q[1] - q[2] * q[2] - q[3] * q[3] - mt * mt;")
+            den.append("    const double re = dd_invariant(q, mt);")
             den.append("    const double im = mt * w, inv = 1.0 / (re * re + im * im);")
             den.append(f"    dt[{idx}] = mk<R>(R(re * inv), R(-im * inv)); }}")
-
         den.append("  // momentum table: external momenta, then the vectors the vertices use")
         den.append(f"  for (int i = 0; i < {self.npar}; ++i)")
         den.append("    for (int m = 0; m < 4; ++m) kt[i * kts + m] = R(p[i][m]);")
