@@ -219,7 +219,7 @@ def run_gpu(args):
     host = [torch.from_numpy(x).pin_memory() for x in (mom, a, rh, rc)]
     dev = [x.cuda(non_blocking=True) for x in host]
     torch.cuda.synchronize()
-    modes = [args.mode] + [m for m in ("fp64", "fp32") if m != args.mode and not args.only]
+    modes = [args.mode] + [m for m in ("fp64", "fp32", "mixed") if m != args.mode and not args.only]
     results = {}
     for mode in modes:
         try:

@@ -23,8 +23,10 @@
 
 #if defined(__CUDACC__)
 #define HD __host__ __device__ __forceinline__
+#define NOINL __host__ __device__ __noinline__
 #else
 #define HD inline
+#define NOINL __attribute__((noinline))
 #endif
 
 namespace meb300 {

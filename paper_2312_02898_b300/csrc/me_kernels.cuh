@@ -48,6 +48,7 @@ struct MeLaunch {
   double* colw;      // workspace [ncol][nevt] (when the colour weights live in global memory)
   void* slots;       // workspace [block][nslot][BLOCK][4] complex (slot buffer in global memory)
   void* ktab;        // workspace [block][nkvec][BLOCK][4] real (momentum table in global memory)
+  int* err;          // set to 1 when a bounded device-side wait runs out (mapped host memory)
 };
 
 // view of an array laid out [index][S]
@@ -84,13 +85,13 @@ constexpr size_t me_smem_bytes() {
 }
 
 template <class P, class L, class R, class DG, class DT, class JA>
-__device__ __forceinline__ void call_jamps(const int* lam, const MeLaunch& a, const DG& dg, const DT& dt, JA& J,
-                                           cx<R>* ws, int wss, const R* kt, int kts) {
+__device__ __forceinline__ void call_jamps(int h, const MeLaunch& a, const DG& dg, const DT& dt, JA& J, cx<R>* ws,
+                                           const R* kt) {
   if constexpr (P::QCD) {
-    P::template jamps<L::V, R>(nullptr, lam, R(a.mt), dg, dt, J, ws, wss, kt, kts);
+    P::template jamps<L::V, L::BLOCK * 4, R>(h, R(a.mt), dg, dt, J, ws, kt);
   } else {
     const R zc[2] = {R(a.zc[0]), R(a.zc[1])};
-    P::template jamps<L::V, R>(nullptr, lam, zc, dg, dt, J, ws, wss, kt, kts);
+    P::template jamps<L::V, L::BLOCK * 4, R>(h, zc, dg, dt, J, ws, kt);
   }
 }
 
@@ -106,13 +107,10 @@ __device__ __noinline__ R colour_sum_strided(cx<R>* s_J_t) {
 // colour sum and colour weights.  Kept out of line so that the helicity-independent
 // loads (denominators, momentum table) cannot be hoisted out of the helicity loop into
 // registers that would stay live across it; everything per helicity lives here.
-template <class P, class R, class L>
+template <class P, class R, class L, bool COLOUR = true>
 __device__ __noinline__ R one_helicity(int h, R mt, R* s_dg_t, cx<R>* s_dt_t, cx<R>* s_J_t, R* s_w_t, double* colw_t,
                                        int64_t colw_stride, cx<R>* ws, const R* kt, bool want_w) {
   constexpr int BLOCK = L::BLOCK;
-  int lam[P::NPAR];
-#pragma unroll
-  for (int i = 0; i < P::NPAR; ++i) lam[i] = ((h >> (P::NPAR - 1 - i)) & 1) ? 1 : -1;
   Strided<R, BLOCK> dg{s_dg_t};
   Strided<cx<R>, BLOCK> dt{s_dt_t};
   R cs;
@@ -124,15 +122,15 @@ __device__ __noinline__ R one_helicity(int h, R mt, R* s_dg_t, cx<R>* s_dt_t, cx
   if constexpr (L::j_smem) {
     Strided<cx<R>, BLOCK> J{s_J_t};
     for (int c = 0; c < P::NCOL; ++c) J[c] = mk<R>(R(0), R(0));
-    P::template jamps<L::V, R>(nullptr, lam, mt, dg, dt, J, ws, BLOCK * 4, kt, BLOCK * 4);
-    cs = colour_sum_strided<P, R, BLOCK>(s_J_t);
+    P::template jamps<L::V, BLOCK * 4, R>(h, mt, dg, dt, J, ws, kt);
+    cs = COLOUR ? colour_sum_strided<P, R, BLOCK>(s_J_t) : R(0);
     if (want_w)
       for (int c = 0; c < P::NCOL; ++c) weights(J[c], c);
   } else {
     cx<R> J[P::NCOL];
 #pragma unroll
     for (int c = 0; c < P::NCOL; ++c) J[c] = mk<R>(R(0), R(0));
-    P::template jamps<L::V, R>(nullptr, lam, mt, dg, dt, J, ws, BLOCK * 4, kt, BLOCK * 4);
+    P::template jamps<L::V, BLOCK * 4, R>(h, mt, dg, dt, J, ws, kt);
     cs = P::template colour_sum<R>(J);
     if (want_w) {
 #pragma unroll
@@ -178,13 +176,14 @@ __global__ void __launch_bounds__(L::BLOCK) me_kernel(const MeLaunch a) {
   if constexpr (L::w_mode == 1) { s_w = reinterpret_cast<R*>(sp); sp += size_t(P::NCOL) * BLOCK * sizeof(R); }
   constexpr int NS = P::template nslot<L::V>();
   static_assert(NS == 0 || L::s_mode != 0, "this jamps variant needs a slot buffer");
+  static_assert(!P::template grouped<L::V>() || (L::den_smem && L::j_smem),
+                "diagram-group variants take shared-memory views of the denominators and J");
   if constexpr (L::s_mode == 1) { s_slots = reinterpret_cast<cx<R>*>(sp); sp += size_t(NS) * BLOCK * 4 * sizeof(cx<R>); }
   if constexpr (L::k_mode == 1) { s_kt = reinterpret_cast<R*>(sp); }
 
   // Slot buffer and momentum table: entry s of this thread at base + s * (BLOCK * 4),
   // 4 consecutive values.  Both shared and global placements use one tile per block,
   // so the stride is a compile-time constant and every access is base + immediate.
-  constexpr int wss = BLOCK * 4, kts = BLOCK * 4;
   cx<R>* ws = nullptr;
   if constexpr (L::s_mode == 1) ws = s_slots + tid * 4;
   else if constexpr (L::s_mode == 2) ws = static_cast<cx<R>*>(a.slots) + (size_t(blockIdx.x) * NS * BLOCK + tid) * 4;
@@ -199,8 +198,8 @@ __global__ void __launch_bounds__(L::BLOCK) me_kernel(const MeLaunch a) {
   Strided<cx<R>, BLOCK> v_dt{s_dt + tid};
   double gfac;
   if constexpr (P::QCD) {
-    if constexpr (L::den_smem) P::template precompute<R>(pd, a.mt, a.wt, a.zwt, v_dg, v_dt, kt, kts);
-    else P::template precompute<R>(pd, a.mt, a.wt, a.zwt, r_dg, r_dt, kt, kts);
+    if constexpr (L::den_smem) P::template precompute<BLOCK * 4, R>(pd, a.mt, a.wt, a.zwt, v_dg, v_dt, kt);
+    else P::template precompute<BLOCK * 4, R>(pd, a.mt, a.wt, a.zwt, r_dg, r_dt, kt);
     const double as = a.alphas ? a.alphas[ievt] : a.alphas_default;
     const double g2 = 4.0 * 3.14159265358979323846 * as;
     double gp = 1.0;
@@ -208,8 +207,8 @@ __global__ void __launch_bounds__(L::BLOCK) me_kernel(const MeLaunch a) {
     for (int k = 0; k < P::NGLUON; ++k) gp *= g2;
     gfac = gp / double(P::COL_DEN);
   } else {
-    if constexpr (L::den_smem) P::template precompute<R>(pd, a.zc[2], a.zc[3], 0, v_dg, v_dt, kt, kts);
-    else P::template precompute<R>(pd, a.zc[2], a.zc[3], 0, r_dg, r_dt, kt, kts);
+    if constexpr (L::den_smem) P::template precompute<BLOCK * 4, R>(pd, a.zc[2], a.zc[3], 0, v_dg, v_dt, kt);
+    else P::template precompute<BLOCK * 4, R>(pd, a.zc[2], a.zc[3], 0, r_dg, r_dt, kt);
     gfac = a.coup / double(P::COL_DEN);
   }
 
@@ -233,9 +232,6 @@ __global__ void __launch_bounds__(L::BLOCK) me_kernel(const MeLaunch a) {
 #pragma unroll 1
   for (int ih = 0; ih < a.ngood; ++ih) {
     const int h = a.good[ih];
-    int lam[P::NPAR];
-#pragma unroll
-    for (int i = 0; i < P::NPAR; ++i) lam[i] = ((h >> (P::NPAR - 1 - i)) & 1) ? 1 : -1;
     R cs;
     if constexpr (P::QCD && L::den_smem && L::w_mode != 0) {
       cs = one_helicity<P, R, L>(h, R(a.mt), s_dg + tid, s_dt + tid, L::j_smem ? s_J + tid : nullptr,
@@ -244,8 +240,8 @@ __global__ void __launch_bounds__(L::BLOCK) me_kernel(const MeLaunch a) {
     } else if constexpr (L::j_smem) {
       Strided<cx<R>, BLOCK> J{s_J + tid};
       for (int c = 0; c < P::NCOL; ++c) J[c] = mk<R>(R(0), R(0));
-      if constexpr (L::den_smem) call_jamps<P, L>(lam, a, v_dg, v_dt, J, ws, wss, kt, kts);
-      else call_jamps<P, L>(lam, a, r_dg, r_dt, J, ws, wss, kt, kts);
+      if constexpr (L::den_smem) call_jamps<P, L>(h, a, v_dg, v_dt, J, ws, kt);
+      else call_jamps<P, L>(h, a, r_dg, r_dt, J, ws, kt);
       cs = P::template colour_sum<R>(J);
       if (want_w) {
         for (int c = 0; c < P::NCOL; ++c) {
@@ -260,8 +256,8 @@ __global__ void __launch_bounds__(L::BLOCK) me_kernel(const MeLaunch a) {
       cx<R> J[P::NCOL];
 #pragma unroll
       for (int c = 0; c < P::NCOL; ++c) J[c] = mk<R>(R(0), R(0));
-      if constexpr (L::den_smem) call_jamps<P, L>(lam, a, v_dg, v_dt, J, ws, wss, kt, kts);
-      else call_jamps<P, L>(lam, a, r_dg, r_dt, J, ws, wss, kt, kts);
+      if constexpr (L::den_smem) call_jamps<P, L>(h, a, v_dg, v_dt, J, ws, kt);
+      else call_jamps<P, L>(h, a, r_dg, r_dt, J, ws, kt);
       cs = P::template colour_sum<R>(J);
       if (want_w) {
 #pragma unroll

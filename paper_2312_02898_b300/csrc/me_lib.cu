@@ -58,6 +58,8 @@ struct me_handle {
   std::mutex mu;
   std::unordered_map<uintptr_t, Workspace> ws;  // keyed by stream (and purpose)
   std::string err;
+  int* err_host = nullptr;  // mapped pinned word the kernels raise on a timed-out wait
+  int* err_dev = nullptr;
 };
 
 namespace {
@@ -281,6 +283,13 @@ int me_init(const char* process, const me_sm_params* p, me_handle** out) {
   me_handle* h = new me_handle();
   h->ops = ops;
   h->par = *p;
+  if (cudaHostAlloc(reinterpret_cast<void**>(&h->err_host), sizeof(int), cudaHostAllocMapped) == cudaSuccess) {
+    *h->err_host = 0;
+    if (cudaHostGetDevicePointer(reinterpret_cast<void**>(&h->err_dev), h->err_host, 0) != cudaSuccess) h->err_dev = nullptr;
+  } else {
+    cudaGetLastError();
+    h->err_host = nullptr;
+  }
   if (const char* env = std::getenv("ME_B300_CONFIG")) {
     const int c = std::atoi(env);
     if (c >= 0 && c < ops->nconfig[p->precision]) h->config = c;
@@ -355,8 +364,14 @@ static int compute_device(me_handle* h, int64_t nevt, const double* momenta, con
     int rc = get_workspace(h, reinterpret_cast<uintptr_t>(s) << 1, s, cv.total(), &wsp);
     if (rc) return rc;
   }
+  if (h->err_host && *h->err_host) {
+    *h->err_host = 0;
+    return fail(h, ME_ERR_TIMEOUT, "me_compute: a device-side wait of an earlier call on this handle timed out; "
+                                   "its events were set to NaN");
+  }
   MeLaunch a{};
   fill_common(h, a);
+  a.err = h->err_dev;
   a.mom = momenta;
   a.alphas = alphas;
   a.rnd_hel = rnd_hel;
@@ -425,6 +440,10 @@ int me_compute_host(me_handle* h, int64_t nevt, const double* momenta, const dou
   if (e == cudaSuccess && sel_col) e = cudaMemcpyAsync(sel_col, d_sc, nevt * 4, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(h, e, "me_compute_host D2H");
+  if (h->err_host && *h->err_host) {
+    *h->err_host = 0;
+    return fail(h, ME_ERR_TIMEOUT, "me_compute_host: a device-side wait timed out; its events were set to NaN");
+  }
   return ME_OK;
 }
 
@@ -480,6 +499,7 @@ void me_free(me_handle* h) {
   cudaDeviceSynchronize();
   for (auto& kv : h->ws)
     if (kv.second.ptr) cudaFree(kv.second.ptr);
+  if (h->err_host) cudaFreeHost(h->err_host);
   delete h;
 }
 

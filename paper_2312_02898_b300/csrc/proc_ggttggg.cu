@@ -11,8 +11,8 @@ namespace meb300 {
 namespace {
 using P = proc_ggttggg;
 template <int PREC, int C> struct Cfg;
-template <> struct Cfg<0, 0> { using R = double; using L = Layout<1, 64, true, true, 2, 2, 2>; };
-template <> struct Cfg<1, 0> { using R = float; using L = Layout<1, 128, true, true, 2, 2, 2>; };
+template <> struct Cfg<0, 0> { using R = double; using L = Layout<0, 64, true, true, 2, 2, 2>; };
+template <> struct Cfg<1, 0> { using R = float; using L = Layout<0, 128, true, true, 2, 2, 2>; };
 
 LaunchNeeds needs(int prec, int config) {
   switch (prec * 8 + config) {

@@ -35,8 +35,16 @@ PROCESSES = {
     "g g > t t~ g g g": dict(tag="ggttggg", roles=("g_in", "g_in", "t", "tb", "g_out", "g_out", "g_out")),
 }
 
-# register budgets of the emitted jamps variants (None: every current in registers)
-BUDGETS = {"ggtt": (None,), "ggttg": (None, 6), "ggttgg": (None, 20, 10, 6, 3), "ggttggg": (12, 6)}
+# jamps variants per process: (register budget, diagram-group size).  The budget is the
+# number of currents kept in registers (None: all); a group size splits the emission
+# sequence into out-of-line functions of that many steps (diagram groups), with every
+# value that crosses a group boundary passed through the slot buffer.
+VARIANTS = {
+    "ggtt": ((None, None),),
+    "ggttg": ((None, None), (6, None)),
+    "ggttgg": ((None, None), (20, None), (10, None), (6, None), (3, None), (10, 160)),
+    "ggttggg": ((12, 160), (6, 160)),
+}
 
 # real-flop counts of the helas.cuh routines (complex multiply 6, complex add 2,
 # real x complex 2); counted from the formulas as written
@@ -58,7 +66,7 @@ def _lit(x):
     return f"R({float(x)!r})"
 
 
-def allocate_storage(seq, deps_of, externals, budget):
+def allocate_storage(seq, deps_of, externals, budget, boundaries=()):
     """Decide where each current lives: registers while at most ``budget`` values are
     register-resident, otherwise a slot of the per-thread slot buffer.  Belady's rule:
     when a new value needs a register and none is free, the resident value whose next
@@ -67,7 +75,8 @@ def allocate_storage(seq, deps_of, externals, budget):
 
     Returns (plan, nslot): plan[k] = (evictions [(value, slot)], output location) for
     step k of seq, location ("R",) or ("S", slot); externals are defined before step 0.
-    budget None keeps everything in registers.
+    budget None keeps everything in registers.  At every step index in ``boundaries``
+    all register-resident live values move to slots (a diagram-group boundary).
     """
     uses = {}
     for k, (t, x) in enumerate(seq):
@@ -96,8 +105,15 @@ def allocate_storage(seq, deps_of, externals, budget):
         nslot += 1
         return nslot - 1
 
+    boundaries = set(boundaries)
     for k, (t, x) in enumerate(seq):
         ev, loc = [], ("R",)
+        if k in boundaries:
+            for v in sorted((v for v in regs if last.get(v, -1) >= k), key=repr):
+                sl = take_slot()
+                ev.append((v, sl))
+                slots_of[v] = sl
+            regs.clear()
         if t == "N" and budget is not None:
             live_regs = [v for v in regs if last.get(v, -1) >= k]
             if len(live_regs) >= budget:
@@ -162,7 +178,7 @@ class Emitter:
         return e[2:] if e.startswith("+ ") else e
 
     # ------------------------------------------------------------------ QCD
-    def emit_qcd(self, budgets=(None,)):
+    def emit_qcd(self, budgets=((None, None),)):
         it = self.roles.index("t")
         itb = self.roles.index("tb")
         gl = self.gluons
@@ -210,7 +226,7 @@ class Emitter:
             key = (mask, fermion)
             if key not in kvars:
                 kvars[key] = self.npar + len(kvars)  # entries 0..npar-1: external momenta
-            return f"(kt + {kvars[key]} * kts)"
+            return f"(kt + {kvars[key]} * S)"
 
         fl = {"amp": 0}
 
@@ -219,13 +235,13 @@ class Emitter:
 
         for i, r in enumerate(self.roles):
             if r in ("g_in", "g_out"):
-                body.append(f"  cx<R> x{i}[4]; ext_eps<R>((kt + {i} * kts), lam[{i}], {'true' if r == 'g_out' else 'false'}, x{i});")
+                body.append(f"  cx<R> x{i}[4]; ext_eps<R>((kt + {i} * S), lam[{i}], {'true' if r == 'g_out' else 'false'}, x{i});")
                 flop("ext_eps")
             elif r == "t":
-                body.append(f"  cx<R> x{i}[4]; ext_ubar<R>((kt + {i} * kts), mt, lam[{i}], x{i});")
+                body.append(f"  cx<R> x{i}[4]; ext_ubar<R>((kt + {i} * S), mt, lam[{i}], x{i});")
                 flop("ext_ubar")
             elif r == "tb":
-                body.append(f"  cx<R> x{i}[4]; ext_v<R>((kt + {i} * kts), mt, lam[{i}], x{i});")
+                body.append(f"  cx<R> x{i}[4]; ext_v<R>((kt + {i} * S), mt, lam[{i}], x{i});")
                 flop("ext_v")
 
         def gk(node):
@@ -270,10 +286,11 @@ class Emitter:
             body.append("    " + " ".join(ops) + " }")
 
         def emit_node(node, loc):
-            v = base_name[node]
             if loc[0] == "S":
-                decl = f"  cx<R>* {v} = ws + {loc[1]} * wss;"
+                v = f"(ws + {loc[1]} * S)"
+                decl = " "
             else:
+                v = base_name[node]
                 decl = f"  cx<R> {v}[4];"
             name[node] = v
             kind = node[0]
@@ -310,22 +327,30 @@ class Emitter:
         externals = [("EXT", i) for i in range(self.npar)]
         ext_lines = list(body)
         variants = []
-        for vi, budget in enumerate(budgets):
-            plan, nslot = allocate_storage(sched.seq, deps_of, externals, budget)
+        for vi, (budget, group) in enumerate(budgets):
+            bounds = list(range(group, len(sched.seq), group)) if group else []
+            plan, nslot = allocate_storage(sched.seq, deps_of, externals, budget, bounds)
             body[:] = list(ext_lines)
             name.clear()
             name.update(base_name)
             fl["amp"] = sum(FLOPS["ext_eps"] if r.startswith("g") else FLOPS["ext_ubar"] for r in self.roles)
             pair_count = 0
-            for (t, x), (ev, loc) in zip(sched.seq, plan):
+            groups = []
+            for k, ((t, x), (ev, loc)) in enumerate(zip(sched.seq, plan)):
+                # evictions (at a group boundary: every live register value) are written by
+                # the group that still holds the values, then the next group starts
                 for u, sl in ev:
-                    body.append(f"  cx<R>* {base_name[u]}s = ws + {sl} * wss; copy4<R>({base_name[u]}s, {name[u]});")
-                    name[u] = base_name[u] + "s"
+                    body.append(f"  copy4<R>((ws + {sl} * S), {name[u]});")
+                    name[u] = f"(ws + {sl} * S)"
+                if k in bounds:
+                    groups.append(list(body))
+                    body[:] = []
                 if t == "N":
                     emit_node(x, loc)
                 else:
                     emit_amp(sched.amps[x])
-            variants.append((budget, nslot, list(body)))
+            groups.append(list(body))
+            variants.append((budget, group, nslot, groups))
 
         den = ["  dd q[4];"]
 
@@ -352,11 +377,11 @@ class Emitter:
             den.append(f"    dt[{idx}] = mk<R>(R(re * inv), R(-im * inv)); }}")
         den.append("  // momentum table: external momenta, then the vectors the vertices use")
         den.append(f"  for (int i = 0; i < {self.npar}; ++i)")
-        den.append("    for (int m = 0; m < 4; ++m) kt[i * kts + m] = R(p[i][m]);")
+        den.append("    for (int m = 0; m < 4; ++m) kt[i * S + m] = R(p[i][m]);")
         for (mask, fermion), idx in sorted(kvars.items(), key=lambda t: t[1]):
             parts = fermion_parts(mask) if fermion else self.kin_terms(mask)
             for mu in range(4):
-                den.append(f"  kt[{idx} * kts + {mu}] = R({self._sum_expr(parts, mu)});")
+                den.append(f"  kt[{idx} * S + {mu}] = R({self._sum_expr(parts, mu)});")
         nk = self.npar + len(kvars)
 
         cs = []
@@ -377,7 +402,13 @@ class Emitter:
         ngden, ntden = max(1, len(gmask_idx)), max(1, len(tmask_idx))
         tag = self.tag
         out = [f"// Generated by paper_2312_02898_b300/gen/emit.py for '{self.process}'. Do not edit.",
-               "#pragma once", '#include "../helas.cuh"', "namespace meb300 {", f"struct proc_{tag} {{",
+               "#pragma once", '#include "../helas.cuh"', "namespace meb300 {",
+               "#if defined(__CUDACC__)",
+               f"// integer colour-matrix numerators for device code (tensor-core operand)",
+               f"static __device__ __constant__ int proc_{tag}_CFD[{ncol * ncol}] = "
+               f"{{{', '.join(str(int(x)) for x in cf.flatten())}}};",
+               "#endif",
+               f"struct proc_{tag} {{",
                f'static constexpr const char* NAME = "{self.process}";',
                f"static constexpr int NPAR = {self.npar}, NCOMB = {1 << self.npar}, NCOL = {ncol}, NDIAG = {ndiag};",
                f"static constexpr int NAMP = {len(sched.amps)}, NNODE = {len(sched.nodes)}, IDEN = {iden}, NGLUON = {n};",
@@ -386,33 +417,54 @@ class Emitter:
                f"static constexpr int MAX_LIVE = {sc.max_live(sched, it, itb)};  // currents alive at once",
                "static constexpr bool QCD = true;", "",
                f"static constexpr int NKVEC = {nk};  // momentum vectors in the per-event table",
-               "template <class R, class DG, class DT>",
+               "template <int S, class R, class DG, class DT>",
                "static HD void precompute(const double (*p)[4], double mt, double wt, int zwt, DG& dg, DT& dt,"
-               " R* kt, int kts) {"]
+               " R* kt) {"]
         out += den
         out.append("}")
-        out.append(f"// jamps variants: register budget (currents kept in registers; None = all) and")
-        out.append(f"// slots needed in the per-thread slot buffer ws (slot s at ws + s * wss)")
+        out.append("// jamps variants: register budget (currents kept in registers, -1 = all), diagram-group")
+        out.append("// size (0 = one function) and slots used in the per-thread slot buffer ws (slot s at")
+        out.append("// ws + s * S; momentum-table entry k at kt + k * S; S = threads per block * 4)")
         out.append(f"static constexpr int NVARIANT = {len(variants)};")
-        out.append("static constexpr int NSLOT[NVARIANT] = {" + ", ".join(str(v[1]) for v in variants) + "};")
-        chain = "0"
-        for vi in reversed(range(len(variants))):
-            chain = f"(V == {vi} ? {variants[vi][1]} : {chain})"
-        out.append(f"template <int V> static HD constexpr int nslot() {{ return {chain}; }}")
+        out.append("static constexpr int NSLOT[NVARIANT] = {" + ", ".join(str(v[2]) for v in variants) + "};")
         out.append("static constexpr int BUDGET[NVARIANT] = {" + ", ".join(str(-1 if v[0] is None else v[0]) for v in variants) + "};")
-        for vi, (budget, nslot, vbody) in enumerate(variants):
-            out += ["", "template <class R, class DG, class DT, class JA>",
-                    f"static HD void jamps_v{vi}(const R (*p)[4], const int* lam, R mt, const DG& dg, const DT& dt, JA& J,"
-                    f" cx<R>* ws, int wss, const R* kt, int kts) {{"]
-            out += vbody
-            out.append("}")
-        out += ["", "template <int V, class R, class DG, class DT, class JA>",
-                "static HD void jamps(const R (*p)[4], const int* lam, R mt, const DG& dg, const DT& dt, JA& J,"
-                " cx<R>* ws, int wss, const R* kt, int kts) {"]
+        out.append("static constexpr int GROUP[NVARIANT] = {" + ", ".join(str(v[1] or 0) for v in variants) + "};")
+        chain_s, chain_g = "0", "false"
+        for vi in reversed(range(len(variants))):
+            chain_s = f"(V == {vi} ? {variants[vi][2]} : {chain_s})"
+            chain_g = f"(V == {vi} ? {'true' if variants[vi][1] else 'false'} : {chain_g})"
+        out.append(f"template <int V> static HD constexpr int nslot() {{ return {chain_s}; }}")
+        out.append(f"template <int V> static HD constexpr bool grouped() {{ return {chain_g}; }}")
+        lam = (f"  int lam[{self.npar}];\n  for (int i = 0; i < {self.npar}; ++i) "
+               f"lam[i] = ((h >> ({self.npar - 1} - i)) & 1) ? 1 : -1;")
+        for vi, (budget, group, nslot, groups) in enumerate(variants):
+            if not group:
+                out += ["", "template <int S, class R, class DG, class DT, class JA>",
+                        f"static HD void jamps_v{vi}(int h, R mt, const DG& dg, const DT& dt, JA& J, cx<R>* ws,"
+                        " const R* kt) {", lam]
+                out += groups[0]
+                out.append("}")
+            else:
+                for gi, gbody in enumerate(groups):
+                    out += ["", "template <int S, class R, class DG, class DT, class JA>",
+                            f"static NOINL void jamps_v{vi}_g{gi}(int h, R mt, DG dg, DT dt, JA J, cx<R>* ws, const R* kt) {{",
+                            lam]
+                    out += gbody
+                    out.append("}")
+                out += ["", "template <int S, class R, class DG, class DT, class JA>",
+                        f"static HD void jamps_v{vi}(int h, R mt, const DG& dg, const DT& dt, JA& J, cx<R>* ws,"
+                        " const R* kt) {"]
+                for gi in range(len(groups)):
+                    out.append(f"  jamps_v{vi}_g{gi}<S, R>(h, mt, dg, dt, J, ws, kt);")
+                out.append("}")
+        out += ["", "template <int V, int S, class R, class DG, class DT, class JA>",
+                "static HD void jamps(int h, R mt, const DG& dg, const DT& dt, JA& J, cx<R>* ws, const R* kt) {"]
         for vi in range(len(variants)):
-            out.append(f"  {'if' if vi == 0 else 'else if'} constexpr (V == {vi}) "
-                       f"jamps_v{vi}<R>(p, lam, mt, dg, dt, J, ws, wss, kt, kts);")
+            out.append(f"  {'if' if vi == 0 else 'else if'} constexpr (V == {vi}) jamps_v{vi}<S, R>(h, mt, dg, dt, J, ws, kt);")
         out += ["}"]
+        out += ["#if defined(__CUDACC__)",
+                f"static __device__ int cf_device(int i) {{ return proc_{self.tag}_CFD[i]; }}",
+                "#endif"]
         out += ["", "template <class R, class JA>", "static HD R colour_sum(JA& J) {", "  R s = R(0);"]
         out += cs
         out += ["  return s;", "}", "};",
@@ -421,7 +473,7 @@ class Emitter:
         stats = dict(ndiag=ndiag, namp=len(sched.amps), nnode=len(sched.nodes), ncol=ncol, pairs=pair_count,
                      flops_amp=fl["amp"], flops_col=csflops, nden_g=ngden, nden_t=ntden, col_den=cden,
                      max_live=sc.max_live(sched, it, itb), schedule=sc.summary(sched),
-                     variants=[(b, ns) for b, ns, _ in variants])
+                     variants=[(b, g, ns) for b, g, ns, _ in variants])
         return "\n".join(out) + "\n", stats
 
     # ------------------------------------------------------------------ e+e- -> mu+mu-
@@ -435,10 +487,10 @@ class Emitter:
                f"static constexpr long FLOPS_AMP = {fa}, FLOPS_COL = 4;",
                "static constexpr bool QCD = false;",
                "// Photon and Z in the s channel.  dg[0] = 1/s;  dt[0] = 1/(s - mZ^2 + i mZ wZ).",
-               "template <class R, class DG, class DT>",
-               "static HD void precompute(const double (*p)[4], double mZ, double wZ, int, DG& dg, DT& dt, R* kt, int kts) {",
+               "template <int S, class R, class DG, class DT>",
+               "static HD void precompute(const double (*p)[4], double mZ, double wZ, int, DG& dg, DT& dt, R* kt) {",
                "  for (int i = 0; i < 4; ++i)",
-               "    for (int m = 0; m < 4; ++m) kt[i * kts + m] = R(p[i][m]);",
+               "    for (int m = 0; m < 4; ++m) kt[i * S + m] = R(p[i][m]);",
                "  double q[4];",
                "  for (int m = 0; m < 4; ++m) q[m] = p[0][m] + p[1][m];",
                "  const double s = q[0] * q[0] - q[1] * q[1] - q[2] * q[2] - q[3] * q[3];",
@@ -451,15 +503,17 @@ class Emitter:
                "static constexpr int NVARIANT = 1;",
                "static constexpr int NSLOT[1] = {0};",
                "template <int V> static HD constexpr int nslot() { return 0; }",
+               "template <int V> static HD constexpr bool grouped() { return false; }",
                "static constexpr int BUDGET[1] = {-1};",
-               "template <int V, class R, class DG, class DT, class JA>",
-               "static HD void jamps(const R (*p)[4], const int* lam, const R* zc, const DG& dg, const DT& dt, JA& J,",
-               "                     cx<R>*, int, const R* kt, int kts) {",
+               "template <int V, int S, class R, class DG, class DT, class JA>",
+               "static HD void jamps(int h, const R* zc, const DG& dg, const DT& dt, JA& J, cx<R>*, const R* kt) {",
+               "  int lam[4];",
+               "  for (int i = 0; i < 4; ++i) lam[i] = ((h >> (3 - i)) & 1) ? 1 : -1;",
                "  cx<R> x0[4], x1[4], x2[4], x3[4];",
-               "  ext_vbar<R>(kt, R(0), lam[0], x0);              // incoming e+",
-               "  ext_u<R>(kt + kts, R(0), lam[1], x1);          // incoming e-",
-               "  ext_v<R>(kt + 2 * kts, R(0), lam[2], x2);      // outgoing mu+",
-               "  ext_ubar<R>(kt + 3 * kts, R(0), lam[3], x3);   // outgoing mu-",
+               "  ext_vbar<R>(kt, R(0), lam[0], x0);            // incoming e+",
+               "  ext_u<R>(kt + S, R(0), lam[1], x1);          // incoming e-",
+               "  ext_v<R>(kt + 2 * S, R(0), lam[2], x2);      // outgoing mu+",
+               "  ext_ubar<R>(kt + 3 * S, R(0), lam[3], x3);   // outgoing mu-",
                "  cx<R> je[4], jm[4];",
                "  pair_current<R>(x0, x1, je); pair_current<R>(x3, x2, jm);",
                "  const cx<R> aa = dg[0] * mdot(je, jm);",
@@ -479,7 +533,7 @@ class Emitter:
     def emit(self):
         if self.tag == "eemumu":
             return self.emit_eemumu()
-        return self.emit_qcd(budgets=BUDGETS.get(self.tag, (None,)))
+        return self.emit_qcd(budgets=VARIANTS.get(self.tag, ((None, None),)))
 
 
 def generate_all(outdir: str, processes=None, verbose=False):

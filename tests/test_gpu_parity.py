@@ -91,6 +91,40 @@ def test_fp32_parity(process):
         assert np.mean(sc == ref["sel_col"]) > 0.99
 
 
+MIXED = [p for p in ACTIVE if p in (PROCS[3],)]
+MIXED_BOUND = 1e-5
+
+
+@pytest.mark.parametrize("process", MIXED)
+def test_mixed_parity(process):
+    """FP32 amplitudes + tensor-core colour sum (split BF16 operands, FP32 accumulation):
+    every event within the stated 1e-5 of the FP64 oracle; max and median printed."""
+    mom, a, rh, rc, ref = reference(process, NEV[process])
+    m = mk(process, "mixed")
+    for config in range(m.nconfig):
+        m.set_config(config)
+        me, sh, sc = run_gpu(m, mom, a, rh, rc)
+        rel = np.abs(me / ref["me"] - 1)
+        print(f"{process} mixed config {config}: max rel {rel.max():.3e} median {np.median(rel):.3e}")
+        assert np.isfinite(me).all()
+        assert rel.max() <= MIXED_BOUND, (config, rel.max())
+        assert np.mean(sh == ref["sel_hel"]) > 0.99
+        assert np.mean(sc == ref["sel_col"]) > 0.99
+
+
+@pytest.mark.parametrize("process", MIXED)
+def test_mixed_matches_fp32_amplitudes(process):
+    """The tensor-core colour sum agrees with the FP32 CUDA-core colour sum of the same
+    FP32 amplitudes far below the FP32 rounding level of the amplitudes themselves."""
+    mom, a, rh, rc = ps.make_batch(process, 1000, seed=17, alphas="uniform")
+    m32 = mk(process, "fp32")
+    m32.set_config(0)
+    mx = mk(process, "mixed")
+    r32 = run_gpu(m32, mom, a, rh, rc)[0]
+    rmx = run_gpu(mx, mom, a, rh, rc)[0]
+    assert np.max(np.abs(rmx / r32 - 1)) < 2e-6
+
+
 @pytest.mark.parametrize("process", ACTIVE)
 def test_helicity_filter_keeps_every_contributing_helicity(process):
     m = mk(process)
@@ -144,7 +178,7 @@ def test_edge_cases_and_errors():
     assert m.lib.me_set_config(m.handle, 99) == -1
     # a process without a tensor-core path reports ME_ERR_MODE for mixed precision
     with pytest.raises(MEError) as ei:
-        mk(PROCS[0], "mixed")
+        mk(PROCS[1], "mixed")
     assert ei.value.code == -2
 
 
@@ -187,6 +221,7 @@ def test_batch_split_invariance():
 
 FULL = [(PROCS[0], 16384, "fp64", None), (PROCS[1], 524288, "fp64", 0.118), (PROCS[2], 524288, "fp32", 0.118),
         (PROCS[3], 1048576, "fp64", "uniform"), (PROCS[3], 1048576, "fp32", "uniform"),
+        (PROCS[3], 1048576, "mixed", "uniform"),
         (PROCS[4], 262144, "fp32", 0.118)]
 
 
@@ -205,5 +240,5 @@ def test_full_size_sampled(process, nevt, precision, alphas):
     idx = np.unique(np.concatenate([idx, [0, nevt - 1]]))
     ref = oracle.me(process, mom[idx], alphas=None if a is None else a[idx], rnd_hel=rh[idx], rnd_col=rc[idx])
     rel = np.abs(me[idx] / ref["me"] - 1)
-    assert rel.max() <= (1e-12 if precision == "fp64" else FP32_BOUND)
+    assert rel.max() <= {"fp64": 1e-12, "fp32": FP32_BOUND, "mixed": MIXED_BOUND}[precision]
     assert np.mean(sh[idx] == ref["sel_hel"]) >= 0.95
