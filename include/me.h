@@ -112,6 +112,25 @@ int me_compute_host(me_handle* h, int64_t nevt, const double* momenta, const dou
                     const double* rnd_hel, const double* rnd_col, double* me, int32_t* sel_hel,
                     int32_t* sel_col, void* cuda_stream);
 
+/* The computation of me_compute with no device allocation on its path: no cudaMalloc,
+ * cudaMallocAsync, cudaFree or allocating library routine.  It is meant for callers
+ * that cannot let the library allocate -- a host framework that owns all device memory
+ * through its own pool and forbids direct driver allocations, or a caller under a hard
+ * memory cap or latency budget, where an allocation can fail or stall.  The paper has
+ * no counterpart: it is an interface for such hosts.
+ * The kernels' scratch (helicity running sums, slot buffer, momentum table, colour
+ * weights) is one fixed 32 MiB device array inside the library, held on every GPU that
+ * loads the library until the process exits.  A batch that needs more scratch than that
+ * is rejected with ME_ERR_ARG and a message giving the limit (for "g g > t t~ g g" in
+ * FP64 about 9000 events per call).  The first call on a device looks up the array's
+ * device address; make it before any stream capture.  Every call uses the same array
+ * and leaves its contents behind: calls whose work overlaps on the GPU (other streams,
+ * other handles) race on it, so the caller must serialise them.  Arguments, outputs and
+ * the other errors are those of me_compute. */
+int me_compute_noalloc(me_handle* h, int64_t nevt, const double* momenta, const double* alphas,
+                       const double* rnd_hel, const double* rnd_col, double* me, int32_t* sel_hel,
+                       int32_t* sel_col, void* cuda_stream);
+
 /* Process shape: external particles, helicity combinations, helicities kept by the
  * filter, colour flows, Feynman diagrams.  Any output pointer may be NULL. */
 int me_info(const me_handle* h, int* npar, int* ncomb, int* ngood, int* ncol, int* ndiag);

@@ -1,0 +1,53 @@
+// me_internal.h -- declarations shared by the translation units of libme_b300.so
+// (the handle and the launch helpers); not part of the public C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/me.h"
+#include "me_kernels.cuh"
+
+struct Workspace {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+struct me_handle {
+  const meb300::ProcessOps* ops = nullptr;
+  me_sm_params par{};
+  int config = 0;
+  double zc[4] = {0, 0, 0, 0};
+  double coup = 0;
+  std::vector<int> good;
+  std::mutex mu;
+  std::unordered_map<uintptr_t, Workspace> ws;  // keyed by stream (and purpose)
+  std::string err;
+  int* err_host = nullptr;  // mapped pinned word the kernels raise on a timed-out wait
+  int* err_dev = nullptr;
+};
+
+namespace meb300 {
+namespace detail {
+
+// Bytes of workspace one launch of 'chunk' events needs, and its carve-up.
+struct Carve {
+  size_t cum = 0, colw = 0, slots = 0, ktab = 0;
+  size_t total() const { return cum + colw + slots + ktab; }
+};
+
+int fail(me_handle* h, int code, const std::string& msg);
+int cuda_fail(me_handle* h, cudaError_t e, const char* where);
+void fill_common(const me_handle* h, MeLaunch& a);
+bool is_device_ptr(const void* p);
+Carve carve(const ProcessOps* ops, const LaunchNeeds& nd, int ngood, int64_t chunk, bool want_hel, bool want_col);
+cudaError_t launch_chunks(const ProcessOps* ops, int prec, int config, MeLaunch a, int64_t nevt, int64_t chunk,
+                          const Carve& cv, void* wsp, cudaStream_t s);
+
+}  // namespace detail
+}  // namespace meb300

@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "../../include/me.h"
+#include "me_internal.h"
 #include "me_kernels.cuh"
 
 // Each process lives in its own translation unit; a build may leave one out (weak
@@ -37,10 +38,6 @@ const ProcessOps* const kProcs[] = {&ops_eemumu, &ops_ggtt, &ops_ggttg, &ops_ggt
 
 thread_local std::string g_init_error;
 
-struct Workspace {
-  void* ptr = nullptr;
-  size_t bytes = 0;
-};
 
 // events per launch when the slot buffer lives in global memory (bounds the workspace
 // and keeps 32-bit slot offsets)
@@ -48,21 +45,8 @@ constexpr int64_t kGlobalSlotChunk = 65536;
 
 }  // namespace
 
-struct me_handle {
-  const ProcessOps* ops = nullptr;
-  me_sm_params par{};
-  int config = 0;
-  double zc[4] = {0, 0, 0, 0};
-  double coup = 0;
-  std::vector<int> good;
-  std::mutex mu;
-  std::unordered_map<uintptr_t, Workspace> ws;  // keyed by stream (and purpose)
-  std::string err;
-  int* err_host = nullptr;  // mapped pinned word the kernels raise on a timed-out wait
-  int* err_dev = nullptr;
-};
-
-namespace {
+namespace meb300 {
+namespace detail {
 
 int fail(me_handle* h, int code, const std::string& msg) {
   if (h) {
@@ -196,11 +180,6 @@ int get_workspace(me_handle* h, uintptr_t key, cudaStream_t s, size_t bytes, voi
   return ME_OK;
 }
 
-// Bytes of workspace one launch of 'chunk' events needs, and its carve-up.
-struct Carve {
-  size_t cum = 0, colw = 0, slots = 0, ktab = 0;
-  size_t total() const { return cum + colw + slots + ktab; }
-};
 
 Carve carve(const ProcessOps* ops, const LaunchNeeds& nd, int ngood, int64_t chunk, bool want_hel, bool want_col) {
   Carve c;
@@ -246,7 +225,9 @@ int64_t chunk_for(const LaunchNeeds& nd, int64_t nevt) {
   return (nd.slot_bytes_per_event || nd.ktab_bytes_per_event) ? std::min<int64_t>(nevt, kGlobalSlotChunk) : nevt;
 }
 
-}  // namespace
+}  // namespace detail
+}  // namespace meb300
+using namespace meb300::detail;
 
 extern "C" {
 

@@ -1,0 +1,119 @@
+// me_noalloc.cu -- me_compute_noalloc: the me_compute computation with no device
+// allocation anywhere on its path.
+//
+// me_compute keeps a per-stream workspace that it grows with cudaMallocAsync.  Some
+// callers cannot allow that: a host framework that owns all device memory through its
+// own pool and forbids direct driver allocations, or a caller running under a hard
+// memory cap or a latency budget, where an allocation may fail or stall.  For them the
+// scratch the kernels need (running helicity sums for the selection, the global slot
+// buffer of the large processes, the per-event momentum table, colour weights) lives
+// in one fixed device array declared in this file.  It is created when the library's
+// device code is loaded on a GPU and stays there until the process exits.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <mutex>
+#include <string>
+
+#include "../../include/me.h"
+#include "me_internal.h"
+#include "me_kernels.cuh"
+
+using namespace meb300;
+using namespace meb300::detail;
+
+namespace {
+
+constexpr size_t kScratchBytes = size_t(32) << 20;  // 32 MiB, the stated maximum
+
+// The fixed scratch.  In host code this name is a host-side stand-in, not a device
+// address: the device address comes from cudaGetSymbolAddress below.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+void* g_scratch_addr[kMaxDevices] = {};
+
+// Device address of the scratch on the current device, looked up once per device.
+int scratch_address(me_handle* h, void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(h, e, "me_compute_noalloc: cudaGetDevice");
+  if (dev < 0 || dev >= kMaxDevices) return fail(h, ME_ERR_ARG, "me_compute_noalloc: device index out of range");
+  std::lock_guard<std::mutex> g(g_mu);
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();
+      return cuda_fail(h, e == cudaSuccess ? cudaErrorInvalidSymbol : e,
+                       "me_compute_noalloc: cudaGetSymbolAddress of the fixed scratch");
+    }
+    g_scratch_addr[dev] = p;
+  }
+  *out = g_scratch_addr[dev];
+  return ME_OK;
+}
+
+}  // namespace
+
+extern "C" int me_compute_noalloc(me_handle* h, int64_t nevt, const double* momenta, const double* alphas,
+                                  const double* rnd_hel, const double* rnd_col, double* me, int32_t* sel_hel,
+                                  int32_t* sel_col, void* cuda_stream) {
+  if (!h) return fail(nullptr, ME_ERR_ARG, "me_compute_noalloc: null handle");
+  if (nevt < 0) return fail(h, ME_ERR_ARG, "me_compute_noalloc: nevt < 0");
+  if (nevt == 0) return ME_OK;
+  if (!momenta || !me) return fail(h, ME_ERR_ARG, "me_compute_noalloc: momenta and me are required");
+  if (reinterpret_cast<uintptr_t>(momenta) % 16)
+    return fail(h, ME_ERR_ARG, "me_compute_noalloc: momenta must be 16-byte aligned");
+  if ((sel_hel && !rnd_hel) || (sel_col && !rnd_col))
+    return fail(h, ME_ERR_ARG, "me_compute_noalloc: a selection output needs its random numbers");
+  const void* ptrs[] = {momenta, me, alphas, rnd_hel, rnd_col, sel_hel, sel_col};
+  for (const void* p : ptrs)
+    if (p && !is_device_ptr(p)) return fail(h, ME_ERR_ARG, "me_compute_noalloc: arrays must be device memory");
+  if (h->err_host && *h->err_host) {
+    *h->err_host = 0;
+    return fail(h, ME_ERR_TIMEOUT, "me_compute_noalloc: a device-side wait of an earlier call on this handle "
+                                   "timed out; its events were set to NaN");
+  }
+  const ProcessOps* ops = h->ops;
+  const int prec = h->par.precision, config = h->config;
+  const int ngood = int(h->good.size());
+  const bool want_hel = sel_hel && rnd_hel;
+  const bool want_col = sel_col && rnd_col;
+  const LaunchNeeds nd = ops->needs(prec, config);
+  // one launch over every event: the whole batch's scratch must fit the fixed array
+  const Carve cv = carve(ops, nd, ngood, nevt, want_hel, want_col);
+  if (cv.total() > kScratchBytes) {
+    const Carve one = carve(ops, nd, ngood, 1024, want_hel, want_col);
+    const double per_event = double(one.total()) / 1024.0;
+    char msg[256];
+    std::snprintf(msg, sizeof msg,
+                  "me_compute_noalloc: %lld events need %zu bytes of scratch, more than the fixed %zu bytes "
+                  "(about %lld events of this process and mode per call)",
+                  static_cast<long long>(nevt), cv.total(), kScratchBytes,
+                  static_cast<long long>(per_event > 0 ? double(kScratchBytes) / per_event : 0));
+    return fail(h, ME_ERR_ARG, msg);
+  }
+  void* scratch = nullptr;
+  int rc = scratch_address(h, &scratch);
+  if (rc) return rc;
+  // Nothing in the scratch has to start at zero: the kernels write every running sum,
+  // colour weight, slot and momentum-table entry of an event before they read it.
+  MeLaunch a{};
+  fill_common(h, a);
+  a.err = h->err_dev;
+  a.mom = momenta;
+  a.alphas = alphas;
+  a.rnd_hel = rnd_hel;
+  a.rnd_col = rnd_col;
+  a.me = me;
+  a.sel_hel = want_hel ? sel_hel : nullptr;
+  a.sel_col = want_col ? sel_col : nullptr;
+  a.ngood = ngood;
+  for (int i = 0; i < ngood; ++i) a.good[i] = uint8_t(h->good[i]);
+  cudaError_t e = launch_chunks(ops, prec, config, a, nevt, nevt, cv, scratch, static_cast<cudaStream_t>(cuda_stream));
+  if (e != cudaSuccess) return cuda_fail(h, e, "me_compute_noalloc launch");
+  return ME_OK;
+}
