@@ -73,10 +73,14 @@ typedef struct {
   int precision;            /* ME_PREC_* */
   int zero_width_tchan;     /* 1: no width in t-channel propagators (those that separate
                                the two incoming particles); Section 3, Tables 1-2 */
+  double rescue_kappa;      /* FP32 and mixed modes: an event whose conditioning
+                               kappa = max over gluon propagators of (sum of energies)^2/|K^2|
+                               exceeds this is re-evaluated in FP64 (0 = never); nearly
+                               collinear gluons make FP32 amplitudes lose digits */
 } me_sm_params;
 
 /* Fill p with the defaults: mZ 91.188, wZ 2.4414, mt 173, wt 1.4915, 1/alpha 132.5,
- * G_F 1.16639e-5, alpha_s 0.118, FP64, widths everywhere. */
+ * G_F 1.16639e-5, alpha_s 0.118, FP64, widths everywhere, rescue_kappa 2000. */
 void me_default_params(me_sm_params* p);
 
 /* Create a handle for one process on the current CUDA device.  Runs the helicity
@@ -96,8 +100,10 @@ int me_init(const char* process, const me_sm_params* p, me_handle** out);
  *   sel_hel  device, int32 [nevt] or NULL             (output)
  *   sel_col  device, int32 [nevt] or NULL             (output)
  * nevt == 0 is a no-op.  The handle keeps one workspace per stream (grown on demand,
- * stream-ordered); make one call at the largest size before capturing a stream into a
- * CUDA graph.  Calls on different streams may run concurrently.
+ * stream-ordered); before capturing calls on a stream into a CUDA graph, size that
+ * stream's workspace for the largest call with me_reserve (a later call that needs more
+ * would move the workspace under the graph).  Calls on different streams may run
+ * concurrently.
  * Errors: ME_ERR_ARG (null handle/momenta/me, nevt < 0, a host pointer, misaligned
  * momenta), ME_ERR_NOMEM, ME_ERR_CUDA, ME_ERR_TIMEOUT. */
 int me_compute(me_handle* h, int64_t nevt, const double* momenta, const double* alphas,
@@ -146,6 +152,12 @@ int me_flops(const me_handle* h, int64_t* flops_amp_per_hel, int64_t* flops_col_
  * and the bytes of stream workspace it needs (with both selection outputs requested).
  * Either output pointer may be NULL. */
 int me_plan(const me_handle* h, int64_t nevt, int64_t* launches, int64_t* workspace_bytes);
+
+/* Grow the handle's workspace on cuda_stream to what a me_compute call of nevt events
+ * with both selection outputs needs under the current configuration, so that calls up
+ * to that size on that stream allocate nothing (stream-ordered allocation on
+ * cuda_stream).  Errors: ME_ERR_ARG (null handle, nevt < 0), ME_ERR_NOMEM, ME_ERR_CUDA. */
+int me_reserve(me_handle* h, int64_t nevt, void* cuda_stream);
 
 /* Select the kernel launch configuration (register budget, block size, placement of
  * per-thread arrays) used by later me_compute calls; 0 is the default.  Returns the

@@ -27,7 +27,12 @@ CFLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptx
 
 
 def _deps(cu):
-    deps = [cu, os.path.join(INCLUDE, "me.h")] + glob.glob(os.path.join(CSRC, "*.cuh"))
+    deps = [cu] + glob.glob(os.path.join(CSRC, "*.cuh"))
+    src = open(cu).read()
+    if "me.h" in src or "me_internal.h" in src:
+        deps += [os.path.join(INCLUDE, "me.h"), os.path.join(CSRC, "me_internal.h")]
+    if "me_probe.h" in src:
+        deps.append(os.path.join(INCLUDE, "me_probe.h"))
     tag = os.path.basename(cu)[:-3]
     if tag.startswith("proc_"):
         deps.append(os.path.join(GEN, tag + ".cuh"))

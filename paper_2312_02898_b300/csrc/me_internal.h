@@ -41,6 +41,19 @@ struct Carve {
   size_t total() const { return cum + colw + slots + ktab; }
 };
 
+// A me_compute call: the main pass (in chunks when the slot buffer is global), the
+// rescue list of ill-conditioned events (FP32 and mixed modes) and the FP64 pass over
+// that list, and where each lives in the call's workspace.
+struct CallPlan {
+  int prec = 0, config = 0;
+  int64_t chunk = 0;
+  Carve main;
+  bool rescue = false;
+  int rescue_cap = 0, rescue_grid = 0;
+  size_t off_count = 0, off_list = 0, off_cum = 0, off_colw = 0, off_slots = 0, off_ktab = 0;
+  size_t total = 0;
+};
+
 int fail(me_handle* h, int code, const std::string& msg);
 int cuda_fail(me_handle* h, cudaError_t e, const char* where);
 void fill_common(const me_handle* h, MeLaunch& a);
@@ -48,6 +61,8 @@ bool is_device_ptr(const void* p);
 Carve carve(const ProcessOps* ops, const LaunchNeeds& nd, int ngood, int64_t chunk, bool want_hel, bool want_col);
 cudaError_t launch_chunks(const ProcessOps* ops, int prec, int config, MeLaunch a, int64_t nevt, int64_t chunk,
                           const Carve& cv, void* wsp, cudaStream_t s);
+CallPlan plan_call(const me_handle* h, int64_t nevt, int64_t chunk, bool want_hel, bool want_col);
+cudaError_t run_call(const me_handle* h, const CallPlan& cp, const MeLaunch& a, int64_t nevt, void* wsp, cudaStream_t s);
 
 }  // namespace detail
 }  // namespace meb300

@@ -39,18 +39,18 @@ __global__ void __launch_bounds__(128) me_kernel_mixed(const MeLaunch a) {
   constexpr int BLOCK = 128;
   static_assert(L::BLOCK == 128, "one block is the 128-row tile of the MMA");
   static_assert(L::den_smem && L::j_smem && L::w_mode == 1, "mixed kernel expects J and weights in shared memory");
-  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_mixed[];  // 16 B suffices for the descriptors
   const int tid = threadIdx.x, warp = tid >> 5;
   const int64_t nevt = a.nevt;
   const int64_t ievt_raw = int64_t(blockIdx.x) * BLOCK + tid;
   const bool active = ievt_raw < nevt;
   const int64_t ievt = active ? ievt_raw : nevt - 1;
 
-  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(smem_raw);
-  uint64_t* s_mbar = reinterpret_cast<uint64_t*>(smem_raw + 16);
-  unsigned char* s_B = smem_raw + S::HEAD;
+  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(smem_mixed);
+  uint64_t* s_mbar = reinterpret_cast<uint64_t*>(smem_mixed + 16);
+  unsigned char* s_B = smem_mixed + S::HEAD;
   unsigned char* s_A = s_B + S::BBYTES;
-  unsigned char* sp = smem_raw + S::TC_BYTES;
+  unsigned char* sp = smem_mixed + S::TC_BYTES;
 
   // --- tensor-core set-up: barrier, TMEM columns, the colour matrix as operand B
   if (tid == 0) tc::mbar_init(s_mbar, 1);
@@ -96,7 +96,11 @@ __global__ void __launch_bounds__(128) me_kernel_mixed(const MeLaunch a) {
   else kt = static_cast<R*>(a.ktab) + (size_t(blockIdx.x) * P::NKVEC * BLOCK + tid) * 4;
   Strided<R, BLOCK> v_dg{s_dg + tid};
   Strided<cx<R>, BLOCK> v_dt{s_dt + tid};
-  P::template precompute<BLOCK * 4, R>(pd, a.mt, a.wt, a.zwt, v_dg, v_dt, kt);
+  const double kappa = P::template precompute<BLOCK * 4, R>(pd, a.mt, a.wt, a.zwt, v_dg, v_dt, kt);
+  if (active && a.rescue_list && kappa > a.rescue_kappa) {
+    const int slot = atomicAdd(a.rescue_count, 1);
+    if (slot < a.rescue_cap) a.rescue_list[slot] = int(a.ibase + ievt);
+  }
   const double as = a.alphas ? a.alphas[ievt] : a.alphas_default;
   const double g2 = 4.0 * 3.14159265358979323846 * as;
   double gp = 1.0;

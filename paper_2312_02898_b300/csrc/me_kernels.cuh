@@ -49,6 +49,21 @@ struct MeLaunch {
   void* slots;       // workspace [block][nslot][BLOCK][4] complex (slot buffer in global memory)
   void* ktab;        // workspace [block][nkvec][BLOCK][4] real (momentum table in global memory)
   int* err;          // set to 1 when a bounded device-side wait runs out (mapped host memory)
+  // precision rescue (FP32 and mixed passes): events whose conditioning kappa exceeds
+  // rescue_kappa are appended, as ibase + local index, to rescue_list (capacity
+  // rescue_cap, counter rescue_count) for a later FP64 pass
+  double rescue_kappa;
+  int* rescue_count;
+  int* rescue_list;
+  int rescue_cap;
+  int64_t ibase;
+  // indexed mode (the FP64 rescue pass): process events index[0 .. *index_count) in a
+  // grid-stride loop over grid_blocks blocks; workspace rows (cum, colw) are the
+  // positions in the list, with row stride index_cap
+  const int* index;
+  const int* index_count;
+  int index_cap;
+  int grid_blocks;
 };
 
 // view of an array laid out [index][S]
@@ -146,8 +161,14 @@ __global__ void __launch_bounds__(L::BLOCK) me_kernel(const MeLaunch a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int tid = threadIdx.x;
   const int64_t nevt = a.nevt;
-  const int64_t ievt = int64_t(blockIdx.x) * BLOCK + tid;
-  if (ievt >= nevt) return;  // no block-wide barrier below
+  const int64_t count = a.index ? int64_t(*a.index_count < a.index_cap ? *a.index_count : a.index_cap) : nevt;
+  const int64_t step = a.index ? int64_t(gridDim.x) * BLOCK : nevt;
+  // one event per thread, or a grid-stride walk over an index list (no block-wide
+  // barrier below, so threads leave independently)
+  for (int64_t pos = int64_t(blockIdx.x) * BLOCK + tid; pos < count; pos += step) {
+  const int64_t ievt = a.index ? int64_t(a.index[pos]) : pos;
+  const int64_t wrow = a.index ? pos : ievt;              // workspace row
+  const int64_t wstride = a.index ? int64_t(a.index_cap) : nevt;
 
   // 1. momenta
   double pd[P::NPAR][4];
@@ -196,10 +217,10 @@ __global__ void __launch_bounds__(L::BLOCK) me_kernel(const MeLaunch a) {
   cx<R> r_dt[L::den_smem ? 1 : P::NDEN_T];
   Strided<R, BLOCK> v_dg{s_dg + tid};
   Strided<cx<R>, BLOCK> v_dt{s_dt + tid};
-  double gfac;
+  double gfac, kappa;
   if constexpr (P::QCD) {
-    if constexpr (L::den_smem) P::template precompute<BLOCK * 4, R>(pd, a.mt, a.wt, a.zwt, v_dg, v_dt, kt);
-    else P::template precompute<BLOCK * 4, R>(pd, a.mt, a.wt, a.zwt, r_dg, r_dt, kt);
+    if constexpr (L::den_smem) kappa = P::template precompute<BLOCK * 4, R>(pd, a.mt, a.wt, a.zwt, v_dg, v_dt, kt);
+    else kappa = P::template precompute<BLOCK * 4, R>(pd, a.mt, a.wt, a.zwt, r_dg, r_dt, kt);
     const double as = a.alphas ? a.alphas[ievt] : a.alphas_default;
     const double g2 = 4.0 * 3.14159265358979323846 * as;
     double gp = 1.0;
@@ -207,9 +228,13 @@ __global__ void __launch_bounds__(L::BLOCK) me_kernel(const MeLaunch a) {
     for (int k = 0; k < P::NGLUON; ++k) gp *= g2;
     gfac = gp / double(P::COL_DEN);
   } else {
-    if constexpr (L::den_smem) P::template precompute<BLOCK * 4, R>(pd, a.zc[2], a.zc[3], 0, v_dg, v_dt, kt);
-    else P::template precompute<BLOCK * 4, R>(pd, a.zc[2], a.zc[3], 0, r_dg, r_dt, kt);
+    if constexpr (L::den_smem) kappa = P::template precompute<BLOCK * 4, R>(pd, a.zc[2], a.zc[3], 0, v_dg, v_dt, kt);
+    else kappa = P::template precompute<BLOCK * 4, R>(pd, a.zc[2], a.zc[3], 0, r_dg, r_dt, kt);
     gfac = a.coup / double(P::COL_DEN);
+  }
+  if (a.rescue_list && kappa > a.rescue_kappa) {
+    const int slot = atomicAdd(a.rescue_count, 1);
+    if (slot < a.rescue_cap) a.rescue_list[slot] = int(a.ibase + ievt);
   }
 
   // colour weights
@@ -223,7 +248,7 @@ __global__ void __launch_bounds__(L::BLOCK) me_kernel(const MeLaunch a) {
     } else if constexpr (L::w_mode == 1) {
       for (int c = 0; c < P::NCOL; ++c) v_w[c] = R(0);
     } else {
-      for (int c = 0; c < P::NCOL; ++c) a.colw[c * nevt + ievt] = 0.0;
+      for (int c = 0; c < P::NCOL; ++c) a.colw[c * wstride + wrow] = 0.0;
     }
   }
 
@@ -235,7 +260,7 @@ __global__ void __launch_bounds__(L::BLOCK) me_kernel(const MeLaunch a) {
     R cs;
     if constexpr (P::QCD && L::den_smem && L::w_mode != 0) {
       cs = one_helicity<P, R, L>(h, R(a.mt), s_dg + tid, s_dt + tid, L::j_smem ? s_J + tid : nullptr,
-                                 L::w_mode == 1 ? s_w + tid : nullptr, a.colw ? a.colw + ievt : nullptr, nevt,
+                                 L::w_mode == 1 ? s_w + tid : nullptr, a.colw ? a.colw + wrow : nullptr, wstride,
                                  ws, kt, want_w);
     } else if constexpr (L::j_smem) {
       Strided<cx<R>, BLOCK> J{s_J + tid};
@@ -249,7 +274,7 @@ __global__ void __launch_bounds__(L::BLOCK) me_kernel(const MeLaunch a) {
           const R m2 = z.r * z.r + z.i * z.i;
           if constexpr (L::w_mode == 0) r_w[c] += m2;
           else if constexpr (L::w_mode == 1) v_w[c] += m2;
-          else a.colw[c * nevt + ievt] += double(m2);
+          else a.colw[c * wstride + wrow] += double(m2);
         }
       }
     } else {
@@ -265,13 +290,13 @@ __global__ void __launch_bounds__(L::BLOCK) me_kernel(const MeLaunch a) {
           const R m2 = J[c].r * J[c].r + J[c].i * J[c].i;
           if constexpr (L::w_mode == 0) r_w[c] += m2;
           else if constexpr (L::w_mode == 1) v_w[c] += m2;
-          else a.colw[c * nevt + ievt] += double(m2);
+          else a.colw[c * wstride + wrow] += double(m2);
         }
       }
     }
     const double mh = double(cs) * gfac;
     total += mh;
-    if (a.cum) a.cum[ih * nevt + ievt] = a.cum_mode ? mh : total;
+    if (a.cum) a.cum[ih * wstride + wrow] = a.cum_mode ? mh : total;
   }
 
   // 4. outputs
@@ -283,7 +308,7 @@ __global__ void __launch_bounds__(L::BLOCK) me_kernel(const MeLaunch a) {
       int found = -1, lastnz = -1;
       double prev = 0.0;
       for (int ih = 0; ih < a.ngood; ++ih) {
-        const double c = a.cum[ih * nevt + ievt];
+        const double c = a.cum[ih * wstride + wrow];
         if (c > prev) lastnz = ih;
         if (c > target) { found = ih; break; }
         prev = c;
@@ -300,7 +325,7 @@ __global__ void __launch_bounds__(L::BLOCK) me_kernel(const MeLaunch a) {
       for (int c = 0; c < P::NCOL; ++c) {
         if constexpr (L::w_mode == 0) wt_tot += double(r_w[c]);
         else if constexpr (L::w_mode == 1) wt_tot += double(v_w[c]);
-        else wt_tot += a.colw[c * nevt + ievt];
+        else wt_tot += a.colw[c * wstride + wrow];
       }
       if (wt_tot > 0.0) {
         const double target = a.rnd_col[ievt] * wt_tot;
@@ -310,7 +335,7 @@ __global__ void __launch_bounds__(L::BLOCK) me_kernel(const MeLaunch a) {
           double w;
           if constexpr (L::w_mode == 0) w = double(r_w[c]);
           else if constexpr (L::w_mode == 1) w = double(v_w[c]);
-          else w = a.colw[c * nevt + ievt];
+          else w = a.colw[c * wstride + wrow];
           run += w;
           if (w > 0.0) lastnz = c;
           if (run > target) { found = c; break; }
@@ -320,6 +345,7 @@ __global__ void __launch_bounds__(L::BLOCK) me_kernel(const MeLaunch a) {
     }
     a.sel_col[ievt] = sel;
   }
+  }  // event loop
 }
 
 // ---------------------------------------------------------------------------
@@ -362,7 +388,7 @@ cudaError_t launch_me(const MeLaunch& a, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
   }
-  const int64_t nblk = (a.nevt + L::BLOCK - 1) / L::BLOCK;
+  const int64_t nblk = a.grid_blocks > 0 ? a.grid_blocks : (a.nevt + L::BLOCK - 1) / L::BLOCK;
   k<<<dim3(unsigned(nblk)), dim3(L::BLOCK), smem, s>>>(a);
   return cudaGetLastError();
 }

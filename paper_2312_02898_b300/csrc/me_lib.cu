@@ -215,6 +215,7 @@ cudaError_t launch_chunks(const ProcessOps* ops, int prec, int config, MeLaunch 
     b.colw = colw;
     b.slots = slots;
     b.ktab = ktab;
+    b.ibase = off;
     cudaError_t e = ops->launch(prec, config, b, s);
     if (e != cudaSuccess) return e;
   }
@@ -223,6 +224,67 @@ cudaError_t launch_chunks(const ProcessOps* ops, int prec, int config, MeLaunch 
 
 int64_t chunk_for(const LaunchNeeds& nd, int64_t nevt) {
   return (nd.slot_bytes_per_event || nd.ktab_bytes_per_event) ? std::min<int64_t>(nevt, kGlobalSlotChunk) : nevt;
+}
+
+static size_t up256(size_t b) { return (b + 255) / 256 * 256; }
+
+CallPlan plan_call(const me_handle* h, int64_t nevt, int64_t chunk, bool want_hel, bool want_col) {
+  const ProcessOps* ops = h->ops;
+  CallPlan cp;
+  cp.prec = h->par.precision;
+  cp.config = h->config;
+  cp.chunk = chunk;
+  const int ngood = int(h->good.size());
+  const LaunchNeeds nd = ops->needs(cp.prec, cp.config);
+  cp.main = carve(ops, nd, ngood, chunk, want_hel, want_col);
+  size_t off = cp.main.total();
+  cp.rescue = (cp.prec == ME_PREC_FP32 || cp.prec == ME_PREC_MIXED) && h->par.rescue_kappa > 0;
+  if (cp.rescue) {
+    const LaunchNeeds n64 = ops->needs(ME_PREC_FP64, 0);
+    const int64_t cap = std::min<int64_t>(nevt, std::max<int64_t>(1024, nevt / 16));
+    cp.rescue_cap = int(cap);
+    cp.rescue_grid = int(std::min<int64_t>((cap + n64.block - 1) / n64.block, 1184));
+    const size_t tile_events = size_t(cp.rescue_grid) * n64.block;
+    cp.off_count = off; off += 256;
+    cp.off_list = off; off += up256(size_t(cap) * sizeof(int));
+    cp.off_cum = off; if (want_hel) off += up256(size_t(ngood) * cap * sizeof(double));
+    cp.off_colw = off; if (want_col && n64.colw_global) off += up256(size_t(ops->ncol) * cap * sizeof(double));
+    cp.off_slots = off; off += up256(n64.slot_bytes_per_event * tile_events);
+    cp.off_ktab = off; off += up256(n64.ktab_bytes_per_event * tile_events);
+  }
+  cp.total = off;
+  return cp;
+}
+
+cudaError_t run_call(const me_handle* h, const CallPlan& cp, const MeLaunch& a0, int64_t nevt, void* wsp,
+                     cudaStream_t s) {
+  const ProcessOps* ops = h->ops;
+  char* w = static_cast<char*>(wsp);
+  MeLaunch a = a0;
+  if (cp.rescue) {
+    cudaError_t e = cudaMemsetAsync(w + cp.off_count, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    a.rescue_kappa = h->par.rescue_kappa;
+    a.rescue_count = reinterpret_cast<int*>(w + cp.off_count);
+    a.rescue_list = reinterpret_cast<int*>(w + cp.off_list);
+    a.rescue_cap = cp.rescue_cap;
+  }
+  cudaError_t e = launch_chunks(ops, cp.prec, cp.config, a, nevt, cp.chunk, cp.main, wsp, s);
+  if (e != cudaSuccess || !cp.rescue) return e;
+  // FP64 pass over the flagged events, in place: same inputs and outputs, workspace
+  // rows indexed by list position
+  MeLaunch b = a0;
+  const bool want_col = a0.sel_col != nullptr;
+  b.nevt = nevt;
+  b.cum = a0.sel_hel ? reinterpret_cast<double*>(w + cp.off_cum) : nullptr;
+  b.colw = (want_col && ops->needs(ME_PREC_FP64, 0).colw_global) ? reinterpret_cast<double*>(w + cp.off_colw) : nullptr;
+  b.slots = w + cp.off_slots;
+  b.ktab = w + cp.off_ktab;
+  b.index = reinterpret_cast<const int*>(w + cp.off_list);
+  b.index_count = reinterpret_cast<const int*>(w + cp.off_count);
+  b.index_cap = cp.rescue_cap;
+  b.grid_blocks = cp.rescue_grid;
+  return ops->launch(ME_PREC_FP64, 0, b, s);
 }
 
 }  // namespace detail
@@ -242,6 +304,7 @@ void me_default_params(me_sm_params* p) {
   p->alphas_default = 0.118;
   p->precision = ME_PREC_FP64;
   p->zero_width_tchan = 0;
+  p->rescue_kappa = 2000.0;
 }
 
 int me_init(const char* process, const me_sm_params* p, me_handle** out) {
@@ -251,7 +314,8 @@ int me_init(const char* process, const me_sm_params* p, me_handle** out) {
   for (const ProcessOps* o : kProcs)
     if (o && std::strcmp(o->name, process) == 0) ops = o;
   if (!ops) return fail(nullptr, ME_ERR_ARG, std::string("me_init: unknown process '") + process + "'");
-  if (!(p->mZ > 0 && p->wZ >= 0 && p->mt > 0 && p->wt >= 0 && p->aEWM1 > 0 && p->Gf > 0 && p->alphas_default > 0))
+  if (!(p->mZ > 0 && p->wZ >= 0 && p->mt > 0 && p->wt >= 0 && p->aEWM1 > 0 && p->Gf > 0 && p->alphas_default > 0 &&
+        p->rescue_kappa >= 0))
     return fail(nullptr, ME_ERR_ARG, "me_init: parameters must be positive (widths non-negative)");
   if (p->precision < 0 || p->precision > 2) return fail(nullptr, ME_ERR_ARG, "me_init: unknown precision mode");
   if (p->precision == ME_PREC_MIXED && !ops->has_mixed)
@@ -332,23 +396,21 @@ int me_init(const char* process, const me_sm_params* p, me_handle** out) {
 static int compute_device(me_handle* h, int64_t nevt, const double* momenta, const double* alphas,
                           const double* rnd_hel, const double* rnd_col, double* me, int32_t* sel_hel,
                           int32_t* sel_col, cudaStream_t s) {
-  const ProcessOps* ops = h->ops;
-  const int prec = h->par.precision, config = h->config;
-  const int ngood = int(h->good.size());
-  const bool want_hel = sel_hel && rnd_hel;
-  const bool want_col = sel_col && rnd_col;
-  const LaunchNeeds nd = ops->needs(prec, config);
-  const int64_t chunk = chunk_for(nd, nevt);
-  const Carve cv = carve(ops, nd, ngood, chunk, want_hel, want_col);
-  void* wsp = nullptr;
-  if (cv.total()) {
-    int rc = get_workspace(h, reinterpret_cast<uintptr_t>(s) << 1, s, cv.total(), &wsp);
-    if (rc) return rc;
-  }
   if (h->err_host && *h->err_host) {
     *h->err_host = 0;
     return fail(h, ME_ERR_TIMEOUT, "me_compute: a device-side wait of an earlier call on this handle timed out; "
                                    "its events were set to NaN");
+  }
+  const ProcessOps* ops = h->ops;
+  const int ngood = int(h->good.size());
+  const bool want_hel = sel_hel && rnd_hel;
+  const bool want_col = sel_col && rnd_col;
+  const LaunchNeeds nd = ops->needs(h->par.precision, h->config);
+  const CallPlan cp = plan_call(h, nevt, chunk_for(nd, nevt), want_hel, want_col);
+  void* wsp = nullptr;
+  if (cp.total) {
+    int rc = get_workspace(h, reinterpret_cast<uintptr_t>(s) << 1, s, cp.total, &wsp);
+    if (rc) return rc;
   }
   MeLaunch a{};
   fill_common(h, a);
@@ -362,9 +424,20 @@ static int compute_device(me_handle* h, int64_t nevt, const double* momenta, con
   a.sel_col = want_col ? sel_col : nullptr;
   a.ngood = ngood;
   for (int i = 0; i < ngood; ++i) a.good[i] = uint8_t(h->good[i]);
-  cudaError_t e = launch_chunks(ops, prec, config, a, nevt, chunk, cv, wsp, s);
+  cudaError_t e = run_call(h, cp, a, nevt, wsp, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "me_compute launch");
   return ME_OK;
+}
+
+int me_reserve(me_handle* h, int64_t nevt, void* cuda_stream) {
+  if (!h) return fail(nullptr, ME_ERR_ARG, "me_reserve: null handle");
+  if (nevt < 0) return fail(h, ME_ERR_ARG, "me_reserve: nevt < 0");
+  if (nevt == 0) return ME_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  const LaunchNeeds nd = h->ops->needs(h->par.precision, h->config);
+  const CallPlan cp = plan_call(h, nevt, chunk_for(nd, nevt), true, true);
+  void* wsp = nullptr;
+  return cp.total ? get_workspace(h, reinterpret_cast<uintptr_t>(s) << 1, s, cp.total, &wsp) : ME_OK;
 }
 
 int me_compute(me_handle* h, int64_t nevt, const double* momenta, const double* alphas, const double* rnd_hel,
@@ -455,9 +528,9 @@ int me_plan(const me_handle* h, int64_t nevt, int64_t* launches, int64_t* worksp
   if (!h || nevt < 0) return ME_ERR_ARG;
   const LaunchNeeds nd = h->ops->needs(h->par.precision, h->config);
   const int64_t chunk = std::max<int64_t>(1, chunk_for(nd, nevt));
-  if (launches) *launches = nevt ? (nevt + chunk - 1) / chunk : 0;
-  if (workspace_bytes)
-    *workspace_bytes = int64_t(carve(h->ops, nd, int(h->good.size()), chunk, true, true).total());
+  const CallPlan cp = plan_call(h, nevt, chunk, true, true);
+  if (launches) *launches = nevt ? (nevt + chunk - 1) / chunk + (cp.rescue ? 1 : 0) : 0;
+  if (workspace_bytes) *workspace_bytes = int64_t(cp.total);
   return ME_OK;
 }
 

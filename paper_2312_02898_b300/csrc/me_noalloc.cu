@@ -77,22 +77,20 @@ extern "C" int me_compute_noalloc(me_handle* h, int64_t nevt, const double* mome
     return fail(h, ME_ERR_TIMEOUT, "me_compute_noalloc: a device-side wait of an earlier call on this handle "
                                    "timed out; its events were set to NaN");
   }
-  const ProcessOps* ops = h->ops;
-  const int prec = h->par.precision, config = h->config;
   const int ngood = int(h->good.size());
   const bool want_hel = sel_hel && rnd_hel;
   const bool want_col = sel_col && rnd_col;
-  const LaunchNeeds nd = ops->needs(prec, config);
-  // one launch over every event: the whole batch's scratch must fit the fixed array
-  const Carve cv = carve(ops, nd, ngood, nevt, want_hel, want_col);
-  if (cv.total() > kScratchBytes) {
-    const Carve one = carve(ops, nd, ngood, 1024, want_hel, want_col);
-    const double per_event = double(one.total()) / 1024.0;
+  // one main launch over every event (plus the FP64 rescue pass of the FP32 and mixed
+  // modes): the whole batch's scratch must fit the fixed array
+  const CallPlan cp = plan_call(h, nevt, nevt, want_hel, want_col);
+  if (cp.total > kScratchBytes) {
+    const CallPlan one = plan_call(h, 1024, 1024, want_hel, want_col);
+    const double per_event = double(one.total) / 1024.0;
     char msg[256];
     std::snprintf(msg, sizeof msg,
                   "me_compute_noalloc: %lld events need %zu bytes of scratch, more than the fixed %zu bytes "
                   "(about %lld events of this process and mode per call)",
-                  static_cast<long long>(nevt), cv.total(), kScratchBytes,
+                  static_cast<long long>(nevt), cp.total, kScratchBytes,
                   static_cast<long long>(per_event > 0 ? double(kScratchBytes) / per_event : 0));
     return fail(h, ME_ERR_ARG, msg);
   }
@@ -100,7 +98,8 @@ extern "C" int me_compute_noalloc(me_handle* h, int64_t nevt, const double* mome
   int rc = scratch_address(h, &scratch);
   if (rc) return rc;
   // Nothing in the scratch has to start at zero: the kernels write every running sum,
-  // colour weight, slot and momentum-table entry of an event before they read it.
+  // colour weight, slot and momentum-table entry of an event before they read it, and
+  // the rescue counter is cleared on the stream at the start of every call.
   MeLaunch a{};
   fill_common(h, a);
   a.err = h->err_dev;
@@ -113,7 +112,7 @@ extern "C" int me_compute_noalloc(me_handle* h, int64_t nevt, const double* mome
   a.sel_col = want_col ? sel_col : nullptr;
   a.ngood = ngood;
   for (int i = 0; i < ngood; ++i) a.good[i] = uint8_t(h->good[i]);
-  cudaError_t e = launch_chunks(ops, prec, config, a, nevt, nevt, cv, scratch, static_cast<cudaStream_t>(cuda_stream));
+  cudaError_t e = run_call(h, cp, a, nevt, scratch, static_cast<cudaStream_t>(cuda_stream));
   if (e != cudaSuccess) return cuda_fail(h, e, "me_compute_noalloc launch");
   return ME_OK;
 }

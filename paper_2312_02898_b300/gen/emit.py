@@ -365,9 +365,12 @@ class Emitter:
                 out.append(f"  q[{mu}] = {e};")
             return out
 
+        den.append("  double kappa = 0.0;  // conditioning: max over gluon propagators of (sum E)^2 / |K^2|")
         for m, idx in sorted(gmask_idx.items(), key=lambda t: t[1]):
             den += dd_sum(self.kin_terms(m))
-            den.append(f"  dg[{idx}] = R(1.0 / dd_invariant(q, 0.0));")
+            esum = " + ".join(f"p[{i}][0]" for _, i in self.kin_terms(m))
+            den.append(f"  {{ const double k2 = dd_invariant(q, 0.0), es = {esum};")
+            den.append(f"    dg[{idx}] = R(1.0 / k2); kappa = fmax(kappa, es * es / fabs(k2)); }}")
         for m, idx in sorted(tmask_idx.items(), key=lambda t: t[1]):
             tchan = (m & 1) != ((m >> 1) & 1)  # separates the two incoming particles
             den += dd_sum(fermion_parts(m))
@@ -418,9 +421,10 @@ class Emitter:
                "static constexpr bool QCD = true;", "",
                f"static constexpr int NKVEC = {nk};  // momentum vectors in the per-event table",
                "template <int S, class R, class DG, class DT>",
-               "static HD void precompute(const double (*p)[4], double mt, double wt, int zwt, DG& dg, DT& dt,"
+               "static HD double precompute(const double (*p)[4], double mt, double wt, int zwt, DG& dg, DT& dt,"
                " R* kt) {"]
         out += den
+        out.append("  return kappa;")
         out.append("}")
         out.append("// jamps variants: register budget (currents kept in registers, -1 = all), diagram-group")
         out.append("// size (0 = one function) and slots used in the per-thread slot buffer ws (slot s at")
@@ -488,7 +492,7 @@ class Emitter:
                "static constexpr bool QCD = false;",
                "// Photon and Z in the s channel.  dg[0] = 1/s;  dt[0] = 1/(s - mZ^2 + i mZ wZ).",
                "template <int S, class R, class DG, class DT>",
-               "static HD void precompute(const double (*p)[4], double mZ, double wZ, int, DG& dg, DT& dt, R* kt) {",
+               "static HD double precompute(const double (*p)[4], double mZ, double wZ, int, DG& dg, DT& dt, R* kt) {",
                "  for (int i = 0; i < 4; ++i)",
                "    for (int m = 0; m < 4; ++m) kt[i * S + m] = R(p[i][m]);",
                "  double q[4];",
@@ -497,6 +501,7 @@ class Emitter:
                "  dg[0] = R(1.0 / s);",
                "  const double re = s - mZ * mZ, im = mZ * wZ, inv = 1.0 / (re * re + im * im);",
                "  dt[0] = mk<R>(R(re * inv), R(-im * inv));",
+               "  return 0.0;",
                "}",
                "// J = i [ (j_e . j_mu)_photon / s + (j_e . j_mu)_Z / D_Z ] in units of e^2: the photon",
                "// couples with Q_e Q_mu = 1 overall, the Z with (gL, gR) = zc[0..1] on each current.",

@@ -112,6 +112,34 @@ def test_mixed_parity(process):
         assert np.mean(sc == ref["sel_col"]) > 0.99
 
 
+@pytest.mark.parametrize("process", [p for p in ACTIVE if p != PROCS[0]])
+def test_rescue_pass_reproduces_fp64(process):
+    """With a conditioning threshold below every event's, the FP32 call flags all events
+    and its FP64 rescue pass (indexed, grid-stride) must reproduce the FP64 handle."""
+    n = 600 if process != PROCS[4] else 100
+    mom, a, rh, rc = ps.make_batch(process, n, seed=19, alphas="uniform")
+    r64 = run_gpu(mk(process, "fp64"), mom, a, rh, rc)
+    r32 = run_gpu(mk(process, "fp32", rescue_kappa=1e-300), mom, a, rh, rc)
+    for x, y in zip(r64, r32):
+        assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("process", [p for p in ACTIVE if p in (PROCS[2], PROCS[3])])
+def test_rescue_removes_the_fp32_error_tail(process):
+    """Without the rescue the FP32 error tail comes from nearly collinear gluons; with
+    it (default threshold) every event stays within the FP32 bound."""
+    mom, a, rh, rc = ps.make_batch(process, 3000, seed=23, alphas="uniform")
+    ref = oracle.me(process, mom, alphas=a)["me"]
+    plain = run_gpu(mk(process, "fp32", rescue_kappa=0.0), mom, a, rh, rc)[0]
+    resc = run_gpu(mk(process, "fp32"), mom, a, rh, rc)[0]
+    e_plain = np.abs(plain / ref - 1)
+    e_resc = np.abs(resc / ref - 1)
+    print(f"{process}: fp32 max rel without rescue {e_plain.max():.3e}, with {e_resc.max():.3e}; "
+          f"events changed {np.mean(plain != resc):.4f}")
+    assert e_resc.max() <= FP32_BOUND
+    assert e_resc.max() <= e_plain.max()
+
+
 @pytest.mark.parametrize("process", MIXED)
 def test_mixed_matches_fp32_amplitudes(process):
     """The tensor-core colour sum agrees with the FP32 CUDA-core colour sum of the same
