@@ -11,6 +11,7 @@ oracle at 1e-12).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--mode fp64|fp32|mixed]
     python bench.py --impl reference      # the FP64 CPU oracle on the host cores
+    python bench.py --serving             # the request stream: p50/p99 latency, sustained ME/s
 
 Multi-GPU: every rank evaluates its own batch (disjoint event indices); the timed
 region is bracketed by barriers and the maximum over ranks is taken.  No data-path
@@ -46,6 +47,16 @@ def dist_env():
 def shard_events(rank: int, nevt_per_rank: int):
     """first event index of this rank's batch (disjoint, batch-independent RNG)"""
     return rank * nevt_per_rank
+
+
+def max_over_ranks(x: float, dist=None, device=None) -> float:
+    """the maximum of x over all ranks (x itself without a process group)"""
+    if not dist:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 class ClockSampler:
@@ -163,11 +174,7 @@ def time_mode(mode, dev_inputs, host_inputs, steps, warmup, dist):
         torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    ms = e0.elapsed_time(e1) / steps
-    if dist:
-        t = torch.tensor([ms], device=mom.device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = t.item()
+    ms = max_over_ranks(e0.elapsed_time(e1) / steps, dist, mom.device)
     launches, ws_bytes = m.plan(nevt)
     # end to end through the host entry point: pinned host inputs, copies inside
     hmom, ha, hrh, hrc = host_inputs
@@ -179,11 +186,7 @@ def time_mode(mode, dev_inputs, host_inputs, steps, warmup, dist):
     t0 = time.perf_counter()
     for _ in range(steps):
         m.compute_host(hmom, ha, hrh, hrc, out=hout, stream=stream)
-    e2e_ms = (time.perf_counter() - t0) * 1e3 / steps
-    if dist:
-        t = torch.tensor([e2e_ms], device=mom.device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = t.item()
+    e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / steps, dist, mom.device)
     return {"ms": ms, "launches": launches, "workspace_bytes": ws_bytes, "clocks": clk.summary(),
             "flops_per_event": m.flops_per_event(), "ngood": m.ngood, "e2e_ms": e2e_ms, "me": out[0],
             "sel": (out[1], out[2])}
@@ -261,7 +264,8 @@ def run_gpu(args):
                 "config": {"workload": f"{PROCESS}, sqrt(s)=1500 GeV, alpha_s~U[0.10,0.13], both selections",
                            "events_per_gpu": NEVT, "global_batch": NEVT * world, "precision": args.mode,
                            "parallelism": f"events sharded over {world} GPU(s), no collective",
-                           "l2": "inputs (226 MB per GPU) larger than L2; no flush"},
+                           "l2": f"inputs ({NEVT * 216 / 1e6:.0f} MB per GPU) "
+                                 + ("larger than L2; no flush" if NEVT * 216 > 126e6 else "smaller than L2")},
                 "clocks": head["clocks"],
                 "gpu_launches": head["launches"] * args.steps,
                 "e2e": {"value": world * NEVT / (head["e2e_ms"] * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
@@ -279,6 +283,66 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def _gen_request(item):
+    from paper_2312_02898_b300.phasespace import make_batch
+    t, proc, n, seed = item
+    mom, a, rh, rc = make_batch(proc, n, seed=seed, alphas="uniform")
+    return t, proc, mom, a, rh, rc
+
+
+def run_serving(args):
+    """The serving stream: Poisson arrivals of requests for all processes (weights
+    0.1 / 0.15 / 0.15 / 0.4 / 0.2 for e+e- -> mu+mu-, gg -> tt~, gg -> tt~g, gg -> tt~gg,
+    gg -> tt~ggg), sizes log-uniform in [256, 65536], request k from seed k.  For each
+    precision: the sustained capacity with every request queued at once, then the
+    open-loop stream at fractions of that capacity with p50/p99 latency (submit to
+    results on the host)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    from paper_2312_02898_b300 import serving
+    nreq = args.serving_requests + args.serving_warmup
+    stream = serving.request_stream(nreq, rate_hz=1.0, seed=0)
+    with cf.ProcessPoolExecutor(max_workers=min(32, os.cpu_count() or 1), mp_context=mp.get_context("spawn")) as ex:
+        reqs = list(ex.map(_gen_request, stream, chunksize=8))
+    import torch
+    mean_events = float(np.mean([r[2].shape[0] for r in reqs]))
+    out = {}
+    for prec in args.serving_precisions.split(","):
+        server = serving.Server([p for p, _ in serving.STREAM_PROCESSES], precision=prec, n_slots=args.serving_slots)
+        try:
+            t0 = time.perf_counter()
+            for p, _ in serving.STREAM_PROCESSES:
+                for b in serving.BUCKETS:
+                    server.warm(p, b)
+            warm_s = time.perf_counter() - t0
+            cap = serving.run_saturated(server, reqs[: args.serving_warmup + args.serving_requests // 4])
+            res = {"capacity_me_per_s": cap, "graphs": len(server.buffers), "warm_s": warm_s,
+                   "precision_per_process": server.precision, "load": {}}
+            loads = [float(x) for x in args.serving_loads.split(",")] if not out else [0.7]
+            for frac in loads:
+                rate = frac * cap / mean_events                   # requests per second
+                st = serving.run_open_loop(server, reqs, rate_scale=rate, warmup=args.serving_warmup)
+                st["offered_requests_per_s"] = rate
+                st["offered_me_per_s"] = frac * cap
+                res["load"][f"{int(round(frac * 100))}%"] = st
+            out[prec] = res
+        finally:
+            server.close()
+            del server
+            torch.cuda.synchronize()
+    head = out[args.serving_precisions.split(",")[0]]
+    key = "70%" if "70%" in head["load"] else next(iter(head["load"]))
+    line = {"metric": METRIC, "value": head["load"][key]["p99_ms"], "unit": "ms (p99 latency)",
+            "higher_is_better": False, "n_gpus": 1, "steps": args.serving_requests, "warmup": args.serving_warmup,
+            "data": "synthetic (RAMBO, Philox4x32-10, request k from seed k)",
+            "config": {"workload": "serving stream: Poisson arrivals over the five processes, "
+                                   "log-uniform 256-65536 events per request, alpha_s~U[0.10,0.13]",
+                       "slots": args.serving_slots, "buckets": list(serving.BUCKETS),
+                       "mean_events_per_request": mean_events, "headline_load": key},
+            "serving": out}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -288,7 +352,19 @@ def main():
     ap.add_argument("--mode", default="fp64", choices=["fp64", "fp32", "mixed"])
     ap.add_argument("--only", action="store_true", help="time only the headline mode")
     ap.add_argument("--ref-sample", type=int, default=4096, help="oracle events per CPU-baseline sample")
+    ap.add_argument("--serving", action="store_true", help="run the serving stream instead of the throughput step")
+    ap.add_argument("--serving-requests", type=int, default=2000)
+    ap.add_argument("--serving-warmup", type=int, default=200)
+    ap.add_argument("--serving-slots", type=int, default=4)
+    ap.add_argument("--serving-loads", default="0.5,0.7,0.9,1.1",
+                    help="offered load as fractions of capacity (first precision; the others run at 0.7)")
+    ap.add_argument("--serving-precisions", default="mixed,fp64")
+    ap.add_argument("--nevt", type=int, default=NEVT,
+                    help="events per GPU per step (a smaller case for profiling; the workload is 1048576)")
     args = ap.parse_args()
+    globals()["NEVT"] = args.nevt
+    if args.serving:
+        return run_serving(args)
     if args.warmup < 3:
         raise SystemExit("at least 3 warm-up steps")
     if args.impl == "reference":

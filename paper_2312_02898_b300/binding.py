@@ -17,14 +17,15 @@ PRECISIONS = {"fp64": 0, "fp32": 1, "mixed": 2}
 
 # the C-ABI entry points declared in include/me.h
 EXPORTS = ("me_default_params", "me_init", "me_compute", "me_compute_host", "me_info", "me_good_helicities",
-           "me_flops", "me_plan", "me_set_config", "me_last_error", "me_free", "me_probe_alu_peak")
+           "me_flops", "me_plan", "me_reserve", "me_set_config", "me_last_error", "me_free",
+           "me_compute_noalloc", "me_probe_alu_peak")
 
 
 class SMParams(ctypes.Structure):
     _fields_ = [("mZ", ctypes.c_double), ("wZ", ctypes.c_double), ("mt", ctypes.c_double),
                 ("wt", ctypes.c_double), ("aEWM1", ctypes.c_double), ("Gf", ctypes.c_double),
                 ("alphas_default", ctypes.c_double), ("precision", ctypes.c_int),
-                ("zero_width_tchan", ctypes.c_int)]
+                ("zero_width_tchan", ctypes.c_int), ("rescue_kappa", ctypes.c_double)]
 
 
 class MEError(RuntimeError):
@@ -51,6 +52,8 @@ def load(path: str = LIB_PATH):
     lib.me_init.argtypes = [ctypes.c_char_p, ctypes.POINTER(SMParams), ctypes.POINTER(vp)]
     lib.me_compute.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.me_compute_host.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.me_compute_noalloc.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp]
+    lib.me_reserve.argtypes = [vp, i64, vp]
     lib.me_info.argtypes = [vp, ip, ip, ip, ip, ip]
     lib.me_good_helicities.argtypes = [vp, ctypes.POINTER(ctypes.c_int32)]
     lib.me_flops.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
@@ -61,8 +64,8 @@ def load(path: str = LIB_PATH):
     lib.me_last_error.restype = ctypes.c_char_p
     lib.me_free.argtypes = [vp]
     lib.me_free.restype = None
-    for f in ("me_init", "me_compute", "me_compute_host", "me_info", "me_good_helicities", "me_flops",
-              "me_set_config", "me_plan", "me_probe_alu_peak"):
+    for f in ("me_init", "me_compute", "me_compute_host", "me_compute_noalloc", "me_info", "me_good_helicities",
+              "me_flops", "me_set_config", "me_plan", "me_reserve", "me_probe_alu_peak"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -75,9 +78,11 @@ def default_params() -> SMParams:
 
 
 def alu_peak(precision: str, seconds: float = 0.3) -> float:
-    """measured FMA throughput (flop/s) of the current device for 'fp64' or 'fp32'"""
+    """measured FMA throughput (flop/s) of the current device for 'fp64', 'fp32' or
+    'fp32x2' (packed pairs, two FMAs per instruction)"""
     v = ctypes.c_double()
-    rc = load().me_probe_alu_peak(PRECISIONS[precision], seconds, ctypes.byref(v))
+    code = {"fp64": 0, "fp32": 1, "fp32x2": 2}[precision]
+    rc = load().me_probe_alu_peak(code, seconds, ctypes.byref(v))
     if rc != ME_OK:
         raise MEError(rc, "ALU probe failed")
     return v.value
@@ -123,6 +128,12 @@ class MatrixElement:
         n, w = ctypes.c_int64(), ctypes.c_int64()
         self._check(self.lib.me_plan(self.handle, nevt, ctypes.byref(n), ctypes.byref(w)))
         return n.value, w.value
+
+    def reserve(self, nevt: int, stream=None):
+        """size the workspace of ``stream`` for calls of up to nevt events (before graph capture)"""
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream()
+        self._check(self.lib.me_reserve(self.handle, nevt, ctypes.c_void_p(s.cuda_stream)))
 
     def set_config(self, config: int):
         self._check(self.lib.me_set_config(self.handle, config))
