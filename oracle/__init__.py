@@ -7,10 +7,13 @@ conventions and the published methods it follows.
 
 Pinned by the ``-m "not gpu"`` tests in ``tests/test_oracle_*.py`` against closed
 forms (e+e- -> mu+mu-, gg -> ttbar), an explicit-colour brute force, exact colour
-algebra, and the Lorentz / gauge / Bose / alpha_s-scaling invariants.  The absolute
-values for gg -> ttbar gg and gg -> ttbar ggg are pinned only through those
-invariants and through the same code being exact for two and three gluons:
-parity of those two processes is "unpinned" beyond that.
+algebra, the Lorentz / gauge / Bose / alpha_s-scaling invariants, and the
+Parke-Taylor formula: with massless quarks every MHV colour-ordered amplitude for 2 to
+5 gluons equals (sqrt(2) g_s)^n_g times its closed form, which fixes the absolute
+normalisation of the recursion for gg -> ttbar gg and gg -> ttbar ggg.  What the
+massless limit leaves open there (the massive spinors and top propagators at 4-5
+gluons) is pinned by the same code being exact for gg -> ttbar against its closed
+form, and by gauge invariance and Bose symmetry at the physical top mass.
 """
 from __future__ import annotations
 
