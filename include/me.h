@@ -86,6 +86,9 @@ void me_default_params(me_sm_params* p);
 /* Create a handle for one process on the current CUDA device.  Runs the helicity
  * filter: a helicity is kept when |M_h|^2 is not exactly zero (FP64) on any of 1024
  * fixed RAMBO events at sqrt(s) = 1500 GeV.  *out receives the handle (NULL on error).
+ * Environment, read here: ME_B300_CONFIG selects the launch configuration (as
+ * me_set_config); ME_B300_MAX_BLOCKS caps the blocks of the persistent grid, which
+ * otherwise holds every block that fits on the device at once (for tests).
  * Errors: ME_ERR_ARG (null pointer, unknown process, invalid parameter),
  * ME_ERR_MODE, ME_ERR_NOMEM, ME_ERR_CUDA. */
 int me_init(const char* process, const me_sm_params* p, me_handle** out);
@@ -137,6 +140,24 @@ int me_compute_noalloc(me_handle* h, int64_t nevt, const double* momenta, const 
                        const double* rnd_hel, const double* rnd_col, double* me, int32_t* sel_hel,
                        int32_t* sel_col, void* cuda_stream);
 
+/* GPU-assisted batch unweighting (Section 3, Table 2): with the whole batch's largest
+ * weight known before any decision, hit-or-miss needs no provisional storage.
+ *   me       device, FP64 [nevt]  matrix elements (e.g. from me_compute)
+ *   wgt      device, FP64 [nevt]  the rest of each event weight (Jacobian x PDFs ...)
+ *   rnd      device, FP64 [nevt]  uniform numbers in [0,1); required when accept or
+ *                                 n_accept is given
+ *   w        device, FP64 [nevt]  output w_i = me_i * wgt_i, or NULL
+ *   accept   device, uint8 [nevt] output 1 when w_i > rnd_i * w_max, else 0; or NULL
+ *   w_max    device, one FP64     output: the largest valid weight (finite, >= 0), or 0
+ *                                 when there is none; 8-byte aligned
+ *   n_accept device, one int64    output: number of accepted events, or NULL
+ * A weight that is NaN, infinite or negative never sets w_max and is never accepted.
+ * Asynchronous on cuda_stream; nevt == 0 is a no-op that leaves the outputs untouched.
+ * Errors: ME_ERR_ARG (null handle or required pointer, nevt < 0, a host pointer,
+ * misaligned scalar), ME_ERR_CUDA. */
+int me_unweight(me_handle* h, int64_t nevt, const double* me, const double* wgt, const double* rnd,
+                double* w, uint8_t* accept, double* w_max, int64_t* n_accept, void* cuda_stream);
+
 /* Process shape: external particles, helicity combinations, helicities kept by the
  * filter, colour flows, Feynman diagrams.  Any output pointer may be NULL. */
 int me_info(const me_handle* h, int* npar, int* ncomb, int* ngood, int* ncol, int* ndiag);
@@ -158,6 +179,11 @@ int me_plan(const me_handle* h, int64_t nevt, int64_t* launches, int64_t* worksp
  * to that size on that stream allocate nothing (stream-ordered allocation on
  * cuda_stream).  Errors: ME_ERR_ARG (null handle, nevt < 0), ME_ERR_NOMEM, ME_ERR_CUDA. */
 int me_reserve(me_handle* h, int64_t nevt, void* cuda_stream);
+
+/* Launch geometry of the main pass of a me_compute call of nevt events: blocks of the
+ * persistent grid, threads per block, resident blocks per SM of the kernel, SMs of the
+ * handle's device.  Any output pointer may be NULL.  Errors: ME_ERR_ARG. */
+int me_launch_shape(const me_handle* h, int64_t nevt, int* grid, int* block, int* blocks_per_sm, int* nsm);
 
 /* Select the kernel launch configuration (register budget, block size, placement of
  * per-thread arrays) used by later me_compute calls; 0 is the default.  Returns the

@@ -13,7 +13,8 @@ extern "C" {
 #endif
 
 /* Sustained FMA throughput of the current device in flop/s (an FMA counts 2):
- * prec 0 = FP64, 1 = FP32.  Runs for roughly 'seconds' (0.05 .. 5).  Returns 0 and
+ * prec 0 = FP64, 1 = FP32, 2 = packed FP32 pairs (fma.rn.f32x2, two FMAs per
+ * instruction).  Runs for roughly 'seconds' (0.05 .. 5).  Returns 0 and
  * writes *flops_per_s, or a negative status (-1 bad argument, -4 CUDA error). */
 int me_probe_alu_peak(int prec, double seconds, double* flops_per_s);
 

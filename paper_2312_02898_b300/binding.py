@@ -17,8 +17,8 @@ PRECISIONS = {"fp64": 0, "fp32": 1, "mixed": 2}
 
 # the C-ABI entry points declared in include/me.h
 EXPORTS = ("me_default_params", "me_init", "me_compute", "me_compute_host", "me_info", "me_good_helicities",
-           "me_flops", "me_plan", "me_reserve", "me_set_config", "me_last_error", "me_free",
-           "me_compute_noalloc", "me_probe_alu_peak")
+           "me_flops", "me_plan", "me_reserve", "me_launch_shape", "me_set_config", "me_last_error", "me_free",
+           "me_compute_noalloc", "me_unweight", "me_probe_alu_peak")
 
 
 class SMParams(ctypes.Structure):
@@ -54,6 +54,8 @@ def load(path: str = LIB_PATH):
     lib.me_compute_host.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.me_compute_noalloc.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.me_reserve.argtypes = [vp, i64, vp]
+    lib.me_launch_shape.argtypes = [vp, i64, ip, ip, ip, ip]
+    lib.me_unweight.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp]
     lib.me_info.argtypes = [vp, ip, ip, ip, ip, ip]
     lib.me_good_helicities.argtypes = [vp, ctypes.POINTER(ctypes.c_int32)]
     lib.me_flops.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
@@ -65,7 +67,8 @@ def load(path: str = LIB_PATH):
     lib.me_free.argtypes = [vp]
     lib.me_free.restype = None
     for f in ("me_init", "me_compute", "me_compute_host", "me_compute_noalloc", "me_info", "me_good_helicities",
-              "me_flops", "me_set_config", "me_plan", "me_reserve", "me_probe_alu_peak"):
+              "me_flops", "me_set_config", "me_plan", "me_reserve", "me_launch_shape", "me_unweight",
+              "me_probe_alu_peak"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -135,6 +138,12 @@ class MatrixElement:
         s = stream if stream is not None else torch.cuda.current_stream()
         self._check(self.lib.me_reserve(self.handle, nevt, ctypes.c_void_p(s.cuda_stream)))
 
+    def launch_shape(self, nevt: int):
+        """(grid blocks, threads per block, resident blocks per SM, SMs) of the main pass"""
+        v = [ctypes.c_int() for _ in range(4)]
+        self._check(self.lib.me_launch_shape(self.handle, nevt, *[ctypes.byref(x) for x in v]))
+        return tuple(x.value for x in v)
+
     def set_config(self, config: int):
         self._check(self.lib.me_set_config(self.handle, config))
 
@@ -170,6 +179,21 @@ class MatrixElement:
                                  _ptr(me), _ptr(sh), _ptr(sc), ctypes.c_void_p(s.cuda_stream))
         self._check(rc)
         return me, sh, sc
+
+    def unweight(self, me, wgt, rnd=None, stream=None, want_w=True, want_accept=True):
+        """GPU-assisted batch unweighting of device tensors: (w, accept, w_max, n_accept),
+        all device tensors (w_max and n_accept one element each); asynchronous."""
+        import torch
+        n = me.shape[0]
+        dev = me.device
+        w = torch.empty(n, dtype=torch.float64, device=dev) if want_w else None
+        acc = torch.empty(n, dtype=torch.uint8, device=dev) if (want_accept and rnd is not None) else None
+        wmax = torch.empty(1, dtype=torch.float64, device=dev)
+        nacc = torch.empty(1, dtype=torch.int64, device=dev) if rnd is not None else None
+        s = stream if stream is not None else torch.cuda.current_stream(dev)
+        self._check(self.lib.me_unweight(self.handle, n, _ptr(me), _ptr(wgt), _ptr(rnd), _ptr(w), _ptr(acc),
+                                         _ptr(wmax), _ptr(nacc), ctypes.c_void_p(s.cuda_stream)))
+        return w, acc, wmax, nacc
 
     def compute_raw(self, nevt, momenta_ptr, alphas_ptr, rnd_hel_ptr, rnd_col_ptr, me_ptr, sel_hel_ptr,
                     sel_col_ptr, stream_ptr):

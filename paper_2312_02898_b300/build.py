@@ -9,6 +9,7 @@ import argparse
 import concurrent.futures as cf
 import glob
 import os
+import re
 import subprocess
 import sys
 import time
@@ -26,17 +27,24 @@ CFLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptx
                  "-I", INCLUDE, "-I", CSRC]
 
 
+_INCLUDE_RE = re.compile(r'^\s*#\s*include\s+"([^"]+)"', re.M)
+
+
 def _deps(cu):
-    deps = [cu] + glob.glob(os.path.join(CSRC, "*.cuh"))
-    src = open(cu).read()
-    if "me.h" in src or "me_internal.h" in src:
-        deps += [os.path.join(INCLUDE, "me.h"), os.path.join(CSRC, "me_internal.h")]
-    if "me_probe.h" in src:
-        deps.append(os.path.join(INCLUDE, "me_probe.h"))
-    tag = os.path.basename(cu)[:-3]
-    if tag.startswith("proc_"):
-        deps.append(os.path.join(GEN, tag + ".cuh"))
-    return [d for d in deps if os.path.exists(d)]
+    """the source and every local header it includes, followed recursively"""
+    seen, todo = set(), [os.path.abspath(cu)]
+    while todo:
+        f = todo.pop()
+        if f in seen or not os.path.exists(f):
+            continue
+        seen.add(f)
+        for inc in _INCLUDE_RE.findall(open(f).read()):
+            for base in (os.path.dirname(f), CSRC, INCLUDE):
+                cand = os.path.normpath(os.path.join(base, inc))
+                if os.path.exists(cand):
+                    todo.append(cand)
+                    break
+    return sorted(seen)
 
 
 def _stale(target, deps):

@@ -28,6 +28,12 @@
 #define HD inline
 #define NOINL __attribute__((noinline))
 #endif
+// block barrier of the generated code's optional sync points (nothing on the host)
+#if defined(__CUDA_ARCH__)
+#define MEB_BLOCK_SYNC() __syncthreads()
+#else
+#define MEB_BLOCK_SYNC() ((void)0)
+#endif
 
 namespace meb300 {
 

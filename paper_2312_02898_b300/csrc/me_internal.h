@@ -30,12 +30,15 @@ struct me_handle {
   std::string err;
   int* err_host = nullptr;  // mapped pinned word the kernels raise on a timed-out wait
   int* err_dev = nullptr;
+  int nsm = 1;              // streaming multiprocessors of the handle's device
+  int max_blocks = 0;       // cap on the persistent grid (0: as many as are resident)
 };
 
 namespace meb300 {
 namespace detail {
 
-// Bytes of workspace one launch of 'chunk' events needs, and its carve-up.
+// Bytes of workspace of one persistent launch (one row per resident thread), and its
+// carve-up.
 struct Carve {
   size_t cum = 0, colw = 0, slots = 0, ktab = 0;
   size_t total() const { return cum + colw + slots + ktab; }
@@ -47,6 +50,7 @@ struct Carve {
 struct CallPlan {
   int prec = 0, config = 0;
   int64_t chunk = 0;
+  int grid = 0, block = 0;  // persistent grid of the main pass
   Carve main;
   bool rescue = false;
   int rescue_cap = 0, rescue_grid = 0;
@@ -58,8 +62,10 @@ int fail(me_handle* h, int code, const std::string& msg);
 int cuda_fail(me_handle* h, cudaError_t e, const char* where);
 void fill_common(const me_handle* h, MeLaunch& a);
 bool is_device_ptr(const void* p);
-Carve carve(const ProcessOps* ops, const LaunchNeeds& nd, int ngood, int64_t chunk, bool want_hel, bool want_col);
+Carve carve(const ProcessOps* ops, const LaunchNeeds& nd, int ngood, int64_t rows, bool want_hel, bool want_col);
+int persistent_grid(const me_handle* h, const LaunchNeeds& nd, int64_t nevt);
 cudaError_t launch_chunks(const ProcessOps* ops, int prec, int config, MeLaunch a, int64_t nevt, int64_t chunk,
+                          int grid, int block,
                           const Carve& cv, void* wsp, cudaStream_t s);
 CallPlan plan_call(const me_handle* h, int64_t nevt, int64_t chunk, bool want_hel, bool want_col);
 cudaError_t run_call(const me_handle* h, const CallPlan& cp, const MeLaunch& a, int64_t nevt, void* wsp, cudaStream_t s);

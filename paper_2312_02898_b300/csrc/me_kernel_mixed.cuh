@@ -2,9 +2,10 @@
 // (generated code, one event per thread, as in me_kernel), colour sum on the tensor
 // cores (colour_mma.cuh), FP64 inputs, denominators and helicity sum.
 //
-// One block = 128 events = the M = 128 rows of one tcgen05 MMA.  Every thread of the
-// block takes part in every barrier (threads past the end of the batch mirror the
-// last event and write nothing).
+// One block tile = 128 events = the M = 128 rows of one tcgen05 MMA.  The grid is
+// persistent: each block sets up its tensor-core state once and walks the batch tile by
+// tile.  Every thread of the block takes part in every barrier (threads past the end
+// of the batch mirror the last event and write nothing).
 #pragma once
 
 #include "colour_mma.cuh"
@@ -42,9 +43,9 @@ __global__ void __launch_bounds__(128) me_kernel_mixed(const MeLaunch a) {
   extern __shared__ __align__(16) unsigned char smem_mixed[];  // 16 B suffices for the descriptors
   const int tid = threadIdx.x, warp = tid >> 5;
   const int64_t nevt = a.nevt;
-  const int64_t ievt_raw = int64_t(blockIdx.x) * BLOCK + tid;
-  const bool active = ievt_raw < nevt;
-  const int64_t ievt = active ? ievt_raw : nevt - 1;
+  const int64_t ntile = (nevt + BLOCK - 1) / BLOCK;
+  const int64_t wrow = int64_t(blockIdx.x) * BLOCK + tid;  // this thread's workspace row
+  const int64_t wstride = int64_t(gridDim.x) * BLOCK;
 
   uint32_t* s_tmem = reinterpret_cast<uint32_t*>(smem_mixed);
   uint64_t* s_mbar = reinterpret_cast<uint64_t*>(smem_mixed + 16);
@@ -68,17 +69,10 @@ __global__ void __launch_bounds__(128) me_kernel_mixed(const MeLaunch a) {
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tbase = *s_tmem;
+  uint32_t phase = 0;
+  bool failed = false;
 
-  // --- per-event set-up, as in me_kernel
-  double pd[P::NPAR][4];
-  {
-    const double2* src = reinterpret_cast<const double2*>(a.mom + ievt * (P::NPAR * 4));
-#pragma unroll
-    for (int i = 0; i < P::NPAR; ++i) {
-      const double2 v0 = __ldg(src + 2 * i), v1 = __ldg(src + 2 * i + 1);
-      pd[i][0] = v0.x; pd[i][1] = v0.y; pd[i][2] = v1.x; pd[i][3] = v1.y;
-    }
-  }
+  // --- per-thread working storage, carved once for all tiles
   R* s_dg = reinterpret_cast<R*>(sp); sp += size_t(P::NDEN_G) * BLOCK * sizeof(R);
   cx<R>* s_dt = reinterpret_cast<cx<R>*>(sp); sp += size_t(P::NDEN_T) * BLOCK * sizeof(cx<R>);
   cx<R>* s_J = reinterpret_cast<cx<R>*>(sp); sp += size_t(P::NCOL) * BLOCK * sizeof(cx<R>);
@@ -96,6 +90,22 @@ __global__ void __launch_bounds__(128) me_kernel_mixed(const MeLaunch a) {
   else kt = static_cast<R*>(a.ktab) + (size_t(blockIdx.x) * P::NKVEC * BLOCK + tid) * 4;
   Strided<R, BLOCK> v_dg{s_dg + tid};
   Strided<cx<R>, BLOCK> v_dt{s_dt + tid};
+
+  for (int64_t tile = blockIdx.x; tile < ntile && !failed; tile += gridDim.x) {
+  const int64_t ievt_raw = tile * BLOCK + tid;
+  const bool active = ievt_raw < nevt;
+  const int64_t ievt = active ? ievt_raw : nevt - 1;
+
+  // --- per-event set-up, as in me_kernel
+  double pd[P::NPAR][4];
+  {
+    const double2* src = reinterpret_cast<const double2*>(a.mom + ievt * (P::NPAR * 4));
+#pragma unroll
+    for (int i = 0; i < P::NPAR; ++i) {
+      const double2 v0 = __ldg(src + 2 * i), v1 = __ldg(src + 2 * i + 1);
+      pd[i][0] = v0.x; pd[i][1] = v0.y; pd[i][2] = v1.x; pd[i][3] = v1.y;
+    }
+  }
   const double kappa = P::template precompute<BLOCK * 4, R>(pd, a.mt, a.wt, a.zwt, v_dg, v_dt, kt);
   if (active && a.rescue_list && kappa > a.rescue_kappa) {
     const int slot = atomicAdd(a.rescue_count, 1);
@@ -115,8 +125,6 @@ __global__ void __launch_bounds__(128) me_kernel_mixed(const MeLaunch a) {
 
   // --- helicity loop
   double total = 0.0;
-  uint32_t phase = 0;
-  bool failed = false;
   for (int ih = 0; ih < a.ngood; ++ih) {
     const int h = a.good[ih];
     one_helicity<P, R, L, false>(h, R(a.mt), s_dg + tid, s_dt + tid, s_J + tid, s_w + tid, nullptr, 0, ws, kt, want_w);
@@ -188,21 +196,10 @@ __global__ void __launch_bounds__(128) me_kernel_mixed(const MeLaunch a) {
     }
     const double mh = double(cs) * gfac;
     total += mh;
-    if (a.cum && active) a.cum[ih * nevt + ievt] = a.cum_mode ? mh : total;
+    if (a.cum) a.cum[ih * wstride + wrow] = a.cum_mode ? mh : total;
   }
 
-  // --- teardown: no MMA may still be in flight when the columns are freed
-  if (failed) {
-    if (tid == 0 && a.err) atomicOr(a.err, 1);
-    tc::mbar_wait_bounded(s_mbar, phase ^ 1u, kMmaWaitLimit);
-  }
-  tc::fence_before_sync();
-  __syncthreads();
-  if (warp == 0) {
-    tc::fence_after_sync();
-    tc::tmem_dealloc(tbase, S::TCOLS);
-  }
-  if (!active) return;
+  if (!active) continue;
   a.me[ievt] = failed ? __longlong_as_double(0x7ff8000000000000ll) : total / double(P::IDEN);
   if (a.sel_hel && a.cum && !a.cum_mode) {
     int sel = 0;
@@ -211,7 +208,7 @@ __global__ void __launch_bounds__(128) me_kernel_mixed(const MeLaunch a) {
       int found = -1, lastnz = -1;
       double prev = 0.0;
       for (int ih = 0; ih < a.ngood; ++ih) {
-        const double c = a.cum[ih * nevt + ievt];
+        const double c = a.cum[ih * wstride + wrow];
         if (c > prev) lastnz = ih;
         if (c > target) { found = ih; break; }
         prev = c;
@@ -241,6 +238,27 @@ __global__ void __launch_bounds__(128) me_kernel_mixed(const MeLaunch a) {
     }
     a.sel_col[ievt] = sel;
   }
+  }  // tile loop
+
+  // --- teardown: no MMA may still be in flight when the columns are freed
+  if (failed) {
+    if (tid == 0 && a.err) atomicOr(a.err, 1);
+    tc::mbar_wait_bounded(s_mbar, phase ^ 1u, kMmaWaitLimit);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tbase, S::TCOLS);
+  }
+}
+
+template <class P, class L, int NTERM>
+LaunchNeeds needs_mixed_of() {
+  static const int bps = resident_blocks(me_kernel_mixed<P, L, NTERM>, 128, me_mixed_smem_bytes<P, L, NTERM>());
+  LaunchNeeds n = sizes_of<P, float, L>();
+  n.blocks_per_sm = bps;
+  return n;
 }
 
 template <class P, class L, int NTERM>
@@ -250,8 +268,8 @@ cudaError_t launch_mixed(const MeLaunch& a, cudaStream_t s) {
   auto k = me_kernel_mixed<P, L, NTERM>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
-  const int64_t nblk = (a.nevt + 127) / 128;
-  k<<<dim3(unsigned(nblk)), dim3(128), smem, s>>>(a);
+  if (a.grid_blocks <= 0) return cudaErrorInvalidConfiguration;  // the caller sizes the persistent grid
+  k<<<dim3(unsigned(a.grid_blocks)), dim3(128), smem, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -19,6 +19,7 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "helas.cuh"
@@ -44,10 +45,14 @@ struct MeLaunch {
   int ngood;
   int cum_mode;      // 0: cum holds running sums; 1: cum holds each |M_h|^2 (filter pass)
   uint8_t good[MAX_COMB];
-  double* cum;       // workspace [ngood][nevt]
-  double* colw;      // workspace [ncol][nevt] (when the colour weights live in global memory)
-  void* slots;       // workspace [block][nslot][BLOCK][4] complex (slot buffer in global memory)
-  void* ktab;        // workspace [block][nkvec][BLOCK][4] real (momentum table in global memory)
+  // Workspace.  The grid is persistent (at most the blocks that are resident at once);
+  // each thread walks the batch and owns one workspace row, row = blockIdx.x * BLOCK +
+  // threadIdx.x of gridDim.x * BLOCK rows, so the workspace scales with the resident
+  // threads, not with the batch.
+  double* cum;       // [ngood][rows]
+  double* colw;      // [ncol][rows] (when the colour weights live in global memory)
+  void* slots;       // [block][nslot][BLOCK][4] complex (slot buffer in global memory)
+  void* ktab;        // [block][nkvec][BLOCK][4] real (momentum table in global memory)
   int* err;          // set to 1 when a bounded device-side wait runs out (mapped host memory)
   // precision rescue (FP32 and mixed passes): events whose conditioning kappa exceeds
   // rescue_kappa are appended, as ibase + local index, to rescue_list (capacity
@@ -57,13 +62,12 @@ struct MeLaunch {
   int* rescue_list;
   int rescue_cap;
   int64_t ibase;
-  // indexed mode (the FP64 rescue pass): process events index[0 .. *index_count) in a
-  // grid-stride loop over grid_blocks blocks; workspace rows (cum, colw) are the
-  // positions in the list, with row stride index_cap
+  // indexed mode (the FP64 rescue pass): process events index[0 .. min(*index_count,
+  // index_cap)) instead of 0 .. nevt
   const int* index;
   const int* index_count;
   int index_cap;
-  int grid_blocks;
+  int grid_blocks;   // blocks of the launch (persistent grid)
 };
 
 // view of an array laid out [index][S]
@@ -81,10 +85,11 @@ struct Strided {
 //   W_MODE   colour weights: 0 registers, 1 shared memory, 2 global workspace
 //   S_MODE   slot buffer: 0 none, 1 shared memory, 2 global workspace
 //   K_MODE   momentum table: 1 shared memory, 2 global workspace
-template <int V_, int BLOCK_, bool DEN_SMEM, bool J_SMEM, int W_MODE, int S_MODE, int K_MODE>
+//   SYNC     a block barrier at the top of every helicity
+template <int V_, int BLOCK_, bool DEN_SMEM, bool J_SMEM, int W_MODE, int S_MODE, int K_MODE, bool SYNC = false>
 struct Layout {
   static constexpr int V = V_, BLOCK = BLOCK_;
-  static constexpr bool den_smem = DEN_SMEM, j_smem = J_SMEM;
+  static constexpr bool den_smem = DEN_SMEM, j_smem = J_SMEM, sync = SYNC;
   static constexpr int w_mode = W_MODE, s_mode = S_MODE, k_mode = K_MODE;
 };
 
@@ -103,10 +108,10 @@ template <class P, class L, class R, class DG, class DT, class JA>
 __device__ __forceinline__ void call_jamps(int h, const MeLaunch& a, const DG& dg, const DT& dt, JA& J, cx<R>* ws,
                                            const R* kt) {
   if constexpr (P::QCD) {
-    P::template jamps<L::V, L::BLOCK * 4, R>(h, R(a.mt), dg, dt, J, ws, kt);
+    P::template jamps<L::V, L::BLOCK * 4, R, L::sync>(h, R(a.mt), dg, dt, J, ws, kt);
   } else {
     const R zc[2] = {R(a.zc[0]), R(a.zc[1])};
-    P::template jamps<L::V, L::BLOCK * 4, R>(h, zc, dg, dt, J, ws, kt);
+    P::template jamps<L::V, L::BLOCK * 4, R, L::sync>(h, zc, dg, dt, J, ws, kt);
   }
 }
 
@@ -137,7 +142,7 @@ __device__ __noinline__ R one_helicity(int h, R mt, R* s_dg_t, cx<R>* s_dt_t, cx
   if constexpr (L::j_smem) {
     Strided<cx<R>, BLOCK> J{s_J_t};
     for (int c = 0; c < P::NCOL; ++c) J[c] = mk<R>(R(0), R(0));
-    P::template jamps<L::V, BLOCK * 4, R>(h, mt, dg, dt, J, ws, kt);
+    P::template jamps<L::V, BLOCK * 4, R, L::sync>(h, mt, dg, dt, J, ws, kt);
     cs = COLOUR ? colour_sum_strided<P, R, BLOCK>(s_J_t) : R(0);
     if (want_w)
       for (int c = 0; c < P::NCOL; ++c) weights(J[c], c);
@@ -145,7 +150,7 @@ __device__ __noinline__ R one_helicity(int h, R mt, R* s_dg_t, cx<R>* s_dt_t, cx
     cx<R> J[P::NCOL];
 #pragma unroll
     for (int c = 0; c < P::NCOL; ++c) J[c] = mk<R>(R(0), R(0));
-    P::template jamps<L::V, BLOCK * 4, R>(h, mt, dg, dt, J, ws, kt);
+    P::template jamps<L::V, BLOCK * 4, R, L::sync>(h, mt, dg, dt, J, ws, kt);
     cs = P::template colour_sum<R>(J);
     if (want_w) {
 #pragma unroll
@@ -160,15 +165,18 @@ __global__ void __launch_bounds__(L::BLOCK) me_kernel(const MeLaunch a) {
   constexpr int BLOCK = L::BLOCK;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int tid = threadIdx.x;
-  const int64_t nevt = a.nevt;
-  const int64_t count = a.index ? int64_t(*a.index_count < a.index_cap ? *a.index_count : a.index_cap) : nevt;
-  const int64_t step = a.index ? int64_t(gridDim.x) * BLOCK : nevt;
-  // one event per thread, or a grid-stride walk over an index list (no block-wide
-  // barrier below, so threads leave independently)
-  for (int64_t pos = int64_t(blockIdx.x) * BLOCK + tid; pos < count; pos += step) {
-  const int64_t ievt = a.index ? int64_t(a.index[pos]) : pos;
-  const int64_t wrow = a.index ? pos : ievt;              // workspace row
-  const int64_t wstride = a.index ? int64_t(a.index_cap) : nevt;
+  const int64_t count = a.index ? int64_t(*a.index_count < a.index_cap ? *a.index_count : a.index_cap) : a.nevt;
+  const int64_t ntile = (count + BLOCK - 1) / BLOCK;
+  const int64_t wrow = int64_t(blockIdx.x) * BLOCK + tid;  // this thread's workspace row
+  const int64_t wstride = int64_t(gridDim.x) * BLOCK;
+  // The persistent grid walks the batch one tile of BLOCK events at a time.  The tile
+  // loop is uniform over the block: a thread past the end of the batch mirrors its last
+  // event and writes nothing, so every thread reaches every block barrier.
+  for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+  const int64_t pos = tile * BLOCK + tid;
+  const bool active = pos < count;
+  const int64_t ipos = active ? pos : count - 1;
+  const int64_t ievt = a.index ? int64_t(a.index[ipos]) : ipos;
 
   // 1. momenta
   double pd[P::NPAR][4];
@@ -232,7 +240,7 @@ __global__ void __launch_bounds__(L::BLOCK) me_kernel(const MeLaunch a) {
     else kappa = P::template precompute<BLOCK * 4, R>(pd, a.zc[2], a.zc[3], 0, r_dg, r_dt, kt);
     gfac = a.coup / double(P::COL_DEN);
   }
-  if (a.rescue_list && kappa > a.rescue_kappa) {
+  if (active && a.rescue_list && kappa > a.rescue_kappa) {
     const int slot = atomicAdd(a.rescue_count, 1);
     if (slot < a.rescue_cap) a.rescue_list[slot] = int(a.ibase + ievt);
   }
@@ -257,6 +265,9 @@ __global__ void __launch_bounds__(L::BLOCK) me_kernel(const MeLaunch a) {
 #pragma unroll 1
   for (int ih = 0; ih < a.ngood; ++ih) {
     const int h = a.good[ih];
+    // keep the block's warps on the same stretch of the (very long, straight-line)
+    // helicity body, so that instruction fetches are shared instead of thrashing
+    if constexpr (L::sync) __syncthreads();
     R cs;
     if constexpr (P::QCD && L::den_smem && L::w_mode != 0) {
       cs = one_helicity<P, R, L>(h, R(a.mt), s_dg + tid, s_dt + tid, L::j_smem ? s_J + tid : nullptr,
@@ -300,6 +311,7 @@ __global__ void __launch_bounds__(L::BLOCK) me_kernel(const MeLaunch a) {
   }
 
   // 4. outputs
+  if (!active) continue;
   a.me[ievt] = total / double(P::IDEN);
   if (a.sel_hel && a.cum && !a.cum_mode) {
     int sel = 0;
@@ -345,7 +357,7 @@ __global__ void __launch_bounds__(L::BLOCK) me_kernel(const MeLaunch a) {
     }
     a.sel_col[ievt] = sel;
   }
-  }  // event loop
+  }  // tile loop
 }
 
 // ---------------------------------------------------------------------------
@@ -353,10 +365,11 @@ __global__ void __launch_bounds__(L::BLOCK) me_kernel(const MeLaunch a) {
 // ---------------------------------------------------------------------------
 // Workspace a launch needs beyond the caller's arrays, in bytes per event.
 struct LaunchNeeds {
-  size_t slot_bytes_per_event;  // global slot buffer
-  size_t ktab_bytes_per_event;  // global momentum table
-  bool colw_global;             // colour weights in a global [ncol][nevt] array
+  size_t slot_bytes_per_event;  // global slot buffer, per workspace row
+  size_t ktab_bytes_per_event;  // global momentum table, per workspace row
+  bool colw_global;             // colour weights in a global [ncol][rows] array
   int block;                    // threads per block (global tiles cover whole blocks)
+  int blocks_per_sm;            // resident blocks per SM (occupancy of the kernel)
 };
 
 struct ProcessOps {
@@ -369,13 +382,56 @@ struct ProcessOps {
   cudaError_t (*launch)(int prec, int config, const MeLaunch& a, cudaStream_t s);
 };
 
+// Resident blocks per SM of a kernel with 'threads' threads and 'smem' bytes of dynamic
+// shared memory, at least 1: the tightest of the register file (registers are granted
+// per warp in units of 256), shared memory (plus the per-block reservation), threads
+// and blocks per SM.  The kernel's shared-memory carveout is set to what that many
+// blocks need, so the hardware can place them all.
+template <class K>
+int resident_blocks(K k, int threads, size_t smem) {
+  int dev = 0, regs_sm = 0, smem_sm = 0, smem_res = 0, thr_sm = 0, blk_sm = 0;
+  cudaFuncAttributes fa{};
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaFuncGetAttributes(&fa, k) != cudaSuccess ||
+      cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&smem_res, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&blk_sm, cudaDevAttrMaxBlocksPerMultiprocessor, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  const int warps = (threads + 31) / 32;
+  const int regs_warp = (fa.numRegs * 32 + 255) / 256 * 256;
+  int b = blk_sm;
+  if (regs_warp > 0) b = std::min(b, regs_sm / (warps * regs_warp));
+  const size_t per_block = smem + fa.sharedSizeBytes + size_t(smem_res);
+  if (per_block > 0) b = std::min<int>(b, int(size_t(smem_sm) / per_block));
+  b = std::min(b, thr_sm / threads);
+  b = std::max(b, 1);
+  if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  const int pct = int((size_t(b) * per_block * 100 + size_t(smem_sm) - 1) / size_t(smem_sm));
+  cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, std::min(100, pct));
+  cudaGetLastError();
+  return b;
+}
+
+// workspace sizes of a layout (everything but the occupancy)
 template <class P, class R, class L>
-LaunchNeeds needs_of() {
+LaunchNeeds sizes_of() {
   LaunchNeeds n;
   n.slot_bytes_per_event = L::s_mode == 2 ? size_t(P::template nslot<L::V>()) * 4 * sizeof(cx<R>) : 0;
   n.ktab_bytes_per_event = L::k_mode == 2 ? size_t(P::NKVEC) * 4 * sizeof(R) : 0;
   n.colw_global = L::w_mode == 2;
   n.block = L::BLOCK;
+  n.blocks_per_sm = 1;
+  return n;
+}
+
+template <class P, class R, class L>
+LaunchNeeds needs_of() {
+  static const int bps = resident_blocks(me_kernel<P, R, L>, L::BLOCK, me_smem_bytes<P, R, L>());
+  LaunchNeeds n = sizes_of<P, R, L>();
+  n.blocks_per_sm = bps;
   return n;
 }
 
@@ -388,8 +444,8 @@ cudaError_t launch_me(const MeLaunch& a, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
   }
-  const int64_t nblk = a.grid_blocks > 0 ? a.grid_blocks : (a.nevt + L::BLOCK - 1) / L::BLOCK;
-  k<<<dim3(unsigned(nblk)), dim3(L::BLOCK), smem, s>>>(a);
+  if (a.grid_blocks <= 0) return cudaErrorInvalidConfiguration;  // the caller sizes the persistent grid
+  k<<<dim3(unsigned(a.grid_blocks)), dim3(L::BLOCK), smem, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -39,9 +39,8 @@ const ProcessOps* const kProcs[] = {&ops_eemumu, &ops_ggtt, &ops_ggttg, &ops_ggt
 thread_local std::string g_init_error;
 
 
-// events per launch when the slot buffer lives in global memory (bounds the workspace
-// and keeps 32-bit slot offsets)
-constexpr int64_t kGlobalSlotChunk = 65536;
+// events per launch: the rescue list holds 32-bit event indices
+constexpr int64_t kMaxChunk = int64_t(1) << 30;
 
 }  // namespace
 
@@ -181,20 +180,28 @@ int get_workspace(me_handle* h, uintptr_t key, cudaStream_t s, size_t bytes, voi
 }
 
 
-Carve carve(const ProcessOps* ops, const LaunchNeeds& nd, int ngood, int64_t chunk, bool want_hel, bool want_col) {
+Carve carve(const ProcessOps* ops, const LaunchNeeds& nd, int ngood, int64_t rows, bool want_hel, bool want_col) {
   Carve c;
   auto up = [](size_t b) { return (b + 255) / 256 * 256; };
-  if (want_hel) c.cum = up(size_t(ngood) * chunk * sizeof(double));
-  if (want_col && nd.colw_global) c.colw = up(size_t(ops->ncol) * chunk * sizeof(double));
-  const int64_t padded = (chunk + nd.block - 1) / nd.block * nd.block;  // whole blocks
-  c.slots = up(nd.slot_bytes_per_event * padded);
-  c.ktab = up(nd.ktab_bytes_per_event * padded);
+  if (want_hel) c.cum = up(size_t(ngood) * rows * sizeof(double));
+  if (want_col && nd.colw_global) c.colw = up(size_t(ops->ncol) * rows * sizeof(double));
+  c.slots = up(nd.slot_bytes_per_event * rows);  // rows cover whole blocks
+  c.ktab = up(nd.ktab_bytes_per_event * rows);
   return c;
 }
 
-// Launch 'a' over nevt events in chunks, with workspace 'wsp' carved per 'cv'.
+// Blocks of the persistent grid for nevt events: no more than are resident at once.
+int persistent_grid(const me_handle* h, const LaunchNeeds& nd, int64_t nevt) {
+  const int64_t tiles = (std::max<int64_t>(nevt, 1) + nd.block - 1) / nd.block;
+  int64_t resident = int64_t(h->nsm) * nd.blocks_per_sm;
+  if (h->max_blocks > 0) resident = std::min<int64_t>(resident, h->max_blocks);
+  return int(std::max<int64_t>(1, std::min(tiles, resident)));
+}
+
+// Launch 'a' over nevt events in chunks, each on at most 'grid' blocks of 'block'
+// threads, with workspace 'wsp' carved per 'cv'.
 cudaError_t launch_chunks(const ProcessOps* ops, int prec, int config, MeLaunch a, int64_t nevt, int64_t chunk,
-                          const Carve& cv, void* wsp, cudaStream_t s) {
+                          int grid, int block, const Carve& cv, void* wsp, cudaStream_t s) {
   char* w = static_cast<char*>(wsp);
   double* cum = cv.cum ? reinterpret_cast<double*>(w) : a.cum;
   double* colw = cv.colw ? reinterpret_cast<double*>(w + cv.cum) : nullptr;
@@ -216,15 +223,14 @@ cudaError_t launch_chunks(const ProcessOps* ops, int prec, int config, MeLaunch 
     b.slots = slots;
     b.ktab = ktab;
     b.ibase = off;
+    b.grid_blocks = int(std::min<int64_t>(grid, (b.nevt + block - 1) / block));
     cudaError_t e = ops->launch(prec, config, b, s);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
 
-int64_t chunk_for(const LaunchNeeds& nd, int64_t nevt) {
-  return (nd.slot_bytes_per_event || nd.ktab_bytes_per_event) ? std::min<int64_t>(nevt, kGlobalSlotChunk) : nevt;
-}
+int64_t chunk_for(const LaunchNeeds&, int64_t nevt) { return std::min<int64_t>(nevt, kMaxChunk); }
 
 static size_t up256(size_t b) { return (b + 255) / 256 * 256; }
 
@@ -236,21 +242,23 @@ CallPlan plan_call(const me_handle* h, int64_t nevt, int64_t chunk, bool want_he
   cp.chunk = chunk;
   const int ngood = int(h->good.size());
   const LaunchNeeds nd = ops->needs(cp.prec, cp.config);
-  cp.main = carve(ops, nd, ngood, chunk, want_hel, want_col);
+  cp.grid = persistent_grid(h, nd, chunk);
+  cp.block = nd.block;
+  cp.main = carve(ops, nd, ngood, int64_t(cp.grid) * nd.block, want_hel, want_col);
   size_t off = cp.main.total();
   cp.rescue = (cp.prec == ME_PREC_FP32 || cp.prec == ME_PREC_MIXED) && h->par.rescue_kappa > 0;
   if (cp.rescue) {
     const LaunchNeeds n64 = ops->needs(ME_PREC_FP64, 0);
     const int64_t cap = std::min<int64_t>(nevt, std::max<int64_t>(1024, nevt / 16));
     cp.rescue_cap = int(cap);
-    cp.rescue_grid = int(std::min<int64_t>((cap + n64.block - 1) / n64.block, 1184));
-    const size_t tile_events = size_t(cp.rescue_grid) * n64.block;
+    cp.rescue_grid = persistent_grid(h, n64, cap);
+    const size_t rows = size_t(cp.rescue_grid) * n64.block;
     cp.off_count = off; off += 256;
     cp.off_list = off; off += up256(size_t(cap) * sizeof(int));
-    cp.off_cum = off; if (want_hel) off += up256(size_t(ngood) * cap * sizeof(double));
-    cp.off_colw = off; if (want_col && n64.colw_global) off += up256(size_t(ops->ncol) * cap * sizeof(double));
-    cp.off_slots = off; off += up256(n64.slot_bytes_per_event * tile_events);
-    cp.off_ktab = off; off += up256(n64.ktab_bytes_per_event * tile_events);
+    cp.off_cum = off; if (want_hel) off += up256(size_t(ngood) * rows * sizeof(double));
+    cp.off_colw = off; if (want_col && n64.colw_global) off += up256(size_t(ops->ncol) * rows * sizeof(double));
+    cp.off_slots = off; off += up256(n64.slot_bytes_per_event * rows);
+    cp.off_ktab = off; off += up256(n64.ktab_bytes_per_event * rows);
   }
   cp.total = off;
   return cp;
@@ -269,10 +277,9 @@ cudaError_t run_call(const me_handle* h, const CallPlan& cp, const MeLaunch& a0,
     a.rescue_list = reinterpret_cast<int*>(w + cp.off_list);
     a.rescue_cap = cp.rescue_cap;
   }
-  cudaError_t e = launch_chunks(ops, cp.prec, cp.config, a, nevt, cp.chunk, cp.main, wsp, s);
+  cudaError_t e = launch_chunks(ops, cp.prec, cp.config, a, nevt, cp.chunk, cp.grid, cp.block, cp.main, wsp, s);
   if (e != cudaSuccess || !cp.rescue) return e;
-  // FP64 pass over the flagged events, in place: same inputs and outputs, workspace
-  // rows indexed by list position
+  // FP64 pass over the flagged events, in place: same inputs and outputs
   MeLaunch b = a0;
   const bool want_col = a0.sel_col != nullptr;
   b.nevt = nevt;
@@ -328,6 +335,13 @@ int me_init(const char* process, const me_sm_params* p, me_handle** out) {
   me_handle* h = new me_handle();
   h->ops = ops;
   h->par = *p;
+  {
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+        nsm > 0)
+      h->nsm = nsm;
+    cudaGetLastError();
+  }
   if (cudaHostAlloc(reinterpret_cast<void**>(&h->err_host), sizeof(int), cudaHostAllocMapped) == cudaSuccess) {
     *h->err_host = 0;
     if (cudaHostGetDevicePointer(reinterpret_cast<void**>(&h->err_dev), h->err_host, 0) != cudaSuccess) h->err_dev = nullptr;
@@ -339,6 +353,7 @@ int me_init(const char* process, const me_sm_params* p, me_handle** out) {
     const int c = std::atoi(env);
     if (c >= 0 && c < ops->nconfig[p->precision]) h->config = c;
   }
+  if (const char* env = std::getenv("ME_B300_MAX_BLOCKS")) h->max_blocks = std::max(0, std::atoi(env));
   const double ee = std::sqrt(4.0 * M_PI * alpha);
   const double mw2 = mz2 / 2.0 + std::sqrt(disc);
   const double sw2 = 1.0 - mw2 / mz2, sw = std::sqrt(sw2), cw = std::sqrt(1.0 - sw2);
@@ -353,8 +368,8 @@ int me_init(const char* process, const me_sm_params* p, me_handle** out) {
   std::vector<double> mom(size_t(nf) * ops->npar * 4);
   rambo_sample(nf, 1500.0, final_masses(ops, p->mt), 12345, mom.data());
   const LaunchNeeds nd = ops->needs(ME_PREC_FP64, 0);
-  const int64_t chunk = chunk_for(nd, nf);
-  Carve cv = carve(ops, nd, 0, chunk, false, false);
+  const int fgrid = (nf + nd.block - 1) / nd.block;  // one event per thread: rows == events
+  Carve cv = carve(ops, nd, 0, int64_t(fgrid) * nd.block, false, false);
   double *d_mom = nullptr, *d_me = nullptr, *d_cum = nullptr;
   void* d_ws = nullptr;
   cudaError_t e = cudaMalloc(&d_mom, mom.size() * sizeof(double));
@@ -371,8 +386,9 @@ int me_init(const char* process, const me_sm_params* p, me_handle** out) {
     a.ngood = ops->ncomb;
     a.cum_mode = 1;
     for (int i = 0; i < ops->ncomb; ++i) a.good[i] = uint8_t(i);
-    a.cum = d_cum;  // one launch: the filter sample is smaller than any chunk
-    e = launch_chunks(ops, ME_PREC_FP64, 0, a, nf, nf, cv, d_ws, 0);
+    a.cum = d_cum;  // [ncomb][rows] with rows == nf: one tile per block, one event per thread
+    if (int64_t(fgrid) * nd.block != nf) e = cudaErrorInvalidConfiguration;
+    if (e == cudaSuccess) e = launch_chunks(ops, ME_PREC_FP64, 0, a, nf, nf, fgrid, nd.block, cv, d_ws, 0);
     if (e == cudaSuccess) e = cudaMemcpy(cum.data(), d_cum, cum.size() * sizeof(double), cudaMemcpyDeviceToHost);
   }
   cudaFree(d_mom);
@@ -445,7 +461,7 @@ int me_compute(me_handle* h, int64_t nevt, const double* momenta, const double* 
   if (!h) return fail(nullptr, ME_ERR_ARG, "me_compute: null handle");
   if (nevt < 0) return fail(h, ME_ERR_ARG, "me_compute: nevt < 0");
   if (nevt == 0) return ME_OK;
-  if (nevt > (int64_t(1) << 31) * 32) return fail(h, ME_ERR_ARG, "me_compute: nevt too large for one call");
+  if (nevt > INT32_MAX) return fail(h, ME_ERR_ARG, "me_compute: more than 2^31 - 1 events in one call");
   if (!momenta || !me) return fail(h, ME_ERR_ARG, "me_compute: momenta and me are required");
   if (reinterpret_cast<uintptr_t>(momenta) % 16) return fail(h, ME_ERR_ARG, "me_compute: momenta must be 16-byte aligned");
   if ((sel_hel && !rnd_hel) || (sel_col && !rnd_col))
@@ -463,6 +479,7 @@ int me_compute_host(me_handle* h, int64_t nevt, const double* momenta, const dou
   if (!h) return fail(nullptr, ME_ERR_ARG, "me_compute_host: null handle");
   if (nevt < 0) return fail(h, ME_ERR_ARG, "me_compute_host: nevt < 0");
   if (nevt == 0) return ME_OK;
+  if (nevt > INT32_MAX) return fail(h, ME_ERR_ARG, "me_compute_host: more than 2^31 - 1 events in one call");
   if (!momenta || !me) return fail(h, ME_ERR_ARG, "me_compute_host: momenta and me are required");
   if ((sel_hel && !rnd_hel) || (sel_col && !rnd_col))
     return fail(h, ME_ERR_ARG, "me_compute_host: a selection output needs its random numbers");
@@ -528,9 +545,19 @@ int me_plan(const me_handle* h, int64_t nevt, int64_t* launches, int64_t* worksp
   if (!h || nevt < 0) return ME_ERR_ARG;
   const LaunchNeeds nd = h->ops->needs(h->par.precision, h->config);
   const int64_t chunk = std::max<int64_t>(1, chunk_for(nd, nevt));
-  const CallPlan cp = plan_call(h, nevt, chunk, true, true);
+  const CallPlan cp = plan_call(h, std::max<int64_t>(nevt, 1), chunk, true, true);
   if (launches) *launches = nevt ? (nevt + chunk - 1) / chunk + (cp.rescue ? 1 : 0) : 0;
   if (workspace_bytes) *workspace_bytes = int64_t(cp.total);
+  return ME_OK;
+}
+
+int me_launch_shape(const me_handle* h, int64_t nevt, int* grid, int* block, int* blocks_per_sm, int* nsm) {
+  if (!h || nevt < 0) return ME_ERR_ARG;
+  const LaunchNeeds nd = h->ops->needs(h->par.precision, h->config);
+  if (grid) *grid = persistent_grid(h, nd, chunk_for(nd, std::max<int64_t>(nevt, 1)));
+  if (block) *block = nd.block;
+  if (blocks_per_sm) *blocks_per_sm = nd.blocks_per_sm;
+  if (nsm) *nsm = h->nsm;
   return ME_OK;
 }
 

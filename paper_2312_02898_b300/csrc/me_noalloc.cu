@@ -64,6 +64,7 @@ extern "C" int me_compute_noalloc(me_handle* h, int64_t nevt, const double* mome
   if (!h) return fail(nullptr, ME_ERR_ARG, "me_compute_noalloc: null handle");
   if (nevt < 0) return fail(h, ME_ERR_ARG, "me_compute_noalloc: nevt < 0");
   if (nevt == 0) return ME_OK;
+  if (nevt > INT32_MAX) return fail(h, ME_ERR_ARG, "me_compute_noalloc: more than 2^31 - 1 events in one call");
   if (!momenta || !me) return fail(h, ME_ERR_ARG, "me_compute_noalloc: momenta and me are required");
   if (reinterpret_cast<uintptr_t>(momenta) % 16)
     return fail(h, ME_ERR_ARG, "me_compute_noalloc: momenta must be 16-byte aligned");
@@ -80,8 +81,8 @@ extern "C" int me_compute_noalloc(me_handle* h, int64_t nevt, const double* mome
   const int ngood = int(h->good.size());
   const bool want_hel = sel_hel && rnd_hel;
   const bool want_col = sel_col && rnd_col;
-  // one main launch over every event (plus the FP64 rescue pass of the FP32 and mixed
-  // modes): the whole batch's scratch must fit the fixed array
+  // one persistent main launch (plus the FP64 rescue pass of the FP32 and mixed modes):
+  // its scratch, one row per resident thread, must fit the fixed array
   const CallPlan cp = plan_call(h, nevt, nevt, want_hel, want_col);
   if (cp.total > kScratchBytes) {
     const CallPlan one = plan_call(h, 1024, 1024, want_hel, want_col);

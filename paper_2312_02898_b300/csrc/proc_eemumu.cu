@@ -18,7 +18,7 @@ LaunchNeeds needs(int prec, int config) {
   switch (prec * 8 + config) {
     case 0: return needs_of<P, Cfg<0, 0>::R, Cfg<0, 0>::L>();
     case 8: return needs_of<P, Cfg<1, 0>::R, Cfg<1, 0>::L>();
-    default: return LaunchNeeds{0, 0, false, 128};
+    default: return LaunchNeeds{0, 0, false, 128, 1};
   }
 }
 

@@ -1,7 +1,8 @@
 // Kernel instantiations and launch table for the process in generated/proc_ggttgg.cuh.
 // Layout<jamps variant (register budget), threads per block, denominators in shared
 // memory, J in shared memory, colour weights (0 registers, 1 shared, 2 global),
-// slot buffer (0 none, 1 shared, 2 global), momentum table (1 shared, 2 global)>.
+// slot buffer (0 none, 1 shared, 2 global), momentum table (1 shared, 2 global),
+// block barriers in the helicity body (default none)>.
 // The first layout of each precision is the default; the others are alternatives for
 // tuning sweeps (me_set_config / ME_B300_CONFIG).
 #include "generated/proc_ggttgg.cuh"
@@ -12,34 +13,42 @@ namespace meb300 {
 namespace {
 using P = proc_ggttgg;
 template <int PREC, int C> struct Cfg;
-template <> struct Cfg<0, 0> { using R = double; using L = Layout<3, 64, true, true, 1, 2, 2>; };
-template <> struct Cfg<0, 1> { using R = double; using L = Layout<4, 64, true, true, 1, 2, 2>; };
-template <> struct Cfg<0, 2> { using R = double; using L = Layout<5, 64, true, true, 1, 2, 2>; };
-template <> struct Cfg<1, 0> { using R = float; using L = Layout<1, 64, true, false, 1, 1, 2>; };
-template <> struct Cfg<1, 1> { using R = float; using L = Layout<0, 128, true, false, 1, 0, 2>; };
-template <> struct Cfg<1, 2> { using R = float; using L = Layout<1, 128, true, false, 1, 2, 2>; };
-template <> struct Cfg<1, 3> { using R = float; using L = Layout<2, 128, true, false, 1, 2, 2>; };
+template <> struct Cfg<0, 0> { using R = double; using L = Layout<3, 64, true, true, 1, 2, 2, true>; };
+template <> struct Cfg<0, 1> { using R = double; using L = Layout<3, 64, true, true, 1, 2, 2>; };
+template <> struct Cfg<0, 2> { using R = double; using L = Layout<4, 64, true, true, 1, 2, 2>; };
+template <> struct Cfg<0, 3> { using R = double; using L = Layout<5, 64, true, true, 1, 2, 2>; };
+template <> struct Cfg<1, 0> { using R = float; using L = Layout<1, 64, true, false, 1, 1, 2, true>; };
+template <> struct Cfg<1, 1> { using R = float; using L = Layout<1, 128, true, false, 1, 1, 2, true>; };
+template <> struct Cfg<1, 2> { using R = float; using L = Layout<1, 64, true, false, 1, 1, 2>; };
+template <> struct Cfg<1, 3> { using R = float; using L = Layout<0, 128, true, false, 1, 0, 2>; };
+template <> struct Cfg<1, 4> { using R = float; using L = Layout<1, 128, true, false, 1, 2, 2>; };
+template <> struct Cfg<1, 5> { using R = float; using L = Layout<2, 128, true, false, 1, 2, 2>; };
 
 // mixed precision: amplitude layout (must use shared J and weights, 128 threads) and the
 // number of BF16 terms of the split colour-flow amplitudes
 template <int C> struct MixedCfg;
-template <> struct MixedCfg<0> { using L = Layout<1, 128, true, true, 1, 2, 2>; static constexpr int NTERM = 3; };
-template <> struct MixedCfg<1> { using L = Layout<1, 128, true, true, 1, 2, 2>; static constexpr int NTERM = 2; };
-template <> struct MixedCfg<2> { using L = Layout<2, 128, true, true, 1, 2, 2>; static constexpr int NTERM = 3; };
+template <> struct MixedCfg<0> { using L = Layout<1, 128, true, true, 1, 2, 2, true>; static constexpr int NTERM = 3; };
+template <> struct MixedCfg<1> { using L = Layout<1, 128, true, true, 1, 2, 2>; static constexpr int NTERM = 3; };
+template <> struct MixedCfg<2> { using L = Layout<1, 128, true, true, 1, 2, 2>; static constexpr int NTERM = 2; };
+template <> struct MixedCfg<3> { using L = Layout<2, 128, true, true, 1, 2, 2>; static constexpr int NTERM = 3; };
 
 LaunchNeeds needs(int prec, int config) {
   switch (prec * 8 + config) {
     case 0: return needs_of<P, Cfg<0, 0>::R, Cfg<0, 0>::L>();
     case 1: return needs_of<P, Cfg<0, 1>::R, Cfg<0, 1>::L>();
     case 2: return needs_of<P, Cfg<0, 2>::R, Cfg<0, 2>::L>();
+    case 3: return needs_of<P, Cfg<0, 3>::R, Cfg<0, 3>::L>();
     case 8: return needs_of<P, Cfg<1, 0>::R, Cfg<1, 0>::L>();
     case 9: return needs_of<P, Cfg<1, 1>::R, Cfg<1, 1>::L>();
     case 10: return needs_of<P, Cfg<1, 2>::R, Cfg<1, 2>::L>();
     case 11: return needs_of<P, Cfg<1, 3>::R, Cfg<1, 3>::L>();
-    case 16: return needs_of<P, float, MixedCfg<0>::L>();
-    case 17: return needs_of<P, float, MixedCfg<1>::L>();
-    case 18: return needs_of<P, float, MixedCfg<2>::L>();
-    default: return LaunchNeeds{0, 0, false, 128};
+    case 12: return needs_of<P, Cfg<1, 4>::R, Cfg<1, 4>::L>();
+    case 13: return needs_of<P, Cfg<1, 5>::R, Cfg<1, 5>::L>();
+    case 16: return needs_mixed_of<P, MixedCfg<0>::L, MixedCfg<0>::NTERM>();
+    case 17: return needs_mixed_of<P, MixedCfg<1>::L, MixedCfg<1>::NTERM>();
+    case 18: return needs_mixed_of<P, MixedCfg<2>::L, MixedCfg<2>::NTERM>();
+    case 19: return needs_mixed_of<P, MixedCfg<3>::L, MixedCfg<3>::NTERM>();
+    default: return LaunchNeeds{0, 0, false, 128, 1};
   }
 }
 
@@ -48,19 +57,23 @@ cudaError_t launch(int prec, int config, const MeLaunch& a, cudaStream_t s) {
     case 0: return launch_me<P, Cfg<0, 0>::R, Cfg<0, 0>::L>(a, s);
     case 1: return launch_me<P, Cfg<0, 1>::R, Cfg<0, 1>::L>(a, s);
     case 2: return launch_me<P, Cfg<0, 2>::R, Cfg<0, 2>::L>(a, s);
+    case 3: return launch_me<P, Cfg<0, 3>::R, Cfg<0, 3>::L>(a, s);
     case 8: return launch_me<P, Cfg<1, 0>::R, Cfg<1, 0>::L>(a, s);
     case 9: return launch_me<P, Cfg<1, 1>::R, Cfg<1, 1>::L>(a, s);
     case 10: return launch_me<P, Cfg<1, 2>::R, Cfg<1, 2>::L>(a, s);
     case 11: return launch_me<P, Cfg<1, 3>::R, Cfg<1, 3>::L>(a, s);
+    case 12: return launch_me<P, Cfg<1, 4>::R, Cfg<1, 4>::L>(a, s);
+    case 13: return launch_me<P, Cfg<1, 5>::R, Cfg<1, 5>::L>(a, s);
     case 16: return launch_mixed<P, MixedCfg<0>::L, MixedCfg<0>::NTERM>(a, s);
     case 17: return launch_mixed<P, MixedCfg<1>::L, MixedCfg<1>::NTERM>(a, s);
     case 18: return launch_mixed<P, MixedCfg<2>::L, MixedCfg<2>::NTERM>(a, s);
+    case 19: return launch_mixed<P, MixedCfg<3>::L, MixedCfg<3>::NTERM>(a, s);
     default: return cudaErrorNotSupported;
   }
 }
 }  // namespace
 
 extern const ProcessOps ops_ggttgg = {P::NAME, P::NPAR, P::NCOMB, P::NCOL, P::NDIAG, P::NAMP, P::IDEN,
-                                   P::FLOPS_AMP, P::FLOPS_COL, /*has_mixed=*/true, {3, 4, 3},
+                                   P::FLOPS_AMP, P::FLOPS_COL, /*has_mixed=*/true, {4, 6, 4},
                                    needs, launch};
 }  // namespace meb300

@@ -13,25 +13,31 @@ using P = proc_ggttggg;
 template <int PREC, int C> struct Cfg;
 template <> struct Cfg<0, 0> { using R = double; using L = Layout<0, 64, true, true, 2, 2, 2>; };
 template <> struct Cfg<1, 0> { using R = float; using L = Layout<0, 128, true, true, 2, 2, 2>; };
+template <> struct Cfg<0, 1> { using R = double; using L = Layout<0, 64, true, true, 2, 2, 2, true>; };
+template <> struct Cfg<1, 1> { using R = float; using L = Layout<0, 128, true, true, 2, 2, 2, true>; };
 
 LaunchNeeds needs(int prec, int config) {
   switch (prec * 8 + config) {
     case 0: return needs_of<P, Cfg<0, 0>::R, Cfg<0, 0>::L>();
+    case 1: return needs_of<P, Cfg<0, 1>::R, Cfg<0, 1>::L>();
     case 8: return needs_of<P, Cfg<1, 0>::R, Cfg<1, 0>::L>();
-    default: return LaunchNeeds{0, 0, false, 128};
+    case 9: return needs_of<P, Cfg<1, 1>::R, Cfg<1, 1>::L>();
+    default: return LaunchNeeds{0, 0, false, 128, 1};
   }
 }
 
 cudaError_t launch(int prec, int config, const MeLaunch& a, cudaStream_t s) {
   switch (prec * 8 + config) {
     case 0: return launch_me<P, Cfg<0, 0>::R, Cfg<0, 0>::L>(a, s);
+    case 1: return launch_me<P, Cfg<0, 1>::R, Cfg<0, 1>::L>(a, s);
     case 8: return launch_me<P, Cfg<1, 0>::R, Cfg<1, 0>::L>(a, s);
+    case 9: return launch_me<P, Cfg<1, 1>::R, Cfg<1, 1>::L>(a, s);
     default: return cudaErrorNotSupported;
   }
 }
 }  // namespace
 
 extern const ProcessOps ops_ggttggg = {P::NAME, P::NPAR, P::NCOMB, P::NCOL, P::NDIAG, P::NAMP, P::IDEN,
-                                   P::FLOPS_AMP, P::FLOPS_COL, /*has_mixed=*/false, {1, 1, 0},
+                                   P::FLOPS_AMP, P::FLOPS_COL, /*has_mixed=*/false, {2, 2, 0},
                                    needs, launch};
 }  // namespace meb300

@@ -270,3 +270,26 @@ def test_full_size_sampled(process, nevt, precision, alphas):
     rel = np.abs(me[idx] / ref["me"] - 1)
     assert rel.max() <= {"fp64": 1e-12, "fp32": FP32_BOUND, "mixed": MIXED_BOUND}[precision]
     assert np.mean(sh[idx] == ref["sel_hel"]) >= 0.95
+
+
+@pytest.mark.parametrize("process", ACTIVE)
+def test_persistent_grid_walks_many_tiles_per_block(process, monkeypatch):
+    """A grid of 3 blocks walks the whole batch tile by tile, with a ragged last tile
+    whose idle threads still take part in every block barrier: every configuration of
+    every precision gives the oracle's results."""
+    monkeypatch.setenv("ME_B300_MAX_BLOCKS", "3")
+    mom, a, rh, rc, ref = reference(process, NEV[process])
+    for prec in ("fp64", "fp32", "mixed"):
+        if prec == "mixed" and process not in MIXED:
+            continue
+        m = mk(process, prec)
+        bound = 1e-12 if prec == "fp64" else FP32_BOUND
+        for config in range(m.nconfig):
+            m.set_config(config)
+            me, sh, sc = run_gpu(m, mom, a, rh, rc)
+            rel = np.abs(me / ref["me"] - 1)
+            assert rel.max() <= bound, (prec, config, rel.max())
+            if prec == "fp64":
+                assert boundary_ok(sh, ref["sel_hel"], ref["me_hel"], rh, 1e-10)[0]
+                assert boundary_ok(sc, ref["sel_col"], ref["colw"], rc, 1e-10)[0]
+        m.close()
