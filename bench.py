@@ -12,6 +12,7 @@ oracle at 1e-12).
     python bench.py [--gpus N] [--steps K] [--warmup W] [--mode fp64|fp32|mixed]
     python bench.py --impl reference      # the FP64 CPU oracle on the host cores
     python bench.py --serving             # the request stream: p50/p99 latency, sustained ME/s
+    python bench.py --processes           # ME/s of every process and precision
 
 Multi-GPU: every rank evaluates its own batch (disjoint event indices); the timed
 region is bracketed by barriers and the maximum over ranks is taken.  No data-path
@@ -147,11 +148,11 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def time_mode(mode, dev_inputs, host_inputs, steps, warmup, dist):
+def time_mode(mode, dev_inputs, host_inputs, steps, warmup, dist, process=None, e2e=True):
     """device-resident timing and end-to-end timing of one precision mode"""
     import torch
     from paper_2312_02898_b300.binding import MatrixElement
-    m = MatrixElement(PROCESS, precision=mode)
+    m = MatrixElement(process or PROCESS, precision=mode)
     mom, a, rh, rc = dev_inputs
     nevt = mom.shape[0]
     out = (torch.empty(nevt, dtype=torch.float64, device=mom.device),
@@ -176,6 +177,10 @@ def time_mode(mode, dev_inputs, host_inputs, steps, warmup, dist):
         dist.barrier()
     ms = max_over_ranks(e0.elapsed_time(e1) / steps, dist, mom.device)
     launches, ws_bytes = m.plan(nevt)
+    res = {"ms": ms, "launches": launches, "workspace_bytes": ws_bytes, "clocks": clk.summary(),
+           "flops_per_event": m.flops_per_event(), "ngood": m.ngood, "me": out[0], "sel": (out[1], out[2])}
+    if not e2e:
+        return res
     # end to end through the host entry point: pinned host inputs, copies inside
     hmom, ha, hrh, hrc = host_inputs
     hout = (torch.empty(nevt, dtype=torch.float64).pin_memory(), torch.empty(nevt, dtype=torch.int32).pin_memory(),
@@ -186,19 +191,49 @@ def time_mode(mode, dev_inputs, host_inputs, steps, warmup, dist):
     t0 = time.perf_counter()
     for _ in range(steps):
         m.compute_host(hmom, ha, hrh, hrc, out=hout, stream=stream)
-    e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / steps, dist, mom.device)
-    return {"ms": ms, "launches": launches, "workspace_bytes": ws_bytes, "clocks": clk.summary(),
-            "flops_per_event": m.flops_per_event(), "ngood": m.ngood, "e2e_ms": e2e_ms, "me": out[0],
-            "sel": (out[1], out[2])}
+    res["e2e_ms"] = max_over_ranks((time.perf_counter() - t0) * 1e3 / steps, dist, mom.device)
+    return res
 
 
-def accuracy_sample(mode_out, host_inputs, n=48):
+def time_unweight(me, warmup, reps):
+    """GPU-assisted batch unweighting of the step's matrix elements: the whole batch and
+    the 16384-event batches madevent uses (Section 3, Table 2); time per call on the
+    device and the achieved bandwidth of the 33 algorithmic bytes per event (read me,
+    weight, random number; write weight and decision)"""
+    import torch
+    from paper_2312_02898_b300.binding import MatrixElement
+    from paper_2312_02898_b300.phasespace import uniforms
+    m = MatrixElement(PROCESS, precision="fp64")
+    n = me.shape[0]
+    u = torch.from_numpy(uniforms(7, np.arange(n, dtype=np.uint64), 0, 2)).cuda()
+    wgt, rnd = u[:, 0].contiguous(), u[:, 1].contiguous()
+    out = {}
+    for size in (n, 16384):
+        args = (me[:size], wgt[:size], rnd[:size])
+        for _ in range(warmup):
+            m.unweight(*args)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            r = m.unweight(*args)
+        e1.record()
+        torch.cuda.synchronize()
+        us = e0.elapsed_time(e1) * 1e3 / reps
+        out[str(size)] = {"us_per_call": us, "gb_per_s": 33 * size / (us * 1e-6) / 1e9,
+                          "accepted": int(r[3].item()), "launches_per_call": 2}
+    m.close()
+    out["note"] = "inputs resident (L2-sized); bound by launch latency at madevent's batch size"
+    return out
+
+
+def accuracy_sample(mode_out, host_inputs, n=48, process=None):
     """max / median relative error of a mode against the FP64 oracle on sampled events"""
     import oracle
     hmom, ha, hrh, hrc = (x.numpy() for x in host_inputs)
     nevt = hmom.shape[0]
     idx = np.unique(np.linspace(0, nevt - 1, n).astype(np.int64))
-    ref = oracle.me(PROCESS, hmom[idx], alphas=ha[idx])["me"]
+    ref = oracle.me(process or PROCESS, hmom[idx], alphas=ha[idx])["me"]
     got = mode_out.cpu().numpy()[idx]
     rel = np.abs(got / ref - 1)
     return float(rel.max()), float(np.median(rel)), len(idx)
@@ -233,6 +268,7 @@ def run_gpu(args):
     if "error" in head:
         raise SystemExit(f"headline mode {args.mode} failed: {head['error']}")
     value = world * NEVT / (head["ms"] * 1e-3)
+    unw = time_unweight(head["me"], args.warmup, max(args.steps, 10))
     peaks = {p: binding.alu_peak(p, 0.3) for p in ("fp64", "fp32")}
     per_launch_ms = head["ms"] / head["launches"]
     events_per_launch = NEVT / head["launches"]
@@ -275,12 +311,61 @@ def run_gpu(args):
                              "peak_source": f"measured {peak_key.upper()} FMA probe (me_probe_alu_peak) in this run",
                              "flops_per_event": head["flops_per_event"], "kernel": "me_kernel (amplitudes + colour sum)"},
                 "modes": acc,
+                "unweight": unw,
                 "cpu_baseline": cpu,
                 "alu_peaks_tflops": {k: v / 1e12 for k, v in peaks.items()}}
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+
+
+# the per-process workloads: (process, events, alpha_s)
+PROCESS_TABLE = (("e+ e- > mu+ mu-", 16384, None), ("g g > t t~", 524288, 0.118), ("g g > t t~ g", 524288, 0.118),
+                 ("g g > t t~ g g", 1048576, "uniform"), ("g g > t t~ g g g", 262144, 0.118))
+
+
+def run_processes(args):
+    """ME/s of every process and precision at its own workload size, with the achieved
+    fraction of the measured FP64 / FP32 FMA peak and the error against the oracle on
+    sampled events (one JSON line)."""
+    import torch
+    from paper_2312_02898_b300 import binding
+    from paper_2312_02898_b300 import phasespace as ps
+    torch.cuda.set_device(0)
+    peaks = {p: binding.alu_peak(p, 0.3) for p in ("fp64", "fp32")}
+    table = {}
+    for process, nevt, alphas in PROCESS_TABLE:
+        if args.only_process and args.only_process not in process:
+            continue
+        mom, a, rh, rc = ps.make_batch(process, nevt, seed=0, alphas=alphas)
+        if a is None:
+            a = np.full(nevt, 0.118)
+        host = [torch.from_numpy(x).pin_memory() for x in (mom, a, rh, rc)]
+        dev = [x.cuda(non_blocking=True) for x in host]
+        torch.cuda.synchronize()
+        row = {"events": nevt, "input_mb": round(sum(x.numel() * x.element_size() for x in host) / 1e6, 1)}
+        for mode in ("fp64", "fp32", "mixed"):
+            try:
+                r = time_mode(mode, dev, host, args.steps, args.warmup, None, process=process, e2e=False)
+            except binding.MEError as e:
+                row[mode] = {"unavailable": str(e)}
+                continue
+            mx, med, ns = accuracy_sample(r["me"], host, n=24, process=process)
+            tf = r["flops_per_event"] * nevt / (r["ms"] * 1e-3) / 1e12
+            pk = peaks["fp64" if mode == "fp64" else "fp32"] / 1e12
+            row[mode] = {"me_per_s": nevt / (r["ms"] * 1e-3), "ms_per_step": r["ms"], "tflops": tf,
+                         "frac_of_measured_peak": tf / pk, "launches_per_step": r["launches"],
+                         "max_rel_err": mx, "median_rel_err": med, "err_sample": ns, "clocks": r["clocks"]}
+            del r
+        table[process] = row
+        del dev, host
+        torch.cuda.synchronize()
+    line = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "data": "synthetic (RAMBO, Philox4x32-10 seed 0)",
+            "config": {"workload": "every process at its own batch size, inputs resident, both selections"},
+            "alu_peaks_tflops": {k: v / 1e12 for k, v in peaks.items()}, "processes": table}
+    print(json.dumps(line), flush=True)
 
 
 def _gen_request(item):
@@ -361,10 +446,14 @@ def main():
     ap.add_argument("--serving-precisions", default="mixed,fp64")
     ap.add_argument("--nevt", type=int, default=NEVT,
                     help="events per GPU per step (a smaller case for profiling; the workload is 1048576)")
+    ap.add_argument("--processes", action="store_true", help="per-process ME/s table instead of the step")
+    ap.add_argument("--only-process", default="", help="with --processes: only processes containing this")
     args = ap.parse_args()
     globals()["NEVT"] = args.nevt
     if args.serving:
         return run_serving(args)
+    if args.processes:
+        return run_processes(args)
     if args.warmup < 3:
         raise SystemExit("at least 3 warm-up steps")
     if args.impl == "reference":
