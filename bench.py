@@ -400,13 +400,17 @@ def run_serving(args):
                 for b in serving.BUCKETS:
                     server.warm(p, b)
             warm_s = time.perf_counter() - t0
-            cap = serving.run_saturated(server, reqs[: args.serving_warmup + args.serving_requests // 4])
+            first = not out
+            ncap = args.serving_warmup + (args.serving_requests // 4 if first else args.serving_requests_other // 4)
+            cap = serving.run_saturated(server, reqs[:ncap])
             res = {"capacity_me_per_s": cap, "graphs": len(server.buffers), "warm_s": warm_s,
                    "precision_per_process": server.precision, "load": {}}
-            loads = [float(x) for x in args.serving_loads.split(",")] if not out else [0.7]
+            loads = [float(x) for x in args.serving_loads.split(",")] if first else [0.7]
+            # the slower precisions replay a prefix of the same stream
+            sub = reqs if first else reqs[: args.serving_warmup + args.serving_requests_other]
             for frac in loads:
                 rate = frac * cap / mean_events                   # requests per second
-                st = serving.run_open_loop(server, reqs, rate_scale=rate, warmup=args.serving_warmup)
+                st = serving.run_open_loop(server, sub, rate_scale=rate, warmup=args.serving_warmup)
                 st["offered_requests_per_s"] = rate
                 st["offered_me_per_s"] = frac * cap
                 res["load"][f"{int(round(frac * 100))}%"] = st
@@ -440,6 +444,8 @@ def main():
     ap.add_argument("--serving", action="store_true", help="run the serving stream instead of the throughput step")
     ap.add_argument("--serving-requests", type=int, default=2000)
     ap.add_argument("--serving-warmup", type=int, default=200)
+    ap.add_argument("--serving-requests-other", type=int, default=300,
+                    help="requests of the stream replayed for the precisions after the first")
     ap.add_argument("--serving-slots", type=int, default=4)
     ap.add_argument("--serving-loads", default="0.5,0.7,0.9,1.1",
                     help="offered load as fractions of capacity (first precision; the others run at 0.7)")

@@ -51,9 +51,10 @@ struct CallPlan {
   int prec = 0, config = 0;
   int64_t chunk = 0;
   int grid = 0, block = 0;  // persistent grid of the main pass
+  int hsplit = 1;           // threads per event of the main pass (helicity split)
   Carve main;
   bool rescue = false;
-  int rescue_cap = 0, rescue_grid = 0;
+  int rescue_cap = 0, rescue_grid = 0, rescue_hsplit = 1;
   size_t off_count = 0, off_list = 0, off_cum = 0, off_colw = 0, off_slots = 0, off_ktab = 0;
   size_t total = 0;
 };
@@ -65,7 +66,7 @@ bool is_device_ptr(const void* p);
 Carve carve(const ProcessOps* ops, const LaunchNeeds& nd, int ngood, int64_t rows, bool want_hel, bool want_col);
 int persistent_grid(const me_handle* h, const LaunchNeeds& nd, int64_t nevt);
 cudaError_t launch_chunks(const ProcessOps* ops, int prec, int config, MeLaunch a, int64_t nevt, int64_t chunk,
-                          int grid, int block,
+                          int grid, int block, int hsplit,
                           const Carve& cv, void* wsp, cudaStream_t s);
 CallPlan plan_call(const me_handle* h, int64_t nevt, int64_t chunk, bool want_hel, bool want_col);
 cudaError_t run_call(const me_handle* h, const CallPlan& cp, const MeLaunch& a, int64_t nevt, void* wsp, cudaStream_t s);

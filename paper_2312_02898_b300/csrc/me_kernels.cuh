@@ -68,6 +68,12 @@ struct MeLaunch {
   const int* index_count;
   int index_cap;
   int grid_blocks;   // blocks of the launch (persistent grid)
+  // helicity split: a group of hsplit consecutive threads (a power of two up to 32)
+  // shares one event, each lane taking a contiguous slice of the helicities; the group
+  // combines the lanes' sums with warp shuffles in a fixed order.  1 = one thread per
+  // event.  Used where events are few (the FP64 rescue pass, small batches), so that the
+  // latency of one event is spread over many threads.
+  int hsplit;
 };
 
 // view of an array laid out [index][S]
@@ -166,16 +172,21 @@ __global__ void __launch_bounds__(L::BLOCK) me_kernel(const MeLaunch a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int tid = threadIdx.x;
   const int64_t count = a.index ? int64_t(*a.index_count < a.index_cap ? *a.index_count : a.index_cap) : a.nevt;
-  const int64_t ntile = (count + BLOCK - 1) / BLOCK;
+  const int G = a.hsplit > 1 ? a.hsplit : 1;  // threads per event
+  const int64_t nunit = count * G;
+  const int64_t ntile = (nunit + BLOCK - 1) / BLOCK;
+  const int lane = tid & (G - 1);
   const int64_t wrow = int64_t(blockIdx.x) * BLOCK + tid;  // this thread's workspace row
   const int64_t wstride = int64_t(gridDim.x) * BLOCK;
   // The persistent grid walks the batch one tile of BLOCK events at a time.  The tile
   // loop is uniform over the block: a thread past the end of the batch mirrors its last
   // event and writes nothing, so every thread reaches every block barrier.
+  // A group of G threads never straddles the end of the batch (nunit is a multiple of G
+  // and BLOCK of 32), so the shuffles below always see whole groups.
   for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
-  const int64_t pos = tile * BLOCK + tid;
-  const bool active = pos < count;
-  const int64_t ipos = active ? pos : count - 1;
+  const int64_t unit = tile * BLOCK + tid;
+  const bool active = unit < nunit;
+  const int64_t ipos = active ? unit / G : count - 1;
   const int64_t ievt = a.index ? int64_t(a.index[ipos]) : ipos;
 
   // 1. momenta
@@ -240,7 +251,7 @@ __global__ void __launch_bounds__(L::BLOCK) me_kernel(const MeLaunch a) {
     else kappa = P::template precompute<BLOCK * 4, R>(pd, a.zc[2], a.zc[3], 0, r_dg, r_dt, kt);
     gfac = a.coup / double(P::COL_DEN);
   }
-  if (active && a.rescue_list && kappa > a.rescue_kappa) {
+  if (active && lane == 0 && a.rescue_list && kappa > a.rescue_kappa) {
     const int slot = atomicAdd(a.rescue_count, 1);
     if (slot < a.rescue_cap) a.rescue_list[slot] = int(a.ibase + ievt);
   }
@@ -260,11 +271,17 @@ __global__ void __launch_bounds__(L::BLOCK) me_kernel(const MeLaunch a) {
     }
   }
 
-  // 3. helicity loop
+  // 3. helicity loop: helicities [h0, h0 + hper) of the good list (all of them when
+  // G == 1); the trip count is the same for every thread, so block barriers stay
+  // uniform, and a slot past the end of the list computes a copy and discards it
   double total = 0.0;
+  const int hper = (a.ngood + G - 1) / G;
+  const int h0 = lane * hper;
 #pragma unroll 1
-  for (int ih = 0; ih < a.ngood; ++ih) {
-    const int h = a.good[ih];
+  for (int k = 0; k < hper; ++k) {
+    const int ih = h0 + k;
+    const bool valid = ih < a.ngood;
+    const int h = a.good[valid ? ih : a.ngood - 1];
     // keep the block's warps on the same stretch of the (very long, straight-line)
     // helicity body, so that instruction fetches are shared instead of thrashing
     if constexpr (L::sync) __syncthreads();
@@ -272,7 +289,7 @@ __global__ void __launch_bounds__(L::BLOCK) me_kernel(const MeLaunch a) {
     if constexpr (P::QCD && L::den_smem && L::w_mode != 0) {
       cs = one_helicity<P, R, L>(h, R(a.mt), s_dg + tid, s_dt + tid, L::j_smem ? s_J + tid : nullptr,
                                  L::w_mode == 1 ? s_w + tid : nullptr, a.colw ? a.colw + wrow : nullptr, wstride,
-                                 ws, kt, want_w);
+                                 ws, kt, want_w && valid);
     } else if constexpr (L::j_smem) {
       Strided<cx<R>, BLOCK> J{s_J + tid};
       for (int c = 0; c < P::NCOL; ++c) J[c] = mk<R>(R(0), R(0));
@@ -282,7 +299,7 @@ __global__ void __launch_bounds__(L::BLOCK) me_kernel(const MeLaunch a) {
       if (want_w) {
         for (int c = 0; c < P::NCOL; ++c) {
           const cx<R> z = J[c];
-          const R m2 = z.r * z.r + z.i * z.i;
+          const R m2 = valid ? z.r * z.r + z.i * z.i : R(0);
           if constexpr (L::w_mode == 0) r_w[c] += m2;
           else if constexpr (L::w_mode == 1) v_w[c] += m2;
           else a.colw[c * wstride + wrow] += double(m2);
@@ -298,22 +315,65 @@ __global__ void __launch_bounds__(L::BLOCK) me_kernel(const MeLaunch a) {
       if (want_w) {
 #pragma unroll
         for (int c = 0; c < P::NCOL; ++c) {
-          const R m2 = J[c].r * J[c].r + J[c].i * J[c].i;
+          const R m2 = valid ? J[c].r * J[c].r + J[c].i * J[c].i : R(0);
           if constexpr (L::w_mode == 0) r_w[c] += m2;
           else if constexpr (L::w_mode == 1) v_w[c] += m2;
           else a.colw[c * wstride + wrow] += double(m2);
         }
       }
     }
-    const double mh = double(cs) * gfac;
+    const double mh = valid ? double(cs) * gfac : 0.0;
     total += mh;
-    if (a.cum) a.cum[ih * wstride + wrow] = a.cum_mode ? mh : total;
+    // split groups keep each |M_h|^2 for the group's first lane to sum in order
+    if (a.cum && valid) a.cum[ih * wstride + wrow] = (a.cum_mode || G > 1) ? mh : total;
   }
 
   // 4. outputs
-  if (!active) continue;
+  int sel_split = 0;
+  if (G > 1) {
+    // The group's first lane sums the |M_h|^2 of all lanes in helicity order, exactly as
+    // one thread would, so the result and the helicity selection do not depend on the
+    // split.  The colour weights are summed over the lanes by a butterfly (the same bits
+    // in every lane), a reassociation of the one-thread sum.
+    const unsigned full = 0xffffffffu;
+    __syncwarp();
+    if (lane == 0) {
+      double run = 0.0, prev = 0.0;
+      const double target = a.sel_hel ? a.rnd_hel[ievt] : 0.0;  // scaled below
+      for (int ih = 0; ih < a.ngood; ++ih) run += a.cum[ih * wstride + wrow + ih / hper];
+      total = run;
+      if (a.sel_hel && total > 0.0) {
+        const double t = target * total;
+        int found = -1, lastnz = -1;
+        run = 0.0;
+        for (int ih = 0; ih < a.ngood; ++ih) {
+          run += a.cum[ih * wstride + wrow + ih / hper];
+          if (run > prev) lastnz = ih;
+          if (run > t) { found = ih; break; }
+          prev = run;
+        }
+        const int pick = found >= 0 ? found : lastnz;
+        sel_split = pick >= 0 ? a.good[pick] : 0;
+      }
+    }
+    if (want_w) {
+      for (int c = 0; c < P::NCOL; ++c) {
+        double w;
+        if constexpr (L::w_mode == 0) w = double(r_w[c]);
+        else if constexpr (L::w_mode == 1) w = double(v_w[c]);
+        else w = a.colw[c * wstride + wrow];
+        for (int o = G >> 1; o > 0; o >>= 1) w += __shfl_xor_sync(full, w, o, G);
+        if constexpr (L::w_mode == 0) r_w[c] = R(w);
+        else if constexpr (L::w_mode == 1) v_w[c] = R(w);
+        else a.colw[c * wstride + wrow] = w;
+      }
+    }
+  }
+  if (!active || lane != 0) continue;
   a.me[ievt] = total / double(P::IDEN);
-  if (a.sel_hel && a.cum && !a.cum_mode) {
+  if (G > 1 && a.sel_hel) {
+    a.sel_hel[ievt] = sel_split;
+  } else if (a.sel_hel && a.cum && !a.cum_mode) {
     int sel = 0;
     if (total > 0.0) {
       const double target = a.rnd_hel[ievt] * total;

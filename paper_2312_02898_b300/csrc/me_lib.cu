@@ -199,9 +199,9 @@ int persistent_grid(const me_handle* h, const LaunchNeeds& nd, int64_t nevt) {
 }
 
 // Launch 'a' over nevt events in chunks, each on at most 'grid' blocks of 'block'
-// threads, with workspace 'wsp' carved per 'cv'.
+// threads with 'hsplit' threads per event, with workspace 'wsp' carved per 'cv'.
 cudaError_t launch_chunks(const ProcessOps* ops, int prec, int config, MeLaunch a, int64_t nevt, int64_t chunk,
-                          int grid, int block, const Carve& cv, void* wsp, cudaStream_t s) {
+                          int grid, int block, int hsplit, const Carve& cv, void* wsp, cudaStream_t s) {
   char* w = static_cast<char*>(wsp);
   double* cum = cv.cum ? reinterpret_cast<double*>(w) : a.cum;
   double* colw = cv.colw ? reinterpret_cast<double*>(w + cv.cum) : nullptr;
@@ -223,7 +223,8 @@ cudaError_t launch_chunks(const ProcessOps* ops, int prec, int config, MeLaunch 
     b.slots = slots;
     b.ktab = ktab;
     b.ibase = off;
-    b.grid_blocks = int(std::min<int64_t>(grid, (b.nevt + block - 1) / block));
+    b.hsplit = hsplit;
+    b.grid_blocks = int(std::min<int64_t>(grid, (b.nevt * hsplit + block - 1) / block));
     cudaError_t e = ops->launch(prec, config, b, s);
     if (e != cudaSuccess) return e;
   }
@@ -242,7 +243,8 @@ CallPlan plan_call(const me_handle* h, int64_t nevt, int64_t chunk, bool want_he
   cp.chunk = chunk;
   const int ngood = int(h->good.size());
   const LaunchNeeds nd = ops->needs(cp.prec, cp.config);
-  cp.grid = persistent_grid(h, nd, chunk);
+  cp.hsplit = 1;  // one thread per event: results independent of the batch they come in
+  cp.grid = persistent_grid(h, nd, chunk * cp.hsplit);
   cp.block = nd.block;
   cp.main = carve(ops, nd, ngood, int64_t(cp.grid) * nd.block, want_hel, want_col);
   size_t off = cp.main.total();
@@ -251,11 +253,18 @@ CallPlan plan_call(const me_handle* h, int64_t nevt, int64_t chunk, bool want_he
     const LaunchNeeds n64 = ops->needs(ME_PREC_FP64, 0);
     const int64_t cap = std::min<int64_t>(nevt, std::max<int64_t>(1024, nevt / 16));
     cp.rescue_cap = int(cap);
-    cp.rescue_grid = persistent_grid(h, n64, cap);
+    // few events, each far slower in FP64: every event is spread over a group of up to
+    // 32 threads, which sum its helicities in the same order as one thread would
+    cp.rescue_hsplit = 1;
+    while (cp.rescue_hsplit < 32 && 2 * cp.rescue_hsplit <= ngood) cp.rescue_hsplit *= 2;
+    // the grid walks the list tile by tile, so any size is correct: it is sized for the
+    // usual flagged fraction (well under 1%), not for the capacity
+    const int64_t expect = std::min<int64_t>(cap, std::max<int64_t>(64, nevt / 100));
+    cp.rescue_grid = persistent_grid(h, n64, expect * cp.rescue_hsplit);
     const size_t rows = size_t(cp.rescue_grid) * n64.block;
     cp.off_count = off; off += 256;
     cp.off_list = off; off += up256(size_t(cap) * sizeof(int));
-    cp.off_cum = off; if (want_hel) off += up256(size_t(ngood) * rows * sizeof(double));
+    cp.off_cum = off; off += up256(size_t(ngood) * rows * sizeof(double));  // the split needs it
     cp.off_colw = off; if (want_col && n64.colw_global) off += up256(size_t(ops->ncol) * rows * sizeof(double));
     cp.off_slots = off; off += up256(n64.slot_bytes_per_event * rows);
     cp.off_ktab = off; off += up256(n64.ktab_bytes_per_event * rows);
@@ -277,13 +286,13 @@ cudaError_t run_call(const me_handle* h, const CallPlan& cp, const MeLaunch& a0,
     a.rescue_list = reinterpret_cast<int*>(w + cp.off_list);
     a.rescue_cap = cp.rescue_cap;
   }
-  cudaError_t e = launch_chunks(ops, cp.prec, cp.config, a, nevt, cp.chunk, cp.grid, cp.block, cp.main, wsp, s);
+  cudaError_t e = launch_chunks(ops, cp.prec, cp.config, a, nevt, cp.chunk, cp.grid, cp.block, cp.hsplit, cp.main, wsp, s);
   if (e != cudaSuccess || !cp.rescue) return e;
   // FP64 pass over the flagged events, in place: same inputs and outputs
   MeLaunch b = a0;
   const bool want_col = a0.sel_col != nullptr;
   b.nevt = nevt;
-  b.cum = a0.sel_hel ? reinterpret_cast<double*>(w + cp.off_cum) : nullptr;
+  b.cum = reinterpret_cast<double*>(w + cp.off_cum);
   b.colw = (want_col && ops->needs(ME_PREC_FP64, 0).colw_global) ? reinterpret_cast<double*>(w + cp.off_colw) : nullptr;
   b.slots = w + cp.off_slots;
   b.ktab = w + cp.off_ktab;
@@ -291,6 +300,7 @@ cudaError_t run_call(const me_handle* h, const CallPlan& cp, const MeLaunch& a0,
   b.index_count = reinterpret_cast<const int*>(w + cp.off_count);
   b.index_cap = cp.rescue_cap;
   b.grid_blocks = cp.rescue_grid;
+  b.hsplit = cp.rescue_hsplit;
   return ops->launch(ME_PREC_FP64, 0, b, s);
 }
 
@@ -388,7 +398,7 @@ int me_init(const char* process, const me_sm_params* p, me_handle** out) {
     for (int i = 0; i < ops->ncomb; ++i) a.good[i] = uint8_t(i);
     a.cum = d_cum;  // [ncomb][rows] with rows == nf: one tile per block, one event per thread
     if (int64_t(fgrid) * nd.block != nf) e = cudaErrorInvalidConfiguration;
-    if (e == cudaSuccess) e = launch_chunks(ops, ME_PREC_FP64, 0, a, nf, nf, fgrid, nd.block, cv, d_ws, 0);
+    if (e == cudaSuccess) e = launch_chunks(ops, ME_PREC_FP64, 0, a, nf, nf, fgrid, nd.block, 1, cv, d_ws, 0);
     if (e == cudaSuccess) e = cudaMemcpy(cum.data(), d_cum, cum.size() * sizeof(double), cudaMemcpyDeviceToHost);
   }
   cudaFree(d_mom);

@@ -70,10 +70,8 @@ def test_overlapping_requests_are_admitted_while_others_run():
     try:
         for b in (4096, 8192):
             server.warm("g g > t t~ g g", b)
-        futs = []
-        for k in range(9):
-            mom, a, rh, rc = make_batch("g g > t t~ g g", 8000, seed=k, alphas="uniform")
-            futs.append(server.submit("g g > t t~ g g", mom, a, rh, rc))
+        batch = [make_batch("g g > t t~ g g", 8000, seed=k, alphas="uniform") for k in range(9)]
+        futs = [server.submit("g g > t t~ g g", *x) for x in batch]  # a burst: all queued at once
         [f.result(timeout=300) for f in futs]
         assert server.max_running >= 2
     finally:
