@@ -39,6 +39,16 @@ METRIC = "ME evals/s per process, FP64 vs mixed at stated rel. err; serving p50/
 UNIT = "ME evals/s"
 FLOP_DTYPE = {"fp64": "f64", "fp32": "f32", "mixed": "f32+bf16"}
 ERR_BOUND = {"fp64": 1e-12, "fp32": 1e-5, "mixed": 1e-5}
+# DRAM bytes per event of each mode's default main-pass kernel, from one ncu capture of
+# 655360 events (profiles/me_kernel_*_655360.md); the traffic grows with the events
+# processed.  Keyed by the kernel's layout, so a changed default reports no traffic.
+DRAM_BYTES_PER_EVENT = {
+    ("fp64", "Layout<3, 64, 1, 1, 1, 2, 2, 1>"): 1.426e11 / 655360,
+    ("fp32", "Layout<1, 64, 1, 0, 1, 1, 2, 1>"): 1.249e9 / 655360,
+    ("mixed", "Layout<1, 128, 1, 1, 1, 2, 2, 1>"): 5.433e8 / 655360,
+}
+DEFAULT_LAYOUT = {"fp64": "Layout<3, 64, 1, 1, 1, 2, 2, 1>", "fp32": "Layout<1, 64, 1, 0, 1, 1, 2, 1>",
+                  "mixed": "Layout<1, 128, 1, 1, 1, 2, 2, 1>"}
 
 
 def dist_env():
@@ -307,7 +317,11 @@ def run_gpu(args):
                 "e2e": {"value": world * NEVT / (head["e2e_ms"] * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h, "entry": "me_compute_host"},
                 "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                             "frac": achieved / peak, "traffic": None,
+                             "frac": achieved / peak,
+                             "traffic": (DRAM_BYTES_PER_EVENT.get((args.mode, DEFAULT_LAYOUT[args.mode]), 0) * NEVT
+                                         / head["launches"] or None),
+                             "traffic_source": "ncu dram__bytes of the default layout at 655360 events, scaled to "
+                                               "one launch of this step",
                              "peak_source": f"measured {peak_key.upper()} FMA probe (me_probe_alu_peak) in this run",
                              "flops_per_event": head["flops_per_event"], "kernel": "me_kernel (amplitudes + colour sum)"},
                 "modes": acc,
