@@ -2,13 +2,13 @@
 //
 // For one helicity, a block of 128 events forms the 128 x K matrices A_re, A_im of
 // colour-flow amplitudes (one event per row, K = number of flows padded to a multiple
-// of 16).  The colour matrix C (integer numerators, symmetric, exact in BF16 for the
-// processes that use this path) is resident in shared memory as the N x K operand B.
+// of 16).  The colour matrix C (integer numerators, symmetric, exact in the 16-bit
+// operand type) is resident in shared memory as the N x K operand B.
 //   D_re = A_re C,  D_im = A_im C          (tcgen05.mma, FP32 accumulation in TMEM)
 //   |M_h|^2 * COL_DEN = sum_j (Re J_j D_re[j] + Im J_j D_im[j])   (per thread, FP32 J)
-// A is split into NTERM BF16 terms, A = a_1 + a_2 (+ a_3), each the BF16 rounding of
-// what the previous terms leave, so the product carries ~8*NTERM significant bits of
-// J; every term accumulates into the same TMEM columns.
+// A is split into NTERM 16-bit terms, A = a_1 + a_2 (+ a_3), each the rounding of what
+// the previous terms leave, so the product carries ~8*NTERM (BF16) or ~11*NTERM (FP16)
+// significant bits of J; every term accumulates into the same TMEM columns.
 //
 // Operands use the no-swizzle K-major shared-memory layout: 8-row x 16-byte core
 // matrices, adjacent along K every 128 bytes (leading byte offset) and along M/N every
@@ -40,12 +40,13 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
   return d;                // base offset 0, relative LBO, no swizzle
 }
 
-// instruction descriptor of kind::f16: BF16 x BF16 -> FP32, both operands K-major
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-  return (1u << 4)                        // D format FP32
-         | (1u << 7) | (1u << 10)         // A, B format BF16
-         | (uint32_t(N >> 3) << 17)       // N / 8
-         | (uint32_t(M >> 4) << 24);      // M / 16
+// instruction descriptor of kind::f16 with an FP32 accumulator, both operands K-major:
+// A and B both FP16 (f16 = true) or both BF16
+__host__ __device__ constexpr uint32_t idesc_f16kind(int M, int N, bool f16) {
+  return (1u << 4)                                   // D format FP32
+         | (f16 ? 0u : ((1u << 7) | (1u << 10)))     // A, B format: 0 FP16, 1 BF16
+         | (uint32_t(N >> 3) << 17)                  // N / 8
+         | (uint32_t(M >> 4) << 24);                 // M / 16
 }
 
 __device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
@@ -62,8 +63,9 @@ __device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fenc
 __device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                         uint32_t accumulate) {
+// D (TMEM) = A B (+ D when accumulate), operand types as the instruction descriptor says
+__device__ __forceinline__ void mma_f16kind(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t accumulate) {
   asm volatile(
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),

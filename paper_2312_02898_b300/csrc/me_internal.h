@@ -40,8 +40,8 @@ namespace detail {
 // Bytes of workspace of one persistent launch (one row per resident thread), and its
 // carve-up.
 struct Carve {
-  size_t cum = 0, colw = 0, slots = 0, ktab = 0;
-  size_t total() const { return cum + colw + slots + ktab; }
+  size_t cum = 0, colw = 0, slots = 0, ktab = 0, den = 0, jt = 0;
+  size_t total() const { return cum + colw + slots + ktab + den + jt; }
 };
 
 // A me_compute call: the main pass (in chunks when the slot buffer is global), the
@@ -55,7 +55,8 @@ struct CallPlan {
   Carve main;
   bool rescue = false;
   int rescue_cap = 0, rescue_grid = 0, rescue_hsplit = 1;
-  size_t off_count = 0, off_list = 0, off_cum = 0, off_colw = 0, off_slots = 0, off_ktab = 0;
+  size_t off_count = 0, off_list = 0, off_cum = 0, off_colw = 0, off_slots = 0, off_ktab = 0, off_den = 0,
+         off_j = 0;
   size_t total = 0;
 };
 

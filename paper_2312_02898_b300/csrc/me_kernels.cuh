@@ -53,6 +53,8 @@ struct MeLaunch {
   double* colw;      // [ncol][rows] (when the colour weights live in global memory)
   void* slots;       // [block][nslot][BLOCK][4] complex (slot buffer in global memory)
   void* ktab;        // [block][nkvec][BLOCK][4] real (momentum table in global memory)
+  void* dtile;       // [block][nden_g][BLOCK] real, then [block][nden_t][BLOCK] complex (denominators in global memory)
+  void* jtile;       // [block][ncol][BLOCK] complex (colour-flow amplitudes in global memory)
   int* err;          // set to 1 when a bounded device-side wait runs out (mapped host memory)
   // precision rescue (FP32 and mixed passes): events whose conditioning kappa exceeds
   // rescue_kappa are appended, as ibase + local index, to rescue_list (capacity
@@ -86,16 +88,19 @@ struct Strided {
 // Launch configuration of one (process, precision):
 //   V        jamps variant (register budget) of the generated code
 //   BLOCK    threads per block
-//   DEN_SMEM denominators in shared memory (else registers)
-//   J_SMEM   colour-flow amplitudes in shared memory (else registers)
+//   DEN_MODE denominators: 0 registers, 1 shared memory, 2 global tile per block
+//   J_MODE   colour-flow amplitudes: 0 registers, 1 shared memory, 2 global tile per block
 //   W_MODE   colour weights: 0 registers, 1 shared memory, 2 global workspace
 //   S_MODE   slot buffer: 0 none, 1 shared memory, 2 global workspace
 //   K_MODE   momentum table: 1 shared memory, 2 global workspace
 //   SYNC     a block barrier at the top of every helicity
-template <int V_, int BLOCK_, bool DEN_SMEM, bool J_SMEM, int W_MODE, int S_MODE, int K_MODE, bool SYNC = false>
+template <int V_, int BLOCK_, int DEN_MODE, int J_MODE, int W_MODE, int S_MODE, int K_MODE, bool SYNC = false>
 struct Layout {
   static constexpr int V = V_, BLOCK = BLOCK_;
-  static constexpr bool den_smem = DEN_SMEM, j_smem = J_SMEM, sync = SYNC;
+  static constexpr int den_mode = DEN_MODE, j_mode = J_MODE;
+  // "view": an array laid out [index][BLOCK] (shared or global) rather than registers
+  static constexpr bool den_view = DEN_MODE != 0, j_view = J_MODE != 0;
+  static constexpr bool den_smem = DEN_MODE == 1, j_smem = J_MODE == 1, sync = SYNC;
   static constexpr int w_mode = W_MODE, s_mode = S_MODE, k_mode = K_MODE;
 };
 
@@ -145,7 +150,7 @@ __device__ __noinline__ R one_helicity(int h, R mt, R* s_dg_t, cx<R>* s_dt_t, cx
     if constexpr (L::w_mode == 1) s_w_t[c * BLOCK] += m2;
     else if constexpr (L::w_mode == 2) colw_t[c * colw_stride] += double(m2);
   };
-  if constexpr (L::j_smem) {
+  if constexpr (L::j_view) {
     Strided<cx<R>, BLOCK> J{s_J_t};
     for (int c = 0; c < P::NCOL; ++c) J[c] = mk<R>(R(0), R(0));
     P::template jamps<L::V, BLOCK * 4, R, L::sync>(h, mt, dg, dt, J, ws, kt);
@@ -164,6 +169,21 @@ __device__ __noinline__ R one_helicity(int h, R mt, R* s_dg_t, cx<R>* s_dt_t, cx
     }
   }
   return cs;
+}
+
+// this block's tiles of the global denominator and colour-flow-amplitude workspaces
+template <class P, class R, int BLOCK>
+__device__ __forceinline__ R* den_tile_g(const MeLaunch& a) {
+  const size_t per_block = size_t(P::NDEN_G) * BLOCK * sizeof(R) + size_t(P::NDEN_T) * BLOCK * sizeof(cx<R>);
+  return reinterpret_cast<R*>(static_cast<char*>(a.dtile) + size_t(blockIdx.x) * per_block);
+}
+template <class P, class R, int BLOCK>
+__device__ __forceinline__ cx<R>* den_tile_t(const MeLaunch& a) {
+  return reinterpret_cast<cx<R>*>(den_tile_g<P, R, BLOCK>(a) + size_t(P::NDEN_G) * BLOCK);
+}
+template <class P, class R, int BLOCK>
+__device__ __forceinline__ cx<R>* j_tile(const MeLaunch& a) {
+  return static_cast<cx<R>*>(a.jtile) + size_t(blockIdx.x) * P::NCOL * BLOCK;
 }
 
 template <class P, class R, class L>
@@ -211,13 +231,17 @@ __global__ void __launch_bounds__(L::BLOCK) me_kernel(const MeLaunch a) {
   if constexpr (L::den_smem) {
     s_dg = reinterpret_cast<R*>(sp); sp += size_t(P::NDEN_G) * BLOCK * sizeof(R);
     s_dt = reinterpret_cast<cx<R>*>(sp); sp += size_t(P::NDEN_T) * BLOCK * sizeof(cx<R>);
+  } else if constexpr (L::den_mode == 2) {
+    s_dg = den_tile_g<P, R, BLOCK>(a);
+    s_dt = den_tile_t<P, R, BLOCK>(a);
   }
   if constexpr (L::j_smem) { s_J = reinterpret_cast<cx<R>*>(sp); sp += size_t(P::NCOL) * BLOCK * sizeof(cx<R>); }
+  else if constexpr (L::j_mode == 2) s_J = j_tile<P, R, BLOCK>(a);
   if constexpr (L::w_mode == 1) { s_w = reinterpret_cast<R*>(sp); sp += size_t(P::NCOL) * BLOCK * sizeof(R); }
   constexpr int NS = P::template nslot<L::V>();
   static_assert(NS == 0 || L::s_mode != 0, "this jamps variant needs a slot buffer");
-  static_assert(!P::template grouped<L::V>() || (L::den_smem && L::j_smem),
-                "diagram-group variants take shared-memory views of the denominators and J");
+  static_assert(!P::template grouped<L::V>() || (L::den_view && L::j_view),
+                "diagram-group variants take views of the denominators and J");
   if constexpr (L::s_mode == 1) { s_slots = reinterpret_cast<cx<R>*>(sp); sp += size_t(NS) * BLOCK * 4 * sizeof(cx<R>); }
   if constexpr (L::k_mode == 1) { s_kt = reinterpret_cast<R*>(sp); }
 
@@ -232,13 +256,13 @@ __global__ void __launch_bounds__(L::BLOCK) me_kernel(const MeLaunch a) {
   else kt = static_cast<R*>(a.ktab) + (size_t(blockIdx.x) * P::NKVEC * BLOCK + tid) * 4;
 
   // 2. denominators and momentum table, FP64 once per event
-  R r_dg[L::den_smem ? 1 : P::NDEN_G];
-  cx<R> r_dt[L::den_smem ? 1 : P::NDEN_T];
+  R r_dg[L::den_view ? 1 : P::NDEN_G];
+  cx<R> r_dt[L::den_view ? 1 : P::NDEN_T];
   Strided<R, BLOCK> v_dg{s_dg + tid};
   Strided<cx<R>, BLOCK> v_dt{s_dt + tid};
   double gfac, kappa;
   if constexpr (P::QCD) {
-    if constexpr (L::den_smem) kappa = P::template precompute<BLOCK * 4, R>(pd, a.mt, a.wt, a.zwt, v_dg, v_dt, kt);
+    if constexpr (L::den_view) kappa = P::template precompute<BLOCK * 4, R>(pd, a.mt, a.wt, a.zwt, v_dg, v_dt, kt);
     else kappa = P::template precompute<BLOCK * 4, R>(pd, a.mt, a.wt, a.zwt, r_dg, r_dt, kt);
     const double as = a.alphas ? a.alphas[ievt] : a.alphas_default;
     const double g2 = 4.0 * 3.14159265358979323846 * as;
@@ -247,7 +271,7 @@ __global__ void __launch_bounds__(L::BLOCK) me_kernel(const MeLaunch a) {
     for (int k = 0; k < P::NGLUON; ++k) gp *= g2;
     gfac = gp / double(P::COL_DEN);
   } else {
-    if constexpr (L::den_smem) kappa = P::template precompute<BLOCK * 4, R>(pd, a.zc[2], a.zc[3], 0, v_dg, v_dt, kt);
+    if constexpr (L::den_view) kappa = P::template precompute<BLOCK * 4, R>(pd, a.zc[2], a.zc[3], 0, v_dg, v_dt, kt);
     else kappa = P::template precompute<BLOCK * 4, R>(pd, a.zc[2], a.zc[3], 0, r_dg, r_dt, kt);
     gfac = a.coup / double(P::COL_DEN);
   }
@@ -286,14 +310,14 @@ __global__ void __launch_bounds__(L::BLOCK) me_kernel(const MeLaunch a) {
     // helicity body, so that instruction fetches are shared instead of thrashing
     if constexpr (L::sync) __syncthreads();
     R cs;
-    if constexpr (P::QCD && L::den_smem && L::w_mode != 0) {
-      cs = one_helicity<P, R, L>(h, R(a.mt), s_dg + tid, s_dt + tid, L::j_smem ? s_J + tid : nullptr,
+    if constexpr (P::QCD && L::den_view && L::w_mode != 0) {
+      cs = one_helicity<P, R, L>(h, R(a.mt), s_dg + tid, s_dt + tid, L::j_view ? s_J + tid : nullptr,
                                  L::w_mode == 1 ? s_w + tid : nullptr, a.colw ? a.colw + wrow : nullptr, wstride,
                                  ws, kt, want_w && valid);
-    } else if constexpr (L::j_smem) {
+    } else if constexpr (L::j_view) {
       Strided<cx<R>, BLOCK> J{s_J + tid};
       for (int c = 0; c < P::NCOL; ++c) J[c] = mk<R>(R(0), R(0));
-      if constexpr (L::den_smem) call_jamps<P, L>(h, a, v_dg, v_dt, J, ws, kt);
+      if constexpr (L::den_view) call_jamps<P, L>(h, a, v_dg, v_dt, J, ws, kt);
       else call_jamps<P, L>(h, a, r_dg, r_dt, J, ws, kt);
       cs = P::template colour_sum<R>(J);
       if (want_w) {
@@ -309,7 +333,7 @@ __global__ void __launch_bounds__(L::BLOCK) me_kernel(const MeLaunch a) {
       cx<R> J[P::NCOL];
 #pragma unroll
       for (int c = 0; c < P::NCOL; ++c) J[c] = mk<R>(R(0), R(0));
-      if constexpr (L::den_smem) call_jamps<P, L>(h, a, v_dg, v_dt, J, ws, kt);
+      if constexpr (L::den_view) call_jamps<P, L>(h, a, v_dg, v_dt, J, ws, kt);
       else call_jamps<P, L>(h, a, r_dg, r_dt, J, ws, kt);
       cs = P::template colour_sum<R>(J);
       if (want_w) {
@@ -427,6 +451,8 @@ __global__ void __launch_bounds__(L::BLOCK) me_kernel(const MeLaunch a) {
 struct LaunchNeeds {
   size_t slot_bytes_per_event;  // global slot buffer, per workspace row
   size_t ktab_bytes_per_event;  // global momentum table, per workspace row
+  size_t den_bytes_per_event;   // global denominators, per workspace row
+  size_t j_bytes_per_event;     // global colour-flow amplitudes, per workspace row
   bool colw_global;             // colour weights in a global [ncol][rows] array
   int block;                    // threads per block (global tiles cover whole blocks)
   int blocks_per_sm;            // resident blocks per SM (occupancy of the kernel)
@@ -481,6 +507,8 @@ LaunchNeeds sizes_of() {
   LaunchNeeds n;
   n.slot_bytes_per_event = L::s_mode == 2 ? size_t(P::template nslot<L::V>()) * 4 * sizeof(cx<R>) : 0;
   n.ktab_bytes_per_event = L::k_mode == 2 ? size_t(P::NKVEC) * 4 * sizeof(R) : 0;
+  n.den_bytes_per_event = L::den_mode == 2 ? size_t(P::NDEN_G) * sizeof(R) + size_t(P::NDEN_T) * sizeof(cx<R>) : 0;
+  n.j_bytes_per_event = L::j_mode == 2 ? size_t(P::NCOL) * sizeof(cx<R>) : 0;
   n.colw_global = L::w_mode == 2;
   n.block = L::BLOCK;
   n.blocks_per_sm = 1;

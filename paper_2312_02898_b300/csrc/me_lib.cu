@@ -187,6 +187,8 @@ Carve carve(const ProcessOps* ops, const LaunchNeeds& nd, int ngood, int64_t row
   if (want_col && nd.colw_global) c.colw = up(size_t(ops->ncol) * rows * sizeof(double));
   c.slots = up(nd.slot_bytes_per_event * rows);  // rows cover whole blocks
   c.ktab = up(nd.ktab_bytes_per_event * rows);
+  c.den = up(nd.den_bytes_per_event * rows);
+  c.jt = up(nd.j_bytes_per_event * rows);
   return c;
 }
 
@@ -207,6 +209,8 @@ cudaError_t launch_chunks(const ProcessOps* ops, int prec, int config, MeLaunch 
   double* colw = cv.colw ? reinterpret_cast<double*>(w + cv.cum) : nullptr;
   void* slots = cv.slots ? static_cast<void*>(w + cv.cum + cv.colw) : nullptr;
   void* ktab = cv.ktab ? static_cast<void*>(w + cv.cum + cv.colw + cv.slots) : nullptr;
+  void* dtile = cv.den ? static_cast<void*>(w + cv.cum + cv.colw + cv.slots + cv.ktab) : nullptr;
+  void* jtile = cv.jt ? static_cast<void*>(w + cv.cum + cv.colw + cv.slots + cv.ktab + cv.den) : nullptr;
   const int npar = ops->npar;
   for (int64_t off = 0; off < nevt; off += chunk) {
     MeLaunch b = a;
@@ -222,6 +226,8 @@ cudaError_t launch_chunks(const ProcessOps* ops, int prec, int config, MeLaunch 
     b.colw = colw;
     b.slots = slots;
     b.ktab = ktab;
+    b.dtile = dtile;
+    b.jtile = jtile;
     b.ibase = off;
     b.hsplit = hsplit;
     b.grid_blocks = int(std::min<int64_t>(grid, (b.nevt * hsplit + block - 1) / block));
@@ -268,6 +274,8 @@ CallPlan plan_call(const me_handle* h, int64_t nevt, int64_t chunk, bool want_he
     cp.off_colw = off; if (want_col && n64.colw_global) off += up256(size_t(ops->ncol) * rows * sizeof(double));
     cp.off_slots = off; off += up256(n64.slot_bytes_per_event * rows);
     cp.off_ktab = off; off += up256(n64.ktab_bytes_per_event * rows);
+    cp.off_den = off; off += up256(n64.den_bytes_per_event * rows);
+    cp.off_j = off; off += up256(n64.j_bytes_per_event * rows);
   }
   cp.total = off;
   return cp;
@@ -296,6 +304,8 @@ cudaError_t run_call(const me_handle* h, const CallPlan& cp, const MeLaunch& a0,
   b.colw = (want_col && ops->needs(ME_PREC_FP64, 0).colw_global) ? reinterpret_cast<double*>(w + cp.off_colw) : nullptr;
   b.slots = w + cp.off_slots;
   b.ktab = w + cp.off_ktab;
+  b.dtile = w + cp.off_den;
+  b.jtile = w + cp.off_j;
   b.index = reinterpret_cast<const int*>(w + cp.off_list);
   b.index_count = reinterpret_cast<const int*>(w + cp.off_count);
   b.index_cap = cp.rescue_cap;

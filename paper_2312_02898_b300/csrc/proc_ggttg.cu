@@ -1,7 +1,8 @@
 // Kernel instantiations and launch table for the process in generated/proc_ggttg.cuh.
-// Layout<jamps variant (register budget), threads per block, denominators in shared
-// memory, J in shared memory, colour weights (0 registers, 1 shared, 2 global),
-// slot buffer (0 none, 1 shared, 2 global), momentum table (1 shared, 2 global)>.
+// Layout<jamps variant (register budget), threads per block, denominators and J and
+// colour weights (each 0 registers, 1 shared memory, 2 global tile), slot buffer (0 none,
+// 1 shared, 2 global), momentum table (1 shared, 2 global), block barriers in the
+// helicity body (default none)>.
 // The first layout of each precision is the default; the others are alternatives for
 // tuning sweeps (me_set_config / ME_B300_CONFIG).
 #include "generated/proc_ggttg.cuh"
@@ -22,7 +23,7 @@ LaunchNeeds needs(int prec, int config) {
     case 1: return needs_of<P, Cfg<0, 1>::R, Cfg<0, 1>::L>();
     case 8: return needs_of<P, Cfg<1, 0>::R, Cfg<1, 0>::L>();
     case 9: return needs_of<P, Cfg<1, 1>::R, Cfg<1, 1>::L>();
-    default: return LaunchNeeds{0, 0, false, 128, 1};
+    default: return LaunchNeeds{0, 0, 0, 0, false, 128, 1};
   }
 }
 

@@ -1,8 +1,8 @@
 // Kernel instantiations and launch table for the process in generated/proc_ggttgg.cuh.
-// Layout<jamps variant (register budget), threads per block, denominators in shared
-// memory, J in shared memory, colour weights (0 registers, 1 shared, 2 global),
-// slot buffer (0 none, 1 shared, 2 global), momentum table (1 shared, 2 global),
-// block barriers in the helicity body (default none)>.
+// Layout<jamps variant (register budget), threads per block, denominators and J and
+// colour weights (each 0 registers, 1 shared memory, 2 global tile), slot buffer (0 none,
+// 1 shared, 2 global), momentum table (1 shared, 2 global), block barriers in the
+// helicity body (default none)>.
 // The first layout of each precision is the default; the others are alternatives for
 // tuning sweeps (me_set_config / ME_B300_CONFIG).
 #include "generated/proc_ggttgg.cuh"
@@ -24,13 +24,14 @@ template <> struct Cfg<1, 3> { using R = float; using L = Layout<0, 128, true, f
 template <> struct Cfg<1, 4> { using R = float; using L = Layout<1, 128, true, false, 1, 2, 2>; };
 template <> struct Cfg<1, 5> { using R = float; using L = Layout<2, 128, true, false, 1, 2, 2>; };
 
-// mixed precision: amplitude layout (must use shared J and weights, 128 threads) and the
-// number of BF16 terms of the split colour-flow amplitudes
+// mixed precision: amplitude layout (views of J and the weights, 128 threads), the
+// number of 16-bit terms of the split colour-flow amplitudes, and the operand type
+// (the colour matrix of this process is exact in BF16)
 template <int C> struct MixedCfg;
-template <> struct MixedCfg<0> { using L = Layout<1, 128, true, true, 1, 2, 2, true>; static constexpr int NTERM = 3; };
-template <> struct MixedCfg<1> { using L = Layout<1, 128, true, true, 1, 2, 2>; static constexpr int NTERM = 3; };
-template <> struct MixedCfg<2> { using L = Layout<1, 128, true, true, 1, 2, 2>; static constexpr int NTERM = 2; };
-template <> struct MixedCfg<3> { using L = Layout<2, 128, true, true, 1, 2, 2>; static constexpr int NTERM = 3; };
+template <> struct MixedCfg<0> { using L = Layout<1, 128, true, true, 1, 2, 2, true>; static constexpr int NTERM = 3; static constexpr bool F16 = false; };
+template <> struct MixedCfg<1> { using L = Layout<1, 128, true, true, 1, 2, 2>; static constexpr int NTERM = 3; static constexpr bool F16 = false; };
+template <> struct MixedCfg<2> { using L = Layout<1, 128, true, true, 1, 2, 2>; static constexpr int NTERM = 2; static constexpr bool F16 = false; };
+template <> struct MixedCfg<3> { using L = Layout<2, 128, true, true, 1, 2, 2>; static constexpr int NTERM = 3; static constexpr bool F16 = false; };
 
 LaunchNeeds needs(int prec, int config) {
   switch (prec * 8 + config) {
@@ -44,11 +45,11 @@ LaunchNeeds needs(int prec, int config) {
     case 11: return needs_of<P, Cfg<1, 3>::R, Cfg<1, 3>::L>();
     case 12: return needs_of<P, Cfg<1, 4>::R, Cfg<1, 4>::L>();
     case 13: return needs_of<P, Cfg<1, 5>::R, Cfg<1, 5>::L>();
-    case 16: return needs_mixed_of<P, MixedCfg<0>::L, MixedCfg<0>::NTERM>();
-    case 17: return needs_mixed_of<P, MixedCfg<1>::L, MixedCfg<1>::NTERM>();
-    case 18: return needs_mixed_of<P, MixedCfg<2>::L, MixedCfg<2>::NTERM>();
-    case 19: return needs_mixed_of<P, MixedCfg<3>::L, MixedCfg<3>::NTERM>();
-    default: return LaunchNeeds{0, 0, false, 128, 1};
+    case 16: return needs_mixed_of<P, MixedCfg<0>::L, MixedCfg<0>::NTERM, MixedCfg<0>::F16>();
+    case 17: return needs_mixed_of<P, MixedCfg<1>::L, MixedCfg<1>::NTERM, MixedCfg<1>::F16>();
+    case 18: return needs_mixed_of<P, MixedCfg<2>::L, MixedCfg<2>::NTERM, MixedCfg<2>::F16>();
+    case 19: return needs_mixed_of<P, MixedCfg<3>::L, MixedCfg<3>::NTERM, MixedCfg<3>::F16>();
+    default: return LaunchNeeds{0, 0, 0, 0, false, 128, 1};
   }
 }
 
@@ -64,10 +65,10 @@ cudaError_t launch(int prec, int config, const MeLaunch& a, cudaStream_t s) {
     case 11: return launch_me<P, Cfg<1, 3>::R, Cfg<1, 3>::L>(a, s);
     case 12: return launch_me<P, Cfg<1, 4>::R, Cfg<1, 4>::L>(a, s);
     case 13: return launch_me<P, Cfg<1, 5>::R, Cfg<1, 5>::L>(a, s);
-    case 16: return launch_mixed<P, MixedCfg<0>::L, MixedCfg<0>::NTERM>(a, s);
-    case 17: return launch_mixed<P, MixedCfg<1>::L, MixedCfg<1>::NTERM>(a, s);
-    case 18: return launch_mixed<P, MixedCfg<2>::L, MixedCfg<2>::NTERM>(a, s);
-    case 19: return launch_mixed<P, MixedCfg<3>::L, MixedCfg<3>::NTERM>(a, s);
+    case 16: return launch_mixed<P, MixedCfg<0>::L, MixedCfg<0>::NTERM, MixedCfg<0>::F16>(a, s);
+    case 17: return launch_mixed<P, MixedCfg<1>::L, MixedCfg<1>::NTERM, MixedCfg<1>::F16>(a, s);
+    case 18: return launch_mixed<P, MixedCfg<2>::L, MixedCfg<2>::NTERM, MixedCfg<2>::F16>(a, s);
+    case 19: return launch_mixed<P, MixedCfg<3>::L, MixedCfg<3>::NTERM, MixedCfg<3>::F16>(a, s);
     default: return cudaErrorNotSupported;
   }
 }

@@ -1,43 +1,53 @@
 // Kernel instantiations and launch table for the process in generated/proc_ggttggg.cuh.
-// Layout<jamps variant (register budget), threads per block, denominators in shared
-// memory, J in shared memory, colour weights (0 registers, 1 shared, 2 global),
-// slot buffer (0 none, 1 shared, 2 global), momentum table (1 shared, 2 global)>.
+// Layout<jamps variant (register budget), threads per block, denominators and J and
+// colour weights (each 0 registers, 1 shared memory, 2 global tile), slot buffer (0 none,
+// 1 shared, 2 global), momentum table (1 shared, 2 global), block barriers in the
+// helicity body (default none)>.
 // The first layout of each precision is the default; the others are alternatives for
 // tuning sweeps (me_set_config / ME_B300_CONFIG).
 #include "generated/proc_ggttggg.cuh"
+#include "me_kernel_mixed.cuh"
 #include "me_kernels.cuh"
 
 namespace meb300 {
 namespace {
 using P = proc_ggttggg;
 template <int PREC, int C> struct Cfg;
-template <> struct Cfg<0, 0> { using R = double; using L = Layout<0, 64, true, true, 2, 2, 2>; };
-template <> struct Cfg<1, 0> { using R = float; using L = Layout<0, 128, true, true, 2, 2, 2>; };
-template <> struct Cfg<0, 1> { using R = double; using L = Layout<0, 64, true, true, 2, 2, 2, true>; };
-template <> struct Cfg<1, 1> { using R = float; using L = Layout<0, 128, true, true, 2, 2, 2, true>; };
+template <> struct Cfg<0, 0> { using R = double; using L = Layout<0, 64, 1, 1, 2, 2, 2>; };
+// FP32: every per-thread array in global tiles leaves shared memory free for two
+// blocks per SM, which doubles the warps that hide latency (1.7x the throughput of
+// shared-memory denominators and J at one block per SM)
+template <> struct Cfg<1, 0> { using R = float; using L = Layout<0, 128, 2, 2, 2, 2, 2>; };
+template <> struct Cfg<1, 1> { using R = float; using L = Layout<0, 128, 1, 1, 2, 2, 2>; };
+
+// mixed precision: every per-thread array in global tiles, so that the FP16 operand
+// tiles (120 flows padded to 128) and the colour matrix fit in shared memory beside two
+// blocks per SM; two FP16 terms (the colour matrix is exact in FP16, not in BF16)
+template <int C> struct MixedCfg;
+template <> struct MixedCfg<0> { using L = Layout<0, 128, 2, 2, 2, 2, 2>; static constexpr int NTERM = 2; static constexpr bool F16 = true; };
 
 LaunchNeeds needs(int prec, int config) {
   switch (prec * 8 + config) {
     case 0: return needs_of<P, Cfg<0, 0>::R, Cfg<0, 0>::L>();
-    case 1: return needs_of<P, Cfg<0, 1>::R, Cfg<0, 1>::L>();
     case 8: return needs_of<P, Cfg<1, 0>::R, Cfg<1, 0>::L>();
     case 9: return needs_of<P, Cfg<1, 1>::R, Cfg<1, 1>::L>();
-    default: return LaunchNeeds{0, 0, false, 128, 1};
+    case 16: return needs_mixed_of<P, MixedCfg<0>::L, MixedCfg<0>::NTERM, MixedCfg<0>::F16>();
+    default: return LaunchNeeds{0, 0, 0, 0, false, 128, 1};
   }
 }
 
 cudaError_t launch(int prec, int config, const MeLaunch& a, cudaStream_t s) {
   switch (prec * 8 + config) {
     case 0: return launch_me<P, Cfg<0, 0>::R, Cfg<0, 0>::L>(a, s);
-    case 1: return launch_me<P, Cfg<0, 1>::R, Cfg<0, 1>::L>(a, s);
     case 8: return launch_me<P, Cfg<1, 0>::R, Cfg<1, 0>::L>(a, s);
     case 9: return launch_me<P, Cfg<1, 1>::R, Cfg<1, 1>::L>(a, s);
+    case 16: return launch_mixed<P, MixedCfg<0>::L, MixedCfg<0>::NTERM, MixedCfg<0>::F16>(a, s);
     default: return cudaErrorNotSupported;
   }
 }
 }  // namespace
 
 extern const ProcessOps ops_ggttggg = {P::NAME, P::NPAR, P::NCOMB, P::NCOL, P::NDIAG, P::NAMP, P::IDEN,
-                                   P::FLOPS_AMP, P::FLOPS_COL, /*has_mixed=*/false, {2, 2, 0},
+                                   P::FLOPS_AMP, P::FLOPS_COL, /*has_mixed=*/true, {1, 2, 1},
                                    needs, launch};
 }  // namespace meb300

@@ -62,6 +62,17 @@ FLOPS = {
 }
 
 
+def _exact(cf, bits):
+    """every integer entry representable with a significand of 'bits' bits (the
+    exponent range of FP16 reaches 65504, beyond every colour-matrix entry here)"""
+    for x in (abs(int(v)) for v in cf.flatten()):
+        if x and (x >> max(0, x.bit_length() - bits)) << max(0, x.bit_length() - bits) != x:
+            return False
+        if bits == 11 and x > 65504:
+            return False
+    return True
+
+
 SYNC_EVERY = 24  # schedule steps (currents and diagram closings) between block barriers
 
 
@@ -423,6 +434,8 @@ class Emitter:
                f"static constexpr int NDEN_G = {ngden}, NDEN_T = {ntden}, COL_DEN = {cden}, NCOLPAIR = {pair_count};",
                f"static constexpr long FLOPS_AMP = {fl['amp']}, FLOPS_COL = {csflops};  // per helicity, real flops",
                f"static constexpr int MAX_LIVE = {sc.max_live(sched, it, itb)};  // currents alive at once",
+               f"static constexpr bool CF_BF16_EXACT = {'true' if _exact(cf, 8) else 'false'}, "
+               f"CF_FP16_EXACT = {'true' if _exact(cf, 11) else 'false'};  // colour matrix exact in 16-bit",
                "static constexpr bool QCD = true;", "",
                f"static constexpr int NKVEC = {nk};  // momentum vectors in the per-event table",
                "template <int S, class R, class DG, class DT>",

@@ -91,7 +91,7 @@ def test_fp32_parity(process):
         assert np.mean(sc == ref["sel_col"]) > 0.99
 
 
-MIXED = [p for p in ACTIVE if p in (PROCS[3],)]
+MIXED = [p for p in ACTIVE if p in (PROCS[3], PROCS[4])]
 MIXED_BOUND = 1e-5
 
 
@@ -149,9 +149,11 @@ def test_rescue_removes_the_fp32_error_tail(process):
 
 @pytest.mark.parametrize("process", MIXED)
 def test_mixed_matches_fp32_amplitudes(process):
-    """The tensor-core colour sum agrees with the FP32 CUDA-core colour sum of the same
-    FP32 amplitudes far below the FP32 rounding level of the amplitudes themselves."""
-    mom, a, rh, rc = ps.make_batch(process, 1000, seed=17, alphas="uniform")
+    """The tensor-core colour sum (BF16 terms for gg -> ttbar gg, FP16 terms with a
+    per-event power-of-two scale for gg -> ttbar ggg) agrees with the FP32 CUDA-core
+    colour sum of the same FP32 amplitudes far below the FP32 rounding level of the
+    amplitudes themselves."""
+    mom, a, rh, rc = ps.make_batch(process, 1000 if process == PROCS[3] else 300, seed=17, alphas="uniform")
     m32 = mk(process, "fp32")
     m32.set_config(0)
     mx = mk(process, "mixed")
@@ -257,7 +259,7 @@ def test_batch_split_invariance():
 FULL = [(PROCS[0], 16384, "fp64", None), (PROCS[1], 524288, "fp64", 0.118), (PROCS[2], 524288, "fp32", 0.118),
         (PROCS[3], 1048576, "fp64", "uniform"), (PROCS[3], 1048576, "fp32", "uniform"),
         (PROCS[3], 1048576, "mixed", "uniform"),
-        (PROCS[4], 262144, "fp32", 0.118)]
+        (PROCS[4], 262144, "fp32", 0.118), (PROCS[4], 262144, "mixed", 0.118)]
 
 
 @pytest.mark.parametrize("process,nevt,precision,alphas", [f for f in FULL if f[0] in ACTIVE])
