@@ -205,6 +205,52 @@ def time_mode(mode, dev_inputs, host_inputs, steps, warmup, dist, process=None, 
     return res
 
 
+def time_testbed(mode, steps, warmup):
+    """The standalone testbed flow (Section 2, Fig. 1b) on the device: every step
+    generates the batch (RAMBO momenta, alpha_s, the two selection numbers) with the
+    counter-based generator on the GPU and evaluates it, with no host round trip."""
+    import ctypes
+    import torch
+    from paper_2312_02898_b300.binding import MatrixElement, _ptr
+    m = MatrixElement(PROCESS, precision=mode)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    mom = torch.empty((NEVT, m.npar, 4), dtype=torch.float64, device=dev)
+    a, rh, rc = (torch.empty(NEVT, dtype=torch.float64, device=dev) for _ in range(3))
+    out = (torch.empty(NEVT, dtype=torch.float64, device=dev), torch.empty(NEVT, dtype=torch.int32, device=dev),
+           torch.empty(NEVT, dtype=torch.int32, device=dev))
+    s = torch.cuda.current_stream()
+    sp = ctypes.c_void_p(s.cuda_stream)
+
+    def step(k):
+        first = k * NEVT
+        m._check(m.lib.me_rambo(m.handle, NEVT, 0, first, 1500.0, _ptr(mom), sp))
+        for t, (stream_id, off, sc) in zip((a, rh, rc), ((1, 0.10, 0.03), (2, 0.0, 1.0), (3, 0.0, 1.0))):
+            m._check(m.lib.me_uniforms(NEVT, 0, first, stream_id, off, sc, _ptr(t), sp))
+        m.compute(mom, a, rh, rc, out=out, stream=s)
+
+    for k in range(warmup):
+        step(k)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for k in range(steps):
+        step(warmup + k)
+    e1.record(s)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    e0.record(s)
+    for k in range(steps):
+        m._check(m.lib.me_rambo(m.handle, NEVT, 0, k * NEVT, 1500.0, _ptr(mom), sp))
+    e1.record(s)
+    torch.cuda.synchronize()
+    gen_ms = e0.elapsed_time(e1) / steps
+    launches = 4 + m.plan(NEVT)[0]  # RAMBO, three uniform streams, the compute call
+    m.close()
+    return {"value": NEVT / (ms * 1e-3), "unit": UNIT, "mode": mode, "ms_per_step": ms,
+            "rambo_ms_per_batch": gen_ms, "launches_per_step": launches,
+            "note": "device RAMBO + alpha_s + selection numbers + me_compute per step, no host transfer"}
+
+
 def time_unweight(me, warmup, reps):
     """GPU-assisted batch unweighting of the step's matrix elements: the whole batch and
     the 16384-event batches madevent uses (Section 3, Table 2); time per call on the
@@ -279,6 +325,7 @@ def run_gpu(args):
         raise SystemExit(f"headline mode {args.mode} failed: {head['error']}")
     value = world * NEVT / (head["ms"] * 1e-3)
     unw = time_unweight(head["me"], args.warmup, max(args.steps, 10))
+    testbed = time_testbed(args.mode, args.steps, args.warmup)
     peaks = {p: binding.alu_peak(p, 0.3) for p in ("fp64", "fp32")}
     per_launch_ms = head["ms"] / head["launches"]
     events_per_launch = NEVT / head["launches"]
@@ -326,6 +373,7 @@ def run_gpu(args):
                              "flops_per_event": head["flops_per_event"], "kernel": "me_kernel (amplitudes + colour sum)"},
                 "modes": acc,
                 "unweight": unw,
+                "testbed": testbed,
                 "cpu_baseline": cpu,
                 "alu_peaks_tflops": {k: v / 1e12 for k, v in peaks.items()}}
         print(json.dumps(line), flush=True)

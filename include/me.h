@@ -158,6 +158,33 @@ int me_compute_noalloc(me_handle* h, int64_t nevt, const double* momenta, const 
 int me_unweight(me_handle* h, int64_t nevt, const double* me, const double* wgt, const double* rnd,
                 double* w, uint8_t* accept, double* w_max, int64_t* n_accept, void* cuda_stream);
 
+/* Synthetic inputs generated on the device, for the standalone multi-event testbed
+ * (Section 2, Fig. 1b): a batch of test events is made and evaluated without a host
+ * round trip.  The numbers are those of the counter-based definition (Philox4x32-10,
+ * Salmon et al. SC'11): every uniform is a function of (seed, event index, stream,
+ * draw), key = (seed mod 2^32, seed div 2^32), counter = (event mod 2^32,
+ * event div 2^32, draw div 2, stream), draw j from output words (x0, x1) for even j and
+ * (x2, x3) for odd j, u = (((hi << 32 | lo) >> 12) + 1/2) 2^-52 in (0, 1); they do not
+ * depend on how a workload is split into batches.
+ *
+ * me_rambo: RAMBO momenta (Kleiss, Stirling, Ellis 1986) for the handle's process at
+ * sqrt_s, events first_event .. first_event + nevt - 1, from stream 0 (4 draws per
+ * final-state particle); beams along +z and -z; massive final states (the top mass of
+ * the handle's parameters) by one Newton-rescaled factor on all three-momenta.
+ *   momenta  device, FP64 [nevt][npar][4] (output, (E, px, py, pz))
+ * An event whose rescaling does not converge in 50 steps gets NaN momenta.
+ * Errors: ME_ERR_ARG (null handle, nevt < 0, host pointer, sqrt_s not above the sum of
+ * the final masses), ME_ERR_CUDA. */
+int me_rambo(me_handle* h, int64_t nevt, uint64_t seed, uint64_t first_event, double sqrt_s, double* momenta,
+             void* cuda_stream);
+
+/* me_uniforms: out[i] = offset + scale * u(seed, first_event + i, stream_id, draw 0),
+ * device FP64 [nevt].  Streams used by the benchmarks: 1 alpha_s (offset 0.10, scale
+ * 0.03), 2 rnd_hel, 3 rnd_col (offset 0, scale 1).  Errors: ME_ERR_ARG (nevt < 0,
+ * stream_id < 0, host pointer; message in me_last_error(NULL)), ME_ERR_CUDA. */
+int me_uniforms(int64_t nevt, uint64_t seed, uint64_t first_event, int stream_id, double offset, double scale,
+                double* out, void* cuda_stream);
+
 /* Process shape: external particles, helicity combinations, helicities kept by the
  * filter, colour flows, Feynman diagrams.  Any output pointer may be NULL. */
 int me_info(const me_handle* h, int* npar, int* ncomb, int* ngood, int* ncol, int* ndiag);

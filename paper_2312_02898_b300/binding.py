@@ -18,7 +18,7 @@ PRECISIONS = {"fp64": 0, "fp32": 1, "mixed": 2}
 # the C-ABI entry points declared in include/me.h
 EXPORTS = ("me_default_params", "me_init", "me_compute", "me_compute_host", "me_info", "me_good_helicities",
            "me_flops", "me_plan", "me_reserve", "me_launch_shape", "me_set_config", "me_last_error", "me_free",
-           "me_compute_noalloc", "me_unweight", "me_probe_alu_peak")
+           "me_compute_noalloc", "me_unweight", "me_rambo", "me_uniforms", "me_probe_alu_peak")
 
 
 class SMParams(ctypes.Structure):
@@ -56,6 +56,9 @@ def load(path: str = LIB_PATH):
     lib.me_reserve.argtypes = [vp, i64, vp]
     lib.me_launch_shape.argtypes = [vp, i64, ip, ip, ip, ip]
     lib.me_unweight.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp]
+    u64 = ctypes.c_uint64
+    lib.me_rambo.argtypes = [vp, i64, u64, u64, ctypes.c_double, vp, vp]
+    lib.me_uniforms.argtypes = [i64, u64, u64, ctypes.c_int, ctypes.c_double, ctypes.c_double, vp, vp]
     lib.me_info.argtypes = [vp, ip, ip, ip, ip, ip]
     lib.me_good_helicities.argtypes = [vp, ctypes.POINTER(ctypes.c_int32)]
     lib.me_flops.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
@@ -68,7 +71,7 @@ def load(path: str = LIB_PATH):
     lib.me_free.restype = None
     for f in ("me_init", "me_compute", "me_compute_host", "me_compute_noalloc", "me_info", "me_good_helicities",
               "me_flops", "me_set_config", "me_plan", "me_reserve", "me_launch_shape", "me_unweight",
-              "me_probe_alu_peak"):
+              "me_rambo", "me_uniforms", "me_probe_alu_peak"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -93,6 +96,18 @@ def alu_peak(precision: str, seconds: float = 0.3) -> float:
 
 def _ptr(t):
     return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def device_uniforms(nevt, seed, first_event, stream_id, offset=0.0, scale=1.0, stream=None):
+    """offset + scale * u for events first_event .. first_event + nevt - 1, generated on
+    the device (the same numbers as phasespace.uniforms)"""
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    out = torch.empty(nevt, dtype=torch.float64, device=s.device)
+    rc = load().me_uniforms(nevt, seed, first_event, stream_id, offset, scale, _ptr(out), ctypes.c_void_p(s.cuda_stream))
+    if rc != ME_OK:
+        raise MEError(rc, load().me_last_error(None).decode())
+    return out
 
 
 class MatrixElement:
@@ -194,6 +209,15 @@ class MatrixElement:
         self._check(self.lib.me_unweight(self.handle, n, _ptr(me), _ptr(wgt), _ptr(rnd), _ptr(w), _ptr(acc),
                                          _ptr(wmax), _ptr(nacc), ctypes.c_void_p(s.cuda_stream)))
         return w, acc, wmax, nacc
+
+    def rambo(self, nevt, seed=0, first_event=0, sqrt_s=1500.0, stream=None):
+        """RAMBO momenta for this process generated on the device: a [nevt][npar][4] tensor"""
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream()
+        mom = torch.empty((nevt, self.npar, 4), dtype=torch.float64, device=s.device)
+        self._check(self.lib.me_rambo(self.handle, nevt, seed, first_event, sqrt_s, _ptr(mom),
+                                      ctypes.c_void_p(s.cuda_stream)))
+        return mom
 
     def compute_raw(self, nevt, momenta_ptr, alphas_ptr, rnd_hel_ptr, rnd_col_ptr, me_ptr, sel_hel_ptr,
                     sel_col_ptr, stream_ptr):

@@ -66,6 +66,7 @@ void fill_common(const me_handle* h, MeLaunch& a);
 bool is_device_ptr(const void* p);
 Carve carve(const ProcessOps* ops, const LaunchNeeds& nd, int ngood, int64_t rows, bool want_hel, bool want_col);
 int persistent_grid(const me_handle* h, const LaunchNeeds& nd, int64_t nevt);
+std::vector<double> final_masses(const ProcessOps* ops, double mt);
 cudaError_t launch_chunks(const ProcessOps* ops, int prec, int config, MeLaunch a, int64_t nevt, int64_t chunk,
                           int grid, int block, int hsplit,
                           const Carve& cv, void* wsp, cudaStream_t s);
