@@ -454,8 +454,11 @@ def run_serving(args):
     import torch
     mean_events = float(np.mean([r[2].shape[0] for r in reqs]))
     out = {}
-    for prec in args.serving_precisions.split(","):
-        server = serving.Server([p for p, _ in serving.STREAM_PROCESSES], precision=prec, n_slots=args.serving_slots)
+    runs = [(prec, "srpt") for prec in args.serving_precisions.split(",")]
+    runs.insert(1, (runs[0][0], "fifo"))  # the same precision with first-come scheduling, for comparison
+    for prec, policy in runs:
+        server = serving.Server([p for p, _ in serving.STREAM_PROCESSES], precision=prec, n_slots=args.serving_slots,
+                                policy=policy, chunk_events=args.serving_chunk)
         try:
             t0 = time.perf_counter()
             for p, _ in serving.STREAM_PROCESSES:
@@ -463,20 +466,24 @@ def run_serving(args):
                     server.warm(p, b)
             warm_s = time.perf_counter() - t0
             first = not out
-            ncap = args.serving_warmup + (args.serving_requests // 4 if first else args.serving_requests_other // 4)
-            cap = serving.run_saturated(server, reqs[:ncap])
-            res = {"capacity_me_per_s": cap, "graphs": len(server.buffers), "warm_s": warm_s,
-                   "precision_per_process": server.precision, "load": {}}
+            same_stream = first or policy == "fifo"   # fifo replays the whole stream beside srpt
+            if policy == "fifo":
+                cap = next(iter(out.values()))["capacity_me_per_s"]
+            else:
+                ncap = args.serving_warmup + (args.serving_requests // 4 if first else args.serving_requests_other // 4)
+                cap = serving.run_saturated(server, reqs[:ncap])
+            res = {"capacity_me_per_s": cap, "graphs": len(server.buffers), "warm_s": warm_s, "policy": policy,
+                   "chunk_events": server.chunk, "precision_per_process": server.precision, "load": {}}
             loads = [float(x) for x in args.serving_loads.split(",")] if first else [0.7]
             # the slower precisions replay a prefix of the same stream
-            sub = reqs if first else reqs[: args.serving_warmup + args.serving_requests_other]
+            sub = reqs if same_stream else reqs[: args.serving_warmup + args.serving_requests_other]
             for frac in loads:
                 rate = frac * cap / mean_events                   # requests per second
                 st = serving.run_open_loop(server, sub, rate_scale=rate, warmup=args.serving_warmup)
                 st["offered_requests_per_s"] = rate
                 st["offered_me_per_s"] = frac * cap
                 res["load"][f"{int(round(frac * 100))}%"] = st
-            out[prec] = res
+            out[prec if policy == "srpt" else f"{prec}_fifo"] = res
         finally:
             server.close()
             del server
@@ -509,6 +516,7 @@ def main():
     ap.add_argument("--serving-requests-other", type=int, default=300,
                     help="requests of the stream replayed for the precisions after the first")
     ap.add_argument("--serving-slots", type=int, default=4)
+    ap.add_argument("--serving-chunk", type=int, default=16384, help="events per chunk of a large request")
     ap.add_argument("--serving-loads", default="0.5,0.7,0.9,1.1",
                     help="offered load as fractions of capacity (first precision; the others run at 0.7)")
     ap.add_argument("--serving-precisions", default="mixed,fp64")

@@ -93,10 +93,12 @@ struct Strided {
 //   W_MODE   colour weights: 0 registers, 1 shared memory, 2 global workspace
 //   S_MODE   slot buffer: 0 none, 1 shared memory, 2 global workspace
 //   K_MODE   momentum table: 1 shared memory, 2 global workspace
-//   SYNC     a block barrier at the top of every helicity
-template <int V_, int BLOCK_, int DEN_MODE, int J_MODE, int W_MODE, int S_MODE, int K_MODE, bool SYNC = false>
+//   SYNC     block barriers in the helicity body (every 24 schedule steps)
+//   MINB     blocks per SM the compiler must fit (caps the registers per thread)
+template <int V_, int BLOCK_, int DEN_MODE, int J_MODE, int W_MODE, int S_MODE, int K_MODE, bool SYNC = false,
+          int MINB = 1>
 struct Layout {
-  static constexpr int V = V_, BLOCK = BLOCK_;
+  static constexpr int V = V_, BLOCK = BLOCK_, minb = MINB;
   static constexpr int den_mode = DEN_MODE, j_mode = J_MODE;
   // "view": an array laid out [index][BLOCK] (shared or global) rather than registers
   static constexpr bool den_view = DEN_MODE != 0, j_view = J_MODE != 0;
@@ -187,7 +189,7 @@ __device__ __forceinline__ cx<R>* j_tile(const MeLaunch& a) {
 }
 
 template <class P, class R, class L>
-__global__ void __launch_bounds__(L::BLOCK) me_kernel(const MeLaunch a) {
+__global__ void __launch_bounds__(L::BLOCK, L::minb) me_kernel(const MeLaunch a) {
   constexpr int BLOCK = L::BLOCK;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int tid = threadIdx.x;

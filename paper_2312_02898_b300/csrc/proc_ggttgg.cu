@@ -34,41 +34,41 @@ template <> struct MixedCfg<2> { using L = Layout<1, 128, true, true, 1, 2, 2>; 
 template <> struct MixedCfg<3> { using L = Layout<2, 128, true, true, 1, 2, 2>; static constexpr int NTERM = 3; static constexpr bool F16 = false; };
 
 LaunchNeeds needs(int prec, int config) {
-  switch (prec * 8 + config) {
+  switch (prec * 16 + config) {
     case 0: return needs_of<P, Cfg<0, 0>::R, Cfg<0, 0>::L>();
     case 1: return needs_of<P, Cfg<0, 1>::R, Cfg<0, 1>::L>();
     case 2: return needs_of<P, Cfg<0, 2>::R, Cfg<0, 2>::L>();
     case 3: return needs_of<P, Cfg<0, 3>::R, Cfg<0, 3>::L>();
-    case 8: return needs_of<P, Cfg<1, 0>::R, Cfg<1, 0>::L>();
-    case 9: return needs_of<P, Cfg<1, 1>::R, Cfg<1, 1>::L>();
-    case 10: return needs_of<P, Cfg<1, 2>::R, Cfg<1, 2>::L>();
-    case 11: return needs_of<P, Cfg<1, 3>::R, Cfg<1, 3>::L>();
-    case 12: return needs_of<P, Cfg<1, 4>::R, Cfg<1, 4>::L>();
-    case 13: return needs_of<P, Cfg<1, 5>::R, Cfg<1, 5>::L>();
-    case 16: return needs_mixed_of<P, MixedCfg<0>::L, MixedCfg<0>::NTERM, MixedCfg<0>::F16>();
-    case 17: return needs_mixed_of<P, MixedCfg<1>::L, MixedCfg<1>::NTERM, MixedCfg<1>::F16>();
-    case 18: return needs_mixed_of<P, MixedCfg<2>::L, MixedCfg<2>::NTERM, MixedCfg<2>::F16>();
-    case 19: return needs_mixed_of<P, MixedCfg<3>::L, MixedCfg<3>::NTERM, MixedCfg<3>::F16>();
+    case 16: return needs_of<P, Cfg<1, 0>::R, Cfg<1, 0>::L>();
+    case 17: return needs_of<P, Cfg<1, 1>::R, Cfg<1, 1>::L>();
+    case 18: return needs_of<P, Cfg<1, 2>::R, Cfg<1, 2>::L>();
+    case 19: return needs_of<P, Cfg<1, 3>::R, Cfg<1, 3>::L>();
+    case 20: return needs_of<P, Cfg<1, 4>::R, Cfg<1, 4>::L>();
+    case 21: return needs_of<P, Cfg<1, 5>::R, Cfg<1, 5>::L>();
+    case 32: return needs_mixed_of<P, MixedCfg<0>::L, MixedCfg<0>::NTERM, MixedCfg<0>::F16>();
+    case 33: return needs_mixed_of<P, MixedCfg<1>::L, MixedCfg<1>::NTERM, MixedCfg<1>::F16>();
+    case 34: return needs_mixed_of<P, MixedCfg<2>::L, MixedCfg<2>::NTERM, MixedCfg<2>::F16>();
+    case 35: return needs_mixed_of<P, MixedCfg<3>::L, MixedCfg<3>::NTERM, MixedCfg<3>::F16>();
     default: return LaunchNeeds{0, 0, 0, 0, false, 128, 1};
   }
 }
 
 cudaError_t launch(int prec, int config, const MeLaunch& a, cudaStream_t s) {
-  switch (prec * 8 + config) {
+  switch (prec * 16 + config) {
     case 0: return launch_me<P, Cfg<0, 0>::R, Cfg<0, 0>::L>(a, s);
     case 1: return launch_me<P, Cfg<0, 1>::R, Cfg<0, 1>::L>(a, s);
     case 2: return launch_me<P, Cfg<0, 2>::R, Cfg<0, 2>::L>(a, s);
     case 3: return launch_me<P, Cfg<0, 3>::R, Cfg<0, 3>::L>(a, s);
-    case 8: return launch_me<P, Cfg<1, 0>::R, Cfg<1, 0>::L>(a, s);
-    case 9: return launch_me<P, Cfg<1, 1>::R, Cfg<1, 1>::L>(a, s);
-    case 10: return launch_me<P, Cfg<1, 2>::R, Cfg<1, 2>::L>(a, s);
-    case 11: return launch_me<P, Cfg<1, 3>::R, Cfg<1, 3>::L>(a, s);
-    case 12: return launch_me<P, Cfg<1, 4>::R, Cfg<1, 4>::L>(a, s);
-    case 13: return launch_me<P, Cfg<1, 5>::R, Cfg<1, 5>::L>(a, s);
-    case 16: return launch_mixed<P, MixedCfg<0>::L, MixedCfg<0>::NTERM, MixedCfg<0>::F16>(a, s);
-    case 17: return launch_mixed<P, MixedCfg<1>::L, MixedCfg<1>::NTERM, MixedCfg<1>::F16>(a, s);
-    case 18: return launch_mixed<P, MixedCfg<2>::L, MixedCfg<2>::NTERM, MixedCfg<2>::F16>(a, s);
-    case 19: return launch_mixed<P, MixedCfg<3>::L, MixedCfg<3>::NTERM, MixedCfg<3>::F16>(a, s);
+    case 16: return launch_me<P, Cfg<1, 0>::R, Cfg<1, 0>::L>(a, s);
+    case 17: return launch_me<P, Cfg<1, 1>::R, Cfg<1, 1>::L>(a, s);
+    case 18: return launch_me<P, Cfg<1, 2>::R, Cfg<1, 2>::L>(a, s);
+    case 19: return launch_me<P, Cfg<1, 3>::R, Cfg<1, 3>::L>(a, s);
+    case 20: return launch_me<P, Cfg<1, 4>::R, Cfg<1, 4>::L>(a, s);
+    case 21: return launch_me<P, Cfg<1, 5>::R, Cfg<1, 5>::L>(a, s);
+    case 32: return launch_mixed<P, MixedCfg<0>::L, MixedCfg<0>::NTERM, MixedCfg<0>::F16>(a, s);
+    case 33: return launch_mixed<P, MixedCfg<1>::L, MixedCfg<1>::NTERM, MixedCfg<1>::F16>(a, s);
+    case 34: return launch_mixed<P, MixedCfg<2>::L, MixedCfg<2>::NTERM, MixedCfg<2>::F16>(a, s);
+    case 35: return launch_mixed<P, MixedCfg<3>::L, MixedCfg<3>::NTERM, MixedCfg<3>::F16>(a, s);
     default: return cudaErrorNotSupported;
   }
 }

@@ -11,9 +11,15 @@ and device memory are free, so work from many requests overlaps on the device.
   result, and a request's results are the same alone and in any mix.
 * Each (slot, process, bucket) owns pinned host staging, device buffers and, once used,
   a captured CUDA graph of [copy in -> me_compute -> copy out] that is replayed.
-* Admission: a request starts when a slot is idle and the device bytes of all running
-  requests plus its own stay within the memory budget.
-* Latency is measured from submit() to the moment its results are on the host.
+* A request larger than the chunk size (16384 events by default) runs as several
+  chunks.  When a slot frees up, the scheduler takes the next chunk either of the oldest
+  request ("fifo") or of the request with the least remaining work, events times the
+  process's flops per event ("srpt"), so that small requests need not wait behind a
+  large one.
+* Admission: a chunk starts when a slot is idle and the device bytes of all running
+  chunks plus its own stay within the memory budget.
+* Latency is measured from submit() to the moment all of a request's results are on
+  the host.
 
 Only host bookkeeping lives here; every evaluation runs in libme_b300.so.
 """
@@ -76,7 +82,7 @@ class MemoryAdmission:
         assert self.used >= 0
 
 
-@dataclass
+@dataclass(eq=False)  # requests compare by identity (the scheduler removes them from its queue)
 class Request:
     process: str
     momenta: np.ndarray
@@ -86,6 +92,14 @@ class Request:
     t_submit: float = 0.0
     future: Future = field(default_factory=Future)
     tag: object = None
+    cost: float = 1.0        # flops per event of the process (scheduling weight)
+    next_event: int = 0      # first event not yet dispatched
+    outstanding: int = 0     # chunks on the GPU
+    out: tuple = None        # (me, sel_hel, sel_col) filled chunk by chunk
+
+    @property
+    def nevt(self):
+        return self.momenta.shape[0]
 
 
 class _Buffers:
@@ -115,7 +129,11 @@ class _Buffers:
 
 class Server:
     def __init__(self, processes, precision="mixed", n_slots=4, mem_budget_bytes=8 << 30, use_graphs=True,
-                 device=0, params=None):
+                 device=0, params=None, policy="srpt", chunk_events=16384):
+        if policy not in ("fifo", "srpt"):
+            raise ValueError(f"unknown scheduling policy {policy!r}")
+        self.policy = policy
+        self.chunk = bucket_for(chunk_events)
         import torch
         from paper_2312_02898_b300.binding import MatrixElement, MEError
         self.torch = torch
@@ -150,19 +168,27 @@ class Server:
         self.stop = False
         self.done = []                              # (process, nevt, latency s, finish time, tag)
         self.max_running = 0                        # most requests on the GPU at once
+        self.error = None                           # what stopped the loop, if anything
         self.thread = threading.Thread(target=self._loop, daemon=True)
         self.thread.start()
 
     # ------------------------------------------------------------------ API
     def submit(self, process, momenta, alphas=None, rnd_hel=None, rnd_col=None, tag=None) -> Future:
         n = momenta.shape[0]
-        bucket_for(n)
+        if n < 1:
+            raise ValueError("a request needs at least one event")
+        if process not in self.handles:
+            raise KeyError(f"process {process!r} is not served here")
         rh = rnd_hel if rnd_hel is not None else np.full(n, 0.5)
         rc = rnd_col if rnd_col is not None else np.full(n, 0.5)
         r = Request(process, np.ascontiguousarray(momenta, dtype=np.float64),
                     None if alphas is None else np.ascontiguousarray(alphas, dtype=np.float64),
                     np.ascontiguousarray(rh, dtype=np.float64), np.ascontiguousarray(rc, dtype=np.float64), tag=tag)
+        r.cost = float(self.handles[process].flops_per_event())
+        r.out = (np.empty(n), np.empty(n, dtype=np.int32), np.empty(n, dtype=np.int32))
         r.t_submit = time.perf_counter()
+        if self.error is not None:
+            raise RuntimeError("the serving loop has stopped") from self.error
         with self.cv:
             self.queue.append(r)
             self.cv.notify()
@@ -175,7 +201,10 @@ class Server:
         self.thread.join()
 
     def warm(self, process, bucket, slots=None):
-        """allocate buffers, grow workspaces and capture graphs ahead of traffic"""
+        """allocate buffers, grow workspaces and capture graphs ahead of traffic (buckets
+        above the chunk size are never used)"""
+        if bucket > self.chunk:
+            return
         for s in (slots if slots is not None else range(len(self.streams))):
             self._prepare(s, process, bucket)
 
@@ -226,16 +255,21 @@ class Server:
                       b.d_me.data_ptr(), b.d_sh.data_ptr(), b.d_sc.data_ptr(), s.cuda_stream)
 
     def _launch(self, slot, r: Request):
-        n = r.momenta.shape[0]
+        """dispatch the next chunk of r on 'slot'; False when memory admission refuses"""
+        lo = r.next_event
+        n = min(self.chunk, r.nevt - lo)
         nb = bucket_for(n)
         b = self._prepare(slot, r.process, nb)
         if not self.admission.try_take(b.nbytes):
             return False
-        a = r.alphas if r.alphas is not None else np.full(n, self.handles[r.process].params.alphas_default)
-        b.h_mom.numpy()[:] = pad_to(r.momenta, nb)
+        sl = slice(lo, lo + n)
+        a = r.alphas[sl] if r.alphas is not None else np.full(n, self.handles[r.process].params.alphas_default)
+        b.h_mom.numpy()[:] = pad_to(r.momenta[sl], nb)
         b.h_as.numpy()[:] = pad_to(a, nb)
-        b.h_rh.numpy()[:] = pad_to(r.rnd_hel, nb)
-        b.h_rc.numpy()[:] = pad_to(r.rnd_col, nb)
+        b.h_rh.numpy()[:] = pad_to(r.rnd_hel[sl], nb)
+        b.h_rc.numpy()[:] = pad_to(r.rnd_col[sl], nb)
+        r.next_event = lo + n
+        r.outstanding += 1
         s = self.streams[slot]
         if b.graph is not None:
             with self.torch.cuda.stream(s):
@@ -246,21 +280,43 @@ class Server:
             self._copy_out(b, s, nb)
         ev = self.torch.cuda.Event()
         ev.record(s)
-        self.slot_busy[slot] = (r, b, ev, b.nbytes)
+        self.slot_busy[slot] = (r, b, ev, b.nbytes, lo, n)
         self.max_running = max(self.max_running, sum(x is not None for x in self.slot_busy))
         return True
 
     def _complete(self, slot):
-        r, b, ev, nbytes = self.slot_busy[slot]
-        n = r.momenta.shape[0]
-        out = (b.h_me.numpy()[:n].copy(), b.h_sh.numpy()[:n].copy(), b.h_sc.numpy()[:n].copy())
+        r, b, ev, nbytes, lo, n = self.slot_busy[slot]
+        r.out[0][lo:lo + n] = b.h_me.numpy()[:n]
+        r.out[1][lo:lo + n] = b.h_sh.numpy()[:n]
+        r.out[2][lo:lo + n] = b.h_sc.numpy()[:n]
         self.slot_busy[slot] = None
         self.admission.give(nbytes)
-        now = time.perf_counter()
-        self.done.append((r.process, n, now - r.t_submit, now, r.tag))
-        r.future.set_result(out)
+        r.outstanding -= 1
+        if r.outstanding == 0 and r.next_event == r.nevt:
+            now = time.perf_counter()
+            self.done.append((r.process, r.nevt, now - r.t_submit, now, r.tag))
+            r.future.set_result(r.out)
+
+    def _pick(self):
+        """the request whose next chunk goes out: the oldest with work left, or the one
+        with the least remaining work"""
+        if self.policy == "fifo":
+            return self.queue[0]
+        return min(self.queue, key=lambda q: (q.nevt - q.next_event) * q.cost)
 
     def _loop(self):
+        try:
+            self._serve()
+        except BaseException as e:  # fail every pending request instead of leaving it hanging
+            self.error = e
+            with self.lock:
+                pending = list(self.queue) + [b[0] for b in self.slot_busy if b is not None]
+                self.queue.clear()
+            for r in pending:
+                if not r.future.done():
+                    r.future.set_exception(e)
+
+    def _serve(self):
         while True:
             with self.cv:
                 if self.stop and not self.queue and all(x is None for x in self.slot_busy):
@@ -277,8 +333,10 @@ class Server:
                     if not self.queue:
                         break
                     if self.slot_busy[slot] is None:
-                        if self._launch(slot, self.queue[0]):
-                            self.queue.popleft()
+                        r = self._pick()
+                        if self._launch(slot, r):
+                            if r.next_event == r.nevt:
+                                self.queue.remove(r)
                             progressed = True
             if not progressed:
                 time.sleep(20e-6)

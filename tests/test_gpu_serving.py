@@ -76,3 +76,44 @@ def test_overlapping_requests_are_admitted_while_others_run():
         assert server.max_running >= 2
     finally:
         server.close()
+
+
+def test_large_requests_run_in_chunks_with_the_same_results():
+    """A request larger than the chunk size is split; its result equals the request
+    evaluated alone, and requests beyond the largest bucket are served too."""
+    from paper_2312_02898_b300 import serving
+    server = serving.Server(("g g > t t~ g", "g g > t t~ g g"), precision="mixed", n_slots=3, chunk_events=4096)
+    try:
+        reqs = [("g g > t t~ g g", 10000, 5), ("g g > t t~ g", 70000, 6), ("g g > t t~ g g", 4096, 7)]
+        batches = [(p,) + make_batch(p, n, seed=s, alphas="uniform") for p, n, s in reqs]
+        futs = [server.submit(*b) for b in batches]
+        for (p, mom, a, rh, rc), f in zip(batches, futs):
+            me, sh, sc = f.result(timeout=300)
+            me0, sh0, sc0 = _alone(server, p, mom, a, rh, rc)
+            np.testing.assert_array_equal(me, me0)
+            np.testing.assert_array_equal(sh, sh0)
+            np.testing.assert_array_equal(sc, sc0)
+    finally:
+        server.close()
+
+
+def test_srpt_lets_small_requests_pass_a_large_one():
+    """With the least-remaining-work policy, small requests submitted just after a large
+    one finish before it; with first-come scheduling they wait behind it."""
+    from paper_2312_02898_b300 import serving
+    big = ("g g > t t~ g g g",) + make_batch("g g > t t~ g g g", 24000, seed=1, alphas="uniform")
+    small = [("g g > t t~",) + make_batch("g g > t t~", 2000, seed=10 + k, alphas="uniform") for k in range(3)]
+    order = {}
+    for policy in ("srpt", "fifo"):
+        server = serving.Server(("g g > t t~", "g g > t t~ g g g"), precision="mixed", n_slots=1,
+                                chunk_events=4096, policy=policy)
+        try:
+            server.warm("g g > t t~", 2048)
+            server.warm("g g > t t~ g g g", 4096)
+            futs = [server.submit(*big, tag="big")] + [server.submit(*s, tag=f"s{k}") for k, s in enumerate(small)]
+            [f.result(timeout=600) for f in futs]
+            order[policy] = [x[4] for x in sorted(server.done, key=lambda x: x[3])]
+        finally:
+            server.close()
+    assert order["srpt"][-1] == "big"
+    assert order["fifo"][0] == "big"
