@@ -44,9 +44,9 @@ struct Carve {
   size_t total() const { return cum + colw + slots + ktab + den + jt; }
 };
 
-// A me_compute call: the main pass (in chunks when the slot buffer is global), the
-// rescue list of ill-conditioned events (FP32 and mixed modes) and the FP64 pass over
-// that list, and where each lives in the call's workspace.
+// A me_compute call: the main pass (one persistent launch per chunk of at most 2^30
+// events), the rescue list of ill-conditioned events (FP32 and mixed modes) and the
+// helicity-split FP64 pass over that list, and where each lives in the call's workspace.
 struct CallPlan {
   int prec = 0, config = 0;
   int64_t chunk = 0;
