@@ -43,12 +43,12 @@ ERR_BOUND = {"fp64": 1e-12, "fp32": 1e-5, "mixed": 1e-5}
 # 655360 events (profiles/me_kernel_*_655360.md); the traffic grows with the events
 # processed.  Keyed by the kernel's layout, so a changed default reports no traffic.
 DRAM_BYTES_PER_EVENT = {
-    ("fp64", "Layout<3, 64, 1, 1, 1, 2, 2, 1>"): 1.423e11 / 655360,
-    ("fp32", "Layout<1, 64, 1, 0, 1, 1, 2, 1>"): 1.239e9 / 655360,
-    ("mixed", "Layout<1, 128, 1, 1, 1, 2, 2, 1>"): 5.469e8 / 655360,
+    ("fp64", "Layout<3, 64, 1, 1, 1, 2, 2, 3, 1>"): 1.421e11 / 655360,
+    ("fp32", "Layout<1, 64, 1, 0, 1, 1, 2, 3, 1>"): 9.192e8 / 655360,
+    ("mixed", "Layout<1, 128, 1, 1, 1, 2, 2, 0, 1>"): 1.572e9 / 655360,
 }
-DEFAULT_LAYOUT = {"fp64": "Layout<3, 64, 1, 1, 1, 2, 2, 1>", "fp32": "Layout<1, 64, 1, 0, 1, 1, 2, 1>",
-                  "mixed": "Layout<1, 128, 1, 1, 1, 2, 2, 1>"}
+DEFAULT_LAYOUT = {"fp64": "Layout<3, 64, 1, 1, 1, 2, 2, 3, 1>", "fp32": "Layout<1, 64, 1, 0, 1, 1, 2, 3, 1>",
+                  "mixed": "Layout<1, 128, 1, 1, 1, 2, 2, 0, 1>"}
 
 
 def dist_env():

@@ -93,16 +93,18 @@ struct Strided {
 //   W_MODE   colour weights: 0 registers, 1 shared memory, 2 global workspace
 //   S_MODE   slot buffer: 0 none, 1 shared memory, 2 global workspace
 //   K_MODE   momentum table: 1 shared memory, 2 global workspace
-//   SYNC     block barriers in the helicity body (every 24 schedule steps)
+//   SYNC     0: no block barriers in the helicity body; k > 0: a barrier every 8k schedule
+//            steps (currents and diagram closings) and between diagram groups
 //   MINB     blocks per SM the compiler must fit (caps the registers per thread)
-template <int V_, int BLOCK_, int DEN_MODE, int J_MODE, int W_MODE, int S_MODE, int K_MODE, bool SYNC = false,
+template <int V_, int BLOCK_, int DEN_MODE, int J_MODE, int W_MODE, int S_MODE, int K_MODE, int SYNC = 0,
           int MINB = 1>
 struct Layout {
   static constexpr int V = V_, BLOCK = BLOCK_, minb = MINB;
   static constexpr int den_mode = DEN_MODE, j_mode = J_MODE;
   // "view": an array laid out [index][BLOCK] (shared or global) rather than registers
   static constexpr bool den_view = DEN_MODE != 0, j_view = J_MODE != 0;
-  static constexpr bool den_smem = DEN_MODE == 1, j_smem = J_MODE == 1, sync = SYNC;
+  static constexpr bool den_smem = DEN_MODE == 1, j_smem = J_MODE == 1;
+  static constexpr int sync = SYNC;
   static constexpr int w_mode = W_MODE, s_mode = S_MODE, k_mode = K_MODE;
 };
 
@@ -310,7 +312,7 @@ __global__ void __launch_bounds__(L::BLOCK, L::minb) me_kernel(const MeLaunch a)
     const int h = a.good[valid ? ih : a.ngood - 1];
     // keep the block's warps on the same stretch of the (very long, straight-line)
     // helicity body, so that instruction fetches are shared instead of thrashing
-    if constexpr (L::sync) __syncthreads();
+    if constexpr (L::sync > 0) __syncthreads();
     R cs;
     if constexpr (P::QCD && L::den_view && L::w_mode != 0) {
       cs = one_helicity<P, R, L>(h, R(a.mt), s_dg + tid, s_dt + tid, L::j_view ? s_J + tid : nullptr,

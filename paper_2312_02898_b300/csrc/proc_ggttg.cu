@@ -12,8 +12,8 @@ namespace meb300 {
 namespace {
 using P = proc_ggttg;
 template <int PREC, int C> struct Cfg;
-template <> struct Cfg<0, 0> { using R = double; using L = Layout<1, 128, false, false, 0, 1, 1, true>; };
-template <> struct Cfg<1, 0> { using R = float; using L = Layout<0, 128, false, false, 0, 0, 1, true>; };
+template <> struct Cfg<0, 0> { using R = double; using L = Layout<1, 128, false, false, 0, 1, 1, 3>; };
+template <> struct Cfg<1, 0> { using R = float; using L = Layout<0, 128, false, false, 0, 0, 1, 3>; };
 template <> struct Cfg<0, 1> { using R = double; using L = Layout<1, 128, false, false, 0, 1, 1>; };
 template <> struct Cfg<1, 1> { using R = float; using L = Layout<0, 128, false, false, 0, 0, 1>; };
 

@@ -13,25 +13,25 @@ namespace meb300 {
 namespace {
 using P = proc_ggttgg;
 template <int PREC, int C> struct Cfg;
-template <> struct Cfg<0, 0> { using R = double; using L = Layout<3, 64, true, true, 1, 2, 2, true>; };
-template <> struct Cfg<0, 1> { using R = double; using L = Layout<3, 64, true, true, 1, 2, 2>; };
-template <> struct Cfg<0, 2> { using R = double; using L = Layout<4, 64, true, true, 1, 2, 2>; };
-template <> struct Cfg<0, 3> { using R = double; using L = Layout<5, 64, true, true, 1, 2, 2>; };
-template <> struct Cfg<1, 0> { using R = float; using L = Layout<1, 64, true, false, 1, 1, 2, true>; };
-template <> struct Cfg<1, 1> { using R = float; using L = Layout<1, 128, true, false, 1, 1, 2, true>; };
-template <> struct Cfg<1, 2> { using R = float; using L = Layout<1, 64, true, false, 1, 1, 2>; };
-template <> struct Cfg<1, 3> { using R = float; using L = Layout<0, 128, true, false, 1, 0, 2>; };
-template <> struct Cfg<1, 4> { using R = float; using L = Layout<1, 128, true, false, 1, 2, 2>; };
-template <> struct Cfg<1, 5> { using R = float; using L = Layout<2, 128, true, false, 1, 2, 2>; };
+template <> struct Cfg<0, 0> { using R = double; using L = Layout<3, 64, 1, 1, 1, 2, 2, 3>; };
+template <> struct Cfg<0, 1> { using R = double; using L = Layout<3, 64, 1, 1, 1, 2, 2>; };
+template <> struct Cfg<0, 2> { using R = double; using L = Layout<4, 64, 1, 1, 1, 2, 2>; };
+template <> struct Cfg<0, 3> { using R = double; using L = Layout<5, 64, 1, 1, 1, 2, 2>; };
+template <> struct Cfg<1, 0> { using R = float; using L = Layout<1, 64, 1, 0, 1, 1, 2, 3>; };
+template <> struct Cfg<1, 1> { using R = float; using L = Layout<1, 128, 1, 0, 1, 1, 2, 3>; };
+template <> struct Cfg<1, 2> { using R = float; using L = Layout<1, 64, 1, 0, 1, 1, 2>; };
+template <> struct Cfg<1, 3> { using R = float; using L = Layout<0, 128, 1, 0, 1, 0, 2>; };
+template <> struct Cfg<1, 4> { using R = float; using L = Layout<1, 128, 1, 0, 1, 2, 2>; };
+template <> struct Cfg<1, 5> { using R = float; using L = Layout<2, 128, 1, 0, 1, 2, 2>; };
 
 // mixed precision: amplitude layout (views of J and the weights, 128 threads), the
-// number of 16-bit terms of the split colour-flow amplitudes, and the operand type
-// (the colour matrix of this process is exact in BF16)
+// number of 16-bit terms of the split colour-flow amplitudes (2 = the hi + lo split),
+// and the operand type (the colour matrix of this process is exact in BF16)
 template <int C> struct MixedCfg;
-template <> struct MixedCfg<0> { using L = Layout<1, 128, true, true, 1, 2, 2, true>; static constexpr int NTERM = 3; static constexpr bool F16 = false; };
-template <> struct MixedCfg<1> { using L = Layout<1, 128, true, true, 1, 2, 2>; static constexpr int NTERM = 3; static constexpr bool F16 = false; };
-template <> struct MixedCfg<2> { using L = Layout<1, 128, true, true, 1, 2, 2>; static constexpr int NTERM = 2; static constexpr bool F16 = false; };
-template <> struct MixedCfg<3> { using L = Layout<2, 128, true, true, 1, 2, 2>; static constexpr int NTERM = 3; static constexpr bool F16 = false; };
+template <> struct MixedCfg<0> { using L = Layout<1, 128, 1, 1, 1, 2, 2>; static constexpr int NTERM = 2; static constexpr bool F16 = false; };
+template <> struct MixedCfg<1> { using L = Layout<1, 128, 1, 1, 1, 2, 2, 3>; static constexpr int NTERM = 3; static constexpr bool F16 = false; };
+template <> struct MixedCfg<2> { using L = Layout<1, 128, 1, 1, 1, 2, 2>; static constexpr int NTERM = 3; static constexpr bool F16 = false; };
+template <> struct MixedCfg<3> { using L = Layout<2, 128, 1, 1, 1, 2, 2>; static constexpr int NTERM = 3; static constexpr bool F16 = false; };
 
 LaunchNeeds needs(int prec, int config) {
   switch (prec * 16 + config) {

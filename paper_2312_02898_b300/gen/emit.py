@@ -73,7 +73,7 @@ def _exact(cf, bits):
     return True
 
 
-SYNC_EVERY = 24  # schedule steps (currents and diagram closings) between block barriers
+SYNC_STEP = 8  # schedule steps (currents and diagram closings) between optional barrier points
 
 
 def _lit(x):
@@ -359,8 +359,8 @@ class Emitter:
                 if k in bounds:
                     groups.append(list(body))
                     body[:] = []
-                elif k and k % SYNC_EVERY == 0:
-                    body.append("  if constexpr (SYNC) MEB_BLOCK_SYNC();")
+                elif k and k % SYNC_STEP == 0:
+                    body.append(f"  if constexpr (SYNC > 0 && {k // SYNC_STEP} % SYNC == 0) MEB_BLOCK_SYNC();")
                 if t == "N":
                     emit_node(x, loc)
                 else:
@@ -460,31 +460,31 @@ class Emitter:
         lam = (f"  int lam[{self.npar}];\n  for (int i = 0; i < {self.npar}; ++i) "
                f"lam[i] = ((h >> ({self.npar - 1} - i)) & 1) ? 1 : -1;")
         for vi, (budget, group, nslot, groups) in enumerate(variants):
-            # SYNC: a block barrier every SYNC_EVERY steps and between diagram groups, which
-            # keeps the warps of a block on the same stretch of code (all threads of the
-            # block must then call the function together)
+            # SYNC > 0: a block barrier every SYNC * SYNC_STEP steps and between diagram
+            # groups, which keeps the warps of a block on the same stretch of code (all
+            # threads of the block must then call the function together)
             if not group:
-                out += ["", "template <int S, class R, bool SYNC = false, class DG, class DT, class JA>",
+                out += ["", "template <int S, class R, int SYNC = 0, class DG, class DT, class JA>",
                         f"static HD void jamps_v{vi}(int h, R mt, const DG& dg, const DT& dt, JA& J, cx<R>* ws,"
                         " const R* kt) {", lam]
                 out += groups[0]
                 out.append("}")
             else:
                 for gi, gbody in enumerate(groups):
-                    out += ["", "template <int S, class R, bool SYNC = false, class DG, class DT, class JA>",
+                    out += ["", "template <int S, class R, int SYNC = 0, class DG, class DT, class JA>",
                             f"static NOINL void jamps_v{vi}_g{gi}(int h, R mt, DG dg, DT dt, JA J, cx<R>* ws, const R* kt) {{",
                             lam]
                     out += gbody
                     out.append("}")
-                out += ["", "template <int S, class R, bool SYNC = false, class DG, class DT, class JA>",
+                out += ["", "template <int S, class R, int SYNC = 0, class DG, class DT, class JA>",
                         f"static HD void jamps_v{vi}(int h, R mt, const DG& dg, const DT& dt, JA& J, cx<R>* ws,"
                         " const R* kt) {"]
                 for gi in range(len(groups)):
                     if gi:
-                        out.append("  if constexpr (SYNC) MEB_BLOCK_SYNC();")
+                        out.append("  if constexpr (SYNC > 0) MEB_BLOCK_SYNC();")
                     out.append(f"  jamps_v{vi}_g{gi}<S, R, SYNC>(h, mt, dg, dt, J, ws, kt);")
                 out.append("}")
-        out += ["", "template <int V, int S, class R, bool SYNC = false, class DG, class DT, class JA>",
+        out += ["", "template <int V, int S, class R, int SYNC = 0, class DG, class DT, class JA>",
                 "static HD void jamps(int h, R mt, const DG& dg, const DT& dt, JA& J, cx<R>* ws, const R* kt) {"]
         for vi in range(len(variants)):
             out.append(f"  {'if' if vi == 0 else 'else if'} constexpr (V == {vi}) jamps_v{vi}<S, R, SYNC>(h, mt, dg, dt, J, ws, kt);")
@@ -533,7 +533,7 @@ class Emitter:
                "template <int V> static HD constexpr int nslot() { return 0; }",
                "template <int V> static HD constexpr bool grouped() { return false; }",
                "static constexpr int BUDGET[1] = {-1};",
-               "template <int V, int S, class R, bool SYNC = false, class DG, class DT, class JA>",
+               "template <int V, int S, class R, int SYNC = 0, class DG, class DT, class JA>",
                "static HD void jamps(int h, const R* zc, const DG& dg, const DT& dt, JA& J, cx<R>*, const R* kt) {",
                "  int lam[4];",
                "  for (int i = 0; i < 4; ++i) lam[i] = ((h >> (3 - i)) & 1) ? 1 : -1;",
