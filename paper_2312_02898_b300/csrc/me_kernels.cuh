@@ -1,4 +1,6 @@
-// me_kernels.cuh -- the event-parallel matrix-element kernel (one event per thread).
+// me_kernels.cuh -- the event-parallel matrix-element kernel: one event per thread (or,
+// for the FP64 rescue pass, one event per group of up to 32 threads that split its
+// helicities), on a persistent grid that walks the batch tile by tile.
 //
 // Per event:
 //   1. load the FP64 momenta (array of structures, 16-byte vector loads);
@@ -12,8 +14,8 @@
 //
 // Where each per-thread array lives is a per-process, per-precision choice (a Layout):
 // registers for small processes; shared memory laid out [index][thread] so that a
-// warp touches consecutive words; or a global workspace laid out [index][event] so
-// that a warp's accesses coalesce.  The generated code keeps at most a fixed number of
+// warp touches consecutive words; or a global tile per block laid out [index][thread]
+// so that a warp's accesses coalesce.  The generated code keeps at most a fixed number of
 // currents in registers (the variant's budget) and the rest in a slot buffer.
 #pragma once
 

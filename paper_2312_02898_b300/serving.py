@@ -6,9 +6,9 @@ Section 3) -- are queued on the host and admitted onto the GPU as soon as a stre
 and device memory are free, so work from many requests overlaps on the device.
 
 * Every process keeps one handle (helicity list, couplings, colour matrix resident).
-* A batch is padded to a size bucket (powers of two from 256 to 65536 events) by
-  repeating its last event; events are independent, so padding does not change any
-  result, and a request's results are the same alone and in any mix.
+* A chunk is padded to a size bucket (powers of two from 256 events up to the chunk
+  size) by repeating its last event; events are independent, so padding does not
+  change any result, and a request's results are the same alone and in any mix.
 * Each (slot, process, bucket) owns pinned host staging, device buffers and, once used,
   a captured CUDA graph of [copy in -> me_compute -> copy out] that is replayed.
 * A request larger than the chunk size (16384 events by default) runs as several
