@@ -150,8 +150,10 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (RAMBO, Philox4x32-10 seed 0)",
-            "config": {"workload": f"{PROCESS}, sqrt(s)=1500 GeV, alpha_s~U[0.10,0.13]",
-                       "events_per_step": sample, "full_batch": NEVT, "precision": "fp64"},
+            "config": {"workload": f"{PROCESS}, sqrt(s)=1500 GeV, alpha_s~U[0.10,0.13], both selections",
+                       "events_per_gpu": NEVT, "global_batch": NEVT, "precision": "fp64",
+                       "parallelism": "host cores (OpenMP over events), rank 0 only",
+                       "events_per_step": sample},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{sample} events of the {NEVT}-event workload per step"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
