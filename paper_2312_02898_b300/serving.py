@@ -64,6 +64,15 @@ def percentile(values, q):
     return v[f] if f == c else v[f] + (v[c] - v[f]) * (k - f)
 
 
+def pick_next(queue, policy):
+    """the request whose next chunk goes out: the oldest with events left ("fifo"), or
+    the one with the least remaining work, undispatched events times flops per event
+    ("srpt"; ties go to the older request)"""
+    if policy == "fifo":
+        return queue[0]
+    return min(queue, key=lambda q: (q.nevt - q.next_event) * q.cost)
+
+
 class MemoryAdmission:
     """Device-byte budget shared by running requests (host-side accounting)."""
 
@@ -298,11 +307,7 @@ class Server:
             r.future.set_result(r.out)
 
     def _pick(self):
-        """the request whose next chunk goes out: the oldest with work left, or the one
-        with the least remaining work"""
-        if self.policy == "fifo":
-            return self.queue[0]
-        return min(self.queue, key=lambda q: (q.nevt - q.next_event) * q.cost)
+        return pick_next(self.queue, self.policy)
 
     def _loop(self):
         try:

@@ -1,5 +1,6 @@
-"""Host-side logic of the serving loop: buckets, padding, admission, percentiles and
-the request stream (no GPU)."""
+"""Host-side logic of the serving loop: buckets, padding, admission, percentiles, the
+request stream and the scheduling policies (no GPU)."""
+import collections
 import math
 
 import numpy as np
@@ -75,3 +76,35 @@ def test_request_stream_weights_are_the_process_class_weights():
     assert w["g g > t t~"] + w["g g > t t~ g"] == pytest.approx(0.3)
     assert w["g g > t t~ g g"] == pytest.approx(0.4)
     assert w["g g > t t~ g g g"] == pytest.approx(0.2)
+
+
+def _req(n, cost, done=0):
+    r = serving.Request("p", np.zeros((n, 4, 4)), None, np.zeros(n), np.zeros(n))
+    r.cost, r.next_event = cost, done
+    return r
+
+
+def test_fifo_takes_the_oldest_request():
+    q = [_req(60000, 1e7), _req(300, 1e4), _req(5000, 1e5)]
+    assert serving.pick_next(q, "fifo") is q[0]
+
+
+def test_srpt_takes_the_least_remaining_work():
+    big, small, mid = _req(60000, 1e7), _req(300, 1e4), _req(5000, 1e5)
+    q = [big, small, mid]
+    assert serving.pick_next(q, "srpt") is small
+    # remaining work counts only undispatched events: a nearly finished large request
+    # goes before a fresh medium one
+    big.next_event = 59990
+    assert serving.pick_next([mid, big], "srpt") is big
+    # equal work: the older request
+    a, b = _req(1000, 1e5), _req(1000, 1e5)
+    assert serving.pick_next([a, b], "srpt") is a
+
+
+def test_requests_compare_by_identity():
+    a, b = _req(10, 1.0), _req(10, 1.0)
+    assert a != b and a == a
+    q = collections.deque([a, b])
+    q.remove(b)
+    assert list(q) == [a]
