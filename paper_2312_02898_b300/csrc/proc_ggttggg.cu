@@ -13,13 +13,13 @@ namespace meb300 {
 namespace {
 using P = proc_ggttggg;
 template <int PREC, int C> struct Cfg;
-// FP64: all per-thread arrays in global tiles, four 64-thread blocks per SM (shared-
-// memory denominators and J, 176 KB, allow one: 1.6x slower)
-template <> struct Cfg<0, 0> { using R = double; using L = Layout<0, 64, 2, 2, 2, 2, 2>; };
-template <> struct Cfg<0, 1> { using R = double; using L = Layout<0, 64, 1, 1, 2, 2, 2>; };
-// FP32: every per-thread array in global tiles leaves shared memory free for two
-// blocks per SM, which doubles the warps that hide latency (1.7x the throughput of
-// shared-memory denominators and J at one block per SM)
+// Every per-thread array in global tiles leaves shared memory free, so registers alone
+// bound the blocks per SM: four 64-thread blocks in FP64, two 128-thread blocks in FP32
+// (with shared-memory denominators and J, 176 KB, one block fits: 1.6-1.7x slower).
+// Block barriers between diagram groups add 13% in FP64 and nothing in FP32.
+template <> struct Cfg<0, 0> { using R = double; using L = Layout<0, 64, 2, 2, 2, 2, 2, 3>; };
+template <> struct Cfg<0, 1> { using R = double; using L = Layout<0, 64, 2, 2, 2, 2, 2>; };
+template <> struct Cfg<0, 2> { using R = double; using L = Layout<0, 64, 1, 1, 2, 2, 2>; };
 template <> struct Cfg<1, 0> { using R = float; using L = Layout<0, 128, 2, 2, 2, 2, 2>; };
 template <> struct Cfg<1, 1> { using R = float; using L = Layout<0, 128, 1, 1, 2, 2, 2>; };
 
@@ -33,6 +33,7 @@ LaunchNeeds needs(int prec, int config) {
   switch (prec * 8 + config) {
     case 0: return needs_of<P, Cfg<0, 0>::R, Cfg<0, 0>::L>();
     case 1: return needs_of<P, Cfg<0, 1>::R, Cfg<0, 1>::L>();
+    case 2: return needs_of<P, Cfg<0, 2>::R, Cfg<0, 2>::L>();
     case 8: return needs_of<P, Cfg<1, 0>::R, Cfg<1, 0>::L>();
     case 9: return needs_of<P, Cfg<1, 1>::R, Cfg<1, 1>::L>();
     case 16: return needs_mixed_of<P, MixedCfg<0>::L, MixedCfg<0>::NTERM, MixedCfg<0>::F16>();
@@ -44,6 +45,7 @@ cudaError_t launch(int prec, int config, const MeLaunch& a, cudaStream_t s) {
   switch (prec * 8 + config) {
     case 0: return launch_me<P, Cfg<0, 0>::R, Cfg<0, 0>::L>(a, s);
     case 1: return launch_me<P, Cfg<0, 1>::R, Cfg<0, 1>::L>(a, s);
+    case 2: return launch_me<P, Cfg<0, 2>::R, Cfg<0, 2>::L>(a, s);
     case 8: return launch_me<P, Cfg<1, 0>::R, Cfg<1, 0>::L>(a, s);
     case 9: return launch_me<P, Cfg<1, 1>::R, Cfg<1, 1>::L>(a, s);
     case 16: return launch_mixed<P, MixedCfg<0>::L, MixedCfg<0>::NTERM, MixedCfg<0>::F16>(a, s);
@@ -53,6 +55,6 @@ cudaError_t launch(int prec, int config, const MeLaunch& a, cudaStream_t s) {
 }  // namespace
 
 extern const ProcessOps ops_ggttggg = {P::NAME, P::NPAR, P::NCOMB, P::NCOL, P::NDIAG, P::NAMP, P::IDEN,
-                                   P::FLOPS_AMP, P::FLOPS_COL, /*has_mixed=*/true, {2, 2, 1},
+                                   P::FLOPS_AMP, P::FLOPS_COL, /*has_mixed=*/true, {3, 2, 1},
                                    needs, launch};
 }  // namespace meb300
