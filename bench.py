@@ -400,8 +400,10 @@ def run_processes(args):
     peaks = {p: binding.alu_peak(p, 0.3) for p in ("fp64", "fp32")}
     table = {}
     for process, nevt, alphas in PROCESS_TABLE:
-        if args.only_process and args.only_process not in process:
+        if args.only_process and args.only_process != process:
             continue
+        if args.process_nevt:
+            nevt = args.process_nevt
         mom, a, rh, rc = ps.make_batch(process, nevt, seed=0, alphas=alphas)
         if a is None:
             a = np.full(nevt, 0.118)
@@ -409,7 +411,7 @@ def run_processes(args):
         dev = [x.cuda(non_blocking=True) for x in host]
         torch.cuda.synchronize()
         row = {"events": nevt, "input_mb": round(sum(x.numel() * x.element_size() for x in host) / 1e6, 1)}
-        for mode in ("fp64", "fp32", "mixed"):
+        for mode in args.process_modes.split(","):
             try:
                 r = time_mode(mode, dev, host, args.steps, args.warmup, None, process=process, e2e=False)
             except binding.MEError as e:
@@ -525,7 +527,9 @@ def main():
     ap.add_argument("--nevt", type=int, default=NEVT,
                     help="events per GPU per step (a smaller case for profiling; the workload is 1048576)")
     ap.add_argument("--processes", action="store_true", help="per-process ME/s table instead of the step")
-    ap.add_argument("--only-process", default="", help="with --processes: only processes containing this")
+    ap.add_argument("--only-process", default="", help="with --processes: only this process")
+    ap.add_argument("--process-nevt", type=int, default=0, help="with --processes: events instead of the workload's")
+    ap.add_argument("--process-modes", default="fp64,fp32,mixed", help="with --processes: precisions to time")
     args = ap.parse_args()
     globals()["NEVT"] = args.nevt
     if args.serving:
