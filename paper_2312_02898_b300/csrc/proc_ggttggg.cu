@@ -14,14 +14,13 @@ namespace {
 using P = proc_ggttggg;
 template <int PREC, int C> struct Cfg;
 // Every per-thread array in global tiles leaves shared memory free, so registers alone
-// bound the blocks per SM: four 64-thread blocks in FP64, two 128-thread blocks in FP32
-// (with shared-memory denominators and J, 176 KB, one block fits: 1.6-1.7x slower).
-// Block barriers between diagram groups add 13% in FP64 and nothing in FP32.
+// bound the blocks per SM: four 64-thread blocks in FP64, two 128-thread blocks in FP32.
+// Measured alternatives (not compiled, to keep the build of this large translation unit
+// short): shared-memory denominators and J (176 KB, one block per SM) were 1.6-1.7x
+// slower; block barriers between diagram groups add 13% in FP64 and nothing in FP32; a
+// register budget of 20 currents instead of 12 changed nothing.
 template <> struct Cfg<0, 0> { using R = double; using L = Layout<0, 64, 2, 2, 2, 2, 2, 3>; };
-template <> struct Cfg<0, 1> { using R = double; using L = Layout<0, 64, 2, 2, 2, 2, 2>; };
-template <> struct Cfg<0, 2> { using R = double; using L = Layout<0, 64, 1, 1, 2, 2, 2>; };
 template <> struct Cfg<1, 0> { using R = float; using L = Layout<0, 128, 2, 2, 2, 2, 2>; };
-template <> struct Cfg<1, 1> { using R = float; using L = Layout<0, 128, 1, 1, 2, 2, 2>; };
 
 // mixed precision: every per-thread array in global tiles, so that the FP16 operand
 // tiles (120 flows padded to 128) and the colour matrix fit in shared memory beside two
@@ -32,10 +31,7 @@ template <> struct MixedCfg<0> { using L = Layout<0, 128, 2, 2, 2, 2, 2>; static
 LaunchNeeds needs(int prec, int config) {
   switch (prec * 8 + config) {
     case 0: return needs_of<P, Cfg<0, 0>::R, Cfg<0, 0>::L>();
-    case 1: return needs_of<P, Cfg<0, 1>::R, Cfg<0, 1>::L>();
-    case 2: return needs_of<P, Cfg<0, 2>::R, Cfg<0, 2>::L>();
     case 8: return needs_of<P, Cfg<1, 0>::R, Cfg<1, 0>::L>();
-    case 9: return needs_of<P, Cfg<1, 1>::R, Cfg<1, 1>::L>();
     case 16: return needs_mixed_of<P, MixedCfg<0>::L, MixedCfg<0>::NTERM, MixedCfg<0>::F16>();
     default: return LaunchNeeds{0, 0, 0, 0, false, 128, 1};
   }
@@ -44,10 +40,7 @@ LaunchNeeds needs(int prec, int config) {
 cudaError_t launch(int prec, int config, const MeLaunch& a, cudaStream_t s) {
   switch (prec * 8 + config) {
     case 0: return launch_me<P, Cfg<0, 0>::R, Cfg<0, 0>::L>(a, s);
-    case 1: return launch_me<P, Cfg<0, 1>::R, Cfg<0, 1>::L>(a, s);
-    case 2: return launch_me<P, Cfg<0, 2>::R, Cfg<0, 2>::L>(a, s);
     case 8: return launch_me<P, Cfg<1, 0>::R, Cfg<1, 0>::L>(a, s);
-    case 9: return launch_me<P, Cfg<1, 1>::R, Cfg<1, 1>::L>(a, s);
     case 16: return launch_mixed<P, MixedCfg<0>::L, MixedCfg<0>::NTERM, MixedCfg<0>::F16>(a, s);
     default: return cudaErrorNotSupported;
   }
@@ -55,6 +48,6 @@ cudaError_t launch(int prec, int config, const MeLaunch& a, cudaStream_t s) {
 }  // namespace
 
 extern const ProcessOps ops_ggttggg = {P::NAME, P::NPAR, P::NCOMB, P::NCOL, P::NDIAG, P::NAMP, P::IDEN,
-                                   P::FLOPS_AMP, P::FLOPS_COL, /*has_mixed=*/true, {3, 2, 1},
+                                   P::FLOPS_AMP, P::FLOPS_COL, /*has_mixed=*/true, {1, 1, 1},
                                    needs, launch};
 }  // namespace meb300
