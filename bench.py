@@ -26,6 +26,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -80,7 +81,9 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        # raw samples go to ME_B300_CLOCKS_DIR (default: the system temporary directory)
+        out_dir = os.environ.get("ME_B300_CLOCKS_DIR", tempfile.gettempdir())
+        self.path = os.path.join(out_dir, f"me_b300_clocks_rank{gpu_index}.csv")
 
     def __enter__(self):
         try:
