@@ -349,9 +349,9 @@ def run_gpu(args):
                          "max_rel_err": mx, "median_rel_err": med, "err_sample": ns, "bound": ERR_BOUND[mode],
                          "gpu_launches_per_step": r["launches"], "clocks": r["clocks"]}
         try:
-            ref_rate, cores, dt = oracle_rate(PROCESS, args.ref_sample, 0)
+            ref_rate, cores, dt = oracle_rate(PROCESS, args.cpu_sample, 0)
             cpu = {"value": ref_rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-                   "sample": f"first {args.ref_sample} events of the workload ({dt:.1f} s)"}
+                   "sample": f"first {args.cpu_sample} events of the workload ({dt:.1f} s)"}
         except Exception as e:  # the oracle needs gcc; report rather than fail
             cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": f"failed: {e}"}
         h2d = sum(x.numel() * x.element_size() for x in host)
@@ -516,7 +516,9 @@ def main():
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
     ap.add_argument("--mode", default="fp64", choices=["fp64", "fp32", "mixed"])
     ap.add_argument("--only", action="store_true", help="time only the headline mode")
-    ap.add_argument("--ref-sample", type=int, default=4096, help="oracle events per CPU-baseline sample")
+    ap.add_argument("--ref-sample", type=int, default=4096, help="oracle events per step of --impl reference")
+    ap.add_argument("--cpu-sample", type=int, default=49152,
+                    help="oracle events of the cpu_baseline leg (about 10 s on 16 host cores)")
     ap.add_argument("--serving", action="store_true", help="run the serving stream instead of the throughput step")
     ap.add_argument("--serving-requests", type=int, default=2000)
     ap.add_argument("--serving-warmup", type=int, default=200)
