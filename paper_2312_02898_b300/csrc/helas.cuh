@@ -108,6 +108,24 @@ HD double dd_invariant(const dd* q, double m) {
   s = dd_add(s, -m * m);
   return s.hi + s.lo;
 }
+// The same calls in plain FP64, for the FP32 and mixed modes.  There the invariants
+// only need to be far more accurate than the FP32 amplitudes: the rounding error of a
+// plain FP64 invariant is about 1e-16 times the event's conditioning number, and events
+// conditioned worse than the rescue threshold are evaluated again in FP64 (with the
+// error-free forms).  The error-free forms take about ten FP64 operations each, and
+// B300 issues FP64 at 1/64 of its FP32 rate, so in those modes they would outweigh the
+// amplitudes of the smaller processes.
+struct dd_plain {
+  double hi, lo;  // lo stays 0; the same initialiser as dd
+};
+HD dd_plain dd_add(dd_plain x, double y) { return dd_plain{x.hi + y, 0.0}; }
+HD double dd_invariant(const dd_plain* q, double m) {
+  return q[0].hi * q[0].hi - q[1].hi * q[1].hi - q[2].hi * q[2].hi - q[3].hi * q[3].hi - m * m;
+}
+// invariant arithmetic for amplitudes of type R: error-free for FP64, plain otherwise
+template <class R> struct dd_select { using type = dd; };
+template <> struct dd_select<float> { using type = dd_plain; };
+template <class R> using dd_for = typename dd_select<R>::type;
 
 // ---------------------------------------------------------------------------
 // external wavefunctions

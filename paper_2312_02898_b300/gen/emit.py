@@ -368,14 +368,14 @@ class Emitter:
             groups.append(list(body))
             variants.append((budget, group, nslot, groups))
 
-        den = ["  dd q[4];"]
+        den = ["  using DD = dd_for<R>;", "  DD q[4];"]
 
         def dd_sum(parts):
             # exact sum of signed momenta, component by component
             out = []
             for mu in range(4):
                 s0, i0 = parts[0]
-                e = f"dd{{{'-' if s0 == '-' else ''}p[{i0}][{mu}], 0.0}}"
+                e = f"DD{{{'-' if s0 == '-' else ''}p[{i0}][{mu}], 0.0}}"
                 for sgn, i in parts[1:]:
                     e = f"dd_add({e}, {'-' if sgn == '-' else ''}p[{i}][{mu}])"
                 out.append(f"  q[{mu}] = {e};")
