@@ -45,8 +45,8 @@ ERR_BOUND = {"fp64": 1e-12, "fp32": 1e-5, "mixed": 1e-5}
 # processed.  Keyed by the kernel's layout, so a changed default reports no traffic.
 DRAM_BYTES_PER_EVENT = {
     ("fp64", "Layout<3, 64, 1, 1, 1, 2, 2, 3, 1>"): 1.421e11 / 655360,
-    ("fp32", "Layout<1, 64, 1, 0, 1, 1, 2, 3, 1>"): 9.192e8 / 655360,
-    ("mixed", "Layout<1, 128, 1, 1, 1, 2, 2, 0, 1>"): 1.572e9 / 655360,
+    ("fp32", "Layout<1, 64, 1, 0, 1, 1, 2, 3, 1>"): 9.812e8 / 655360,
+    ("mixed", "Layout<1, 128, 1, 1, 1, 2, 2, 0, 1>"): 1.492e9 / 655360,
 }
 DEFAULT_LAYOUT = {"fp64": "Layout<3, 64, 1, 1, 1, 2, 2, 3, 1>", "fp32": "Layout<1, 64, 1, 0, 1, 1, 2, 3, 1>",
                   "mixed": "Layout<1, 128, 1, 1, 1, 2, 2, 0, 1>"}
