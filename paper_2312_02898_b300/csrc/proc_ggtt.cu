@@ -12,13 +12,19 @@ namespace meb300 {
 namespace {
 using P = proc_ggtt;
 template <int PREC, int C> struct Cfg;
-template <> struct Cfg<0, 0> { using R = double; using L = Layout<0, 128, false, false, 0, 0, 1>; };
-template <> struct Cfg<1, 0> { using R = float; using L = Layout<0, 128, false, false, 0, 0, 1>; };
+template <> struct Cfg<0, 0> { using R = double; using L = Layout<0, 128, 0, 0, 0, 0, 1>; };
+// FP32: registers capped at 96 by asking for 5 blocks per SM (20 warps), without
+// spills; the uncapped layout (151 registers, 12 warps) and a cap at 128 follow
+template <> struct Cfg<1, 0> { using R = float; using L = Layout<0, 128, 0, 0, 0, 0, 1, 0, 5>; };
+template <> struct Cfg<1, 1> { using R = float; using L = Layout<0, 128, 0, 0, 0, 0, 1>; };
+template <> struct Cfg<1, 2> { using R = float; using L = Layout<0, 128, 0, 0, 0, 0, 1, 0, 4>; };
 
 LaunchNeeds needs(int prec, int config) {
   switch (prec * 8 + config) {
     case 0: return needs_of<P, Cfg<0, 0>::R, Cfg<0, 0>::L>();
     case 8: return needs_of<P, Cfg<1, 0>::R, Cfg<1, 0>::L>();
+    case 9: return needs_of<P, Cfg<1, 1>::R, Cfg<1, 1>::L>();
+    case 10: return needs_of<P, Cfg<1, 2>::R, Cfg<1, 2>::L>();
     default: return LaunchNeeds{0, 0, 0, 0, false, 128, 1};
   }
 }
@@ -27,12 +33,14 @@ cudaError_t launch(int prec, int config, const MeLaunch& a, cudaStream_t s) {
   switch (prec * 8 + config) {
     case 0: return launch_me<P, Cfg<0, 0>::R, Cfg<0, 0>::L>(a, s);
     case 8: return launch_me<P, Cfg<1, 0>::R, Cfg<1, 0>::L>(a, s);
+    case 9: return launch_me<P, Cfg<1, 1>::R, Cfg<1, 1>::L>(a, s);
+    case 10: return launch_me<P, Cfg<1, 2>::R, Cfg<1, 2>::L>(a, s);
     default: return cudaErrorNotSupported;
   }
 }
 }  // namespace
 
 extern const ProcessOps ops_ggtt = {P::NAME, P::NPAR, P::NCOMB, P::NCOL, P::NDIAG, P::NAMP, P::IDEN,
-                                   P::FLOPS_AMP, P::FLOPS_COL, /*has_mixed=*/false, {1, 1, 0},
+                                   P::FLOPS_AMP, P::FLOPS_COL, /*has_mixed=*/false, {1, 3, 0},
                                    needs, launch};
 }  // namespace meb300

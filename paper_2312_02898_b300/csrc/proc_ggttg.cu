@@ -13,9 +13,14 @@ namespace {
 using P = proc_ggttg;
 template <int PREC, int C> struct Cfg;
 template <> struct Cfg<0, 0> { using R = double; using L = Layout<1, 128, false, false, 0, 1, 1, 3>; };
-template <> struct Cfg<1, 0> { using R = float; using L = Layout<0, 128, false, false, 0, 0, 1, 3>; };
 template <> struct Cfg<0, 1> { using R = double; using L = Layout<1, 128, false, false, 0, 1, 1>; };
-template <> struct Cfg<1, 1> { using R = float; using L = Layout<0, 128, false, false, 0, 0, 1>; };
+// FP32: registers capped at 168 by asking for 3 blocks per SM (12 warps), without
+// spills; then the uncapped layout (254 registers, 8 warps), the same without block
+// barriers, and a cap at 128
+template <> struct Cfg<1, 0> { using R = float; using L = Layout<0, 128, 0, 0, 0, 0, 1, 3, 3>; };
+template <> struct Cfg<1, 1> { using R = float; using L = Layout<0, 128, false, false, 0, 0, 1, 3>; };
+template <> struct Cfg<1, 2> { using R = float; using L = Layout<0, 128, false, false, 0, 0, 1>; };
+template <> struct Cfg<1, 3> { using R = float; using L = Layout<0, 128, 0, 0, 0, 0, 1, 3, 4>; };
 
 LaunchNeeds needs(int prec, int config) {
   switch (prec * 8 + config) {
@@ -23,6 +28,8 @@ LaunchNeeds needs(int prec, int config) {
     case 1: return needs_of<P, Cfg<0, 1>::R, Cfg<0, 1>::L>();
     case 8: return needs_of<P, Cfg<1, 0>::R, Cfg<1, 0>::L>();
     case 9: return needs_of<P, Cfg<1, 1>::R, Cfg<1, 1>::L>();
+    case 10: return needs_of<P, Cfg<1, 2>::R, Cfg<1, 2>::L>();
+    case 11: return needs_of<P, Cfg<1, 3>::R, Cfg<1, 3>::L>();
     default: return LaunchNeeds{0, 0, 0, 0, false, 128, 1};
   }
 }
@@ -33,12 +40,14 @@ cudaError_t launch(int prec, int config, const MeLaunch& a, cudaStream_t s) {
     case 1: return launch_me<P, Cfg<0, 1>::R, Cfg<0, 1>::L>(a, s);
     case 8: return launch_me<P, Cfg<1, 0>::R, Cfg<1, 0>::L>(a, s);
     case 9: return launch_me<P, Cfg<1, 1>::R, Cfg<1, 1>::L>(a, s);
+    case 10: return launch_me<P, Cfg<1, 2>::R, Cfg<1, 2>::L>(a, s);
+    case 11: return launch_me<P, Cfg<1, 3>::R, Cfg<1, 3>::L>(a, s);
     default: return cudaErrorNotSupported;
   }
 }
 }  // namespace
 
 extern const ProcessOps ops_ggttg = {P::NAME, P::NPAR, P::NCOMB, P::NCOL, P::NDIAG, P::NAMP, P::IDEN,
-                                   P::FLOPS_AMP, P::FLOPS_COL, /*has_mixed=*/false, {2, 2, 0},
+                                   P::FLOPS_AMP, P::FLOPS_COL, /*has_mixed=*/false, {2, 4, 0},
                                    needs, launch};
 }  // namespace meb300
