@@ -131,70 +131,86 @@ def test_rescue_pass_reproduces_fp64(process):
     assert ok, e
 
 
-def _collinear_gluon_events(n, seed, theta=(3e-3, 1e-2), sqrt_s=1500.0, mt=173.0):
-    """g g > t t~ g g events whose two final gluons are a small angle theta apart.
-    The gluons are massless, E (1, n).  The top pair balances them: it is built back to
-    back on the top mass shell in its own rest frame and boosted to the lab.  The gluon
-    propagator invariant (k1 + k2)^2 ~ E1 E2 theta^2 is then 1e4 to 1e6 times smaller
-    than (E1 + E2)^2."""
+def _top_pair(P, mt, rng):
+    """t and t~ on the mass shell, back to back in the rest frame of P, boosted to the lab"""
+    M = np.sqrt(P[0] ** 2 - P[1:] @ P[1:])
+    u = rng.normal(size=3)
+    u /= np.linalg.norm(u)
+    q = np.sqrt(M * M / 4 - mt * mt) * u
+    out = []
+    for qv in (q, -q):
+        en = (P[0] * M / 2 + P[1:] @ qv) / M
+        out.append(np.concatenate([[en], qv + P[1:] * (M / 2 + en) / (P[0] + M)]))
+    return out
+
+
+# the nearly light-like propagator momentum of the events below, as signed particles
+COLLINEAR_TERMS = {PROCS[2]: ((1, 0), (-1, 4)), PROCS[3]: ((1, 4), (1, 5))}
+
+
+def _collinear_events(process, n, seed, theta=(3e-3, 1e-2), sqrt_s=1500.0, mt=173.0):
+    """Events with a gluon propagator that is nearly on shell, at sqrt(s).
+    * g g > t t~ g g: the two final gluons are a small angle theta apart, so
+      (k1 + k2)^2 ~ E1 E2 theta^2.
+    * g g > t t~ g: the final gluon is theta from the first beam, so the t-channel
+      invariant is (p1 - k)^2 ~ -E1 E theta^2.
+    The gluons are massless, E (1, n), and the top pair balances them.  The invariant is
+    then 1e4 to 1e6 times smaller than the square of the summed energies."""
     rng = np.random.default_rng(seed)
-    mom = np.zeros((n, 6, 4))
+    npar = 6 if process == PROCS[3] else 5
+    mom = np.zeros((n, npar, 4))
     h = sqrt_s / 2
+    p1, p2 = np.array([h, 0, 0, h]), np.array([h, 0, 0, -h])
     for e in range(n):
-        nv = rng.normal(size=3)
-        nv /= np.linalg.norm(nv)
-        m = np.cross(nv, rng.normal(size=3))
-        m /= np.linalg.norm(m)
         th = rng.uniform(*theta)
-        n2 = np.cos(th) * nv + np.sin(th) * m
-        e1, e2 = rng.uniform(100.0, 300.0, size=2)
-        k1 = np.concatenate([[e1], e1 * nv])
-        k2 = np.concatenate([[e2], e2 * n2])
-        P = np.array([sqrt_s, 0.0, 0.0, 0.0]) - k1 - k2
-        M = np.sqrt(P[0] ** 2 - P[1:] @ P[1:])
-        u = rng.normal(size=3)
-        u /= np.linalg.norm(u)
-        q = np.sqrt(M * M / 4 - mt * mt) * u
-        tops = []
-        for qv in (q, -q):  # rest-frame (M/2, qv) boosted by P
-            en = (P[0] * M / 2 + P[1:] @ qv) / M
-            tops.append(np.concatenate([[en], qv + P[1:] * (M / 2 + en) / (P[0] + M)]))
-        mom[e] = [[h, 0, 0, h], [h, 0, 0, -h], tops[0], tops[1], k1, k2]
+        if process == PROCS[3]:
+            nv = rng.normal(size=3)
+            nv /= np.linalg.norm(nv)
+            m = np.cross(nv, rng.normal(size=3))
+            m /= np.linalg.norm(m)
+            n2 = np.cos(th) * nv + np.sin(th) * m
+            e1, e2 = rng.uniform(100.0, 300.0, size=2)
+            gl = [np.concatenate([[e1], e1 * nv]), np.concatenate([[e2], e2 * n2])]
+        else:
+            en, phi = rng.uniform(100.0, 300.0), rng.uniform(0, 2 * np.pi)
+            gl = [en * np.array([1.0, np.sin(th) * np.cos(phi), np.sin(th) * np.sin(phi), np.cos(th)])]
+        tops = _top_pair(p1 + p2 - sum(gl), mt, rng)
+        mom[e] = [p1, p2] + tops + gl
     return mom
 
 
-@pytest.mark.skipif(PROCS[3] not in ACTIVE, reason="process not selected")
-def test_nearly_collinear_gluons():
+@pytest.mark.parametrize("process", [p for p in ACTIVE if p in (PROCS[2], PROCS[3])])
+def test_nearly_collinear_gluons(process):
     """On events whose gluon propagator invariant cancels four to six digits, a plain FP64
     invariant is off by more than 1e-12.  The FP64 mode still stays within 1e-12 of the
-    oracle, because it forms the invariants in double-double.  The FP32 and mixed modes
+    oracle, because it forms the invariants in double-double.  The FP32 (and mixed) modes
     flag every such event for their FP64 rescue pass, and so return the FP64 mode's bits."""
     from fractions import Fraction
-    proc = PROCS[3]
     n = 64
-    mom = _collinear_gluon_events(n, seed=31)
+    mom = _collinear_events(process, n, seed=31)
     np.testing.assert_allclose(mom[:, 2:].sum(axis=1), mom[:, :2].sum(axis=1), rtol=0, atol=1e-9)
     rng = np.random.default_rng(32)
     rh, rc = rng.random(n), rng.random(n)
-    # the inputs are as ill-conditioned as intended: the plain FP64 invariant of the gluon
-    # pair against its exact value (rational arithmetic on the same doubles)
-    k = mom[:, 4] + mom[:, 5]
+    # the inputs are as ill-conditioned as intended: the plain FP64 invariant against its
+    # exact value (rational arithmetic on the same doubles)
+    terms = COLLINEAR_TERMS[process]
+    k = sum(sg * mom[:, i] for sg, i in terms)
     plain = k[:, 0] ** 2 - k[:, 1] ** 2 - k[:, 2] ** 2 - k[:, 3] ** 2
     exact = []
     for e in range(n):
-        c = [Fraction(mom[e, 4, mu]) + Fraction(mom[e, 5, mu]) for mu in range(4)]
+        c = [sum(sg * Fraction(mom[e, i, mu]) for sg, i in terms) for mu in range(4)]
         exact.append(float(c[0] ** 2 - c[1] ** 2 - c[2] ** 2 - c[3] ** 2))
     exact = np.array(exact)
     assert np.median(np.abs(plain / exact - 1)) > 1e-12
-    kappa = (mom[:, 4, 0] + mom[:, 5, 0]) ** 2 / exact
+    kappa = sum(mom[:, i, 0] for _, i in terms) ** 2 / np.abs(exact)
     assert kappa.min() > 2000.0  # above the default rescue threshold
-    ref = oracle.me(proc, mom, rnd_hel=rh, rnd_col=rc)
-    r64 = run_gpu(mk(proc, "fp64"), mom, None, rh, rc)
+    ref = oracle.me(process, mom, rnd_hel=rh, rnd_col=rc)
+    r64 = run_gpu(mk(process, "fp64"), mom, None, rh, rc)
     rel = np.abs(r64[0] / ref["me"] - 1)
-    print(f"collinear gluons: kappa {kappa.min():.2e}..{kappa.max():.2e}, FP64 max rel {rel.max():.3e}")
+    print(f"{process} collinear: kappa {kappa.min():.2e}..{kappa.max():.2e}, FP64 max rel {rel.max():.3e}")
     assert rel.max() <= 1e-12
-    for prec in ("fp32", "mixed"):
-        r = run_gpu(mk(proc, prec), mom, None, rh, rc)
+    for prec in ("fp32", "mixed") if process == PROCS[3] else ("fp32",):
+        r = run_gpu(mk(process, prec), mom, None, rh, rc)
         assert np.array_equal(r[0], r64[0]), prec
         assert np.array_equal(r[1], r64[1]), prec
 
