@@ -249,10 +249,20 @@ CallPlan plan_call(const me_handle* h, int64_t nevt, int64_t chunk, bool want_he
   cp.chunk = chunk;
   const int ngood = int(h->good.size());
   const LaunchNeeds nd = ops->needs(cp.prec, cp.config);
-  cp.hsplit = 1;  // one thread per event: results independent of the batch they come in
+  // One thread per event, so that results do not depend on the batch they come in;
+  // except for a process with a single colour flow, which has no colour weights to
+  // combine.  There a group of threads per event gives the same bits (its first lane
+  // sums the helicities in order), and a batch that would leave most resident threads
+  // idle is spread over up to ngood threads per event.
+  cp.hsplit = 1;
+  if (ops->ncol == 1) {
+    const int64_t resident = int64_t(h->nsm) * nd.blocks_per_sm * nd.block;
+    while (cp.hsplit < 32 && 2 * cp.hsplit <= ngood && 2 * cp.hsplit * chunk <= resident) cp.hsplit *= 2;
+  }
   cp.grid = persistent_grid(h, nd, chunk * cp.hsplit);
   cp.block = nd.block;
-  cp.main = carve(ops, nd, ngood, int64_t(cp.grid) * nd.block, want_hel, want_col);
+  // the split's first lane reads the group's per-helicity values back from cum
+  cp.main = carve(ops, nd, ngood, int64_t(cp.grid) * nd.block, want_hel || cp.hsplit > 1, want_col);
   size_t off = cp.main.total();
   cp.rescue = (cp.prec == ME_PREC_FP32 || cp.prec == ME_PREC_MIXED) && h->par.rescue_kappa > 0;
   if (cp.rescue) {
@@ -574,7 +584,10 @@ int me_plan(const me_handle* h, int64_t nevt, int64_t* launches, int64_t* worksp
 int me_launch_shape(const me_handle* h, int64_t nevt, int* grid, int* block, int* blocks_per_sm, int* nsm) {
   if (!h || nevt < 0) return ME_ERR_ARG;
   const LaunchNeeds nd = h->ops->needs(h->par.precision, h->config);
-  if (grid) *grid = persistent_grid(h, nd, chunk_for(nd, std::max<int64_t>(nevt, 1)));
+  if (grid) {
+    const int64_t n = std::max<int64_t>(nevt, 1);
+    *grid = plan_call(h, n, chunk_for(nd, n), true, true).grid;
+  }
   if (block) *block = nd.block;
   if (blocks_per_sm) *blocks_per_sm = nd.blocks_per_sm;
   if (nsm) *nsm = h->nsm;

@@ -340,6 +340,24 @@ def test_batch_split_invariance():
         assert np.array_equal(x[700:1300], y)
 
 
+@pytest.mark.skipif(PROCS[0] not in ACTIVE, reason="process not selected")
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_split_helicities_give_the_same_bits(precision):
+    """e+ e- > mu+ mu- has one colour flow, so a small batch spreads each event's
+    helicities over a group of threads while a large batch keeps one thread per event.
+    Either way an event's matrix element and helicity selection have the same bits."""
+    p = PROCS[0]
+    m = mk(p, precision)
+    _, block, bps, nsm = m.launch_shape(1)
+    big = 2 * block * bps * nsm  # beyond the resident threads: one thread per event
+    mom, _, rh, rc = ps.make_batch(p, big, seed=12)
+    whole = run_gpu(m, mom, None, rh, rc)
+    for lo, hi in ((0, 1), (100, 131), (5000, 5777), (big - 1000, big)):
+        part = run_gpu(m, mom[lo:hi], None, rh[lo:hi], rc[lo:hi])
+        for x, y in zip(whole, part):
+            assert np.array_equal(x[lo:hi], y), (lo, hi)
+
+
 FULL = [(PROCS[0], 16384, "fp64", None), (PROCS[1], 524288, "fp64", 0.118), (PROCS[2], 524288, "fp32", 0.118),
         (PROCS[3], 1048576, "fp64", "uniform"), (PROCS[3], 1048576, "fp32", "uniform"),
         (PROCS[3], 1048576, "mixed", "uniform"),
