@@ -6,9 +6,12 @@ the two share no code.  The C source ``me_oracle.c`` states the physics, the
 conventions and the published methods it follows.
 
 Pinned by the ``-m "not gpu"`` tests in ``tests/test_oracle_*.py`` against closed
-forms (e+e- -> mu+mu-, gg -> ttbar), an explicit-colour brute force, exact colour
-algebra, the Lorentz / gauge / Bose / alpha_s-scaling invariants, and the
-Parke-Taylor formula: with massless quarks every MHV colour-ordered amplitude for 2 to
+forms (e+e- -> mu+mu-, gg -> ttbar), an explicit-colour brute force (also at the
+physical top width, with and without width in t-channel propagators), exact colour
+algebra checked entry by entry against explicit Gell-Mann sums for 2 to 5 gluons, the
+propagator invariants checked against exact rational arithmetic on nearly collinear
+events, the Lorentz / gauge / Bose / alpha_s-scaling invariants, and the Parke-Taylor
+formula: with massless quarks every MHV colour-ordered amplitude for 2 to
 5 gluons equals (sqrt(2) g_s)^n_g times its closed form, which fixes the absolute
 normalisation of the recursion for gg -> ttbar gg and gg -> ttbar ggg.  What the
 massless limit leaves open there (the massive spinors and top propagators at 4-5
@@ -91,6 +94,8 @@ def lib():
         _lib.oracle_colour_matrix_exact.argtypes = [ctypes.c_int, i64, i64]
         _lib.oracle_process_id.argtypes = [ctypes.c_char_p]
         _lib.oracle_sm_derived.argtypes = [ctypes.POINTER(OracleParams), d]
+        _lib.oracle_invariants.argtypes = [ctypes.c_int, ctypes.POINTER(OracleParams), ctypes.c_int64, d, d, d]
+        _lib.oracle_invariants.restype = ctypes.c_int
     return _lib
 
 
@@ -129,6 +134,23 @@ def sm_derived(params: Params | None = None):
     p = (params or Params()).c()
     lib().oracle_sm_derived(ctypes.byref(p), _ptr(out))
     return tuple(out)
+
+
+def invariants(process: str, momenta, params: Params | None = None):
+    """The propagator invariants the oracle's recursion uses, per event and particle
+    mask (bit i = particle i): (gsq, tden), each [nevt][2^npar].  gsq[mask] is K^2 of
+    the gluons in the mask (incoming +p, outgoing -p); tden[mask] is q^2 - mt^2 of the
+    top-line propagator q = p_t - K(mask).  Formed in quadruple precision and rounded
+    once to FP64."""
+    npar, ncomb, _, _ = info(process)
+    mom = np.ascontiguousarray(momenta, dtype=np.float64)
+    nevt = mom.shape[0]
+    assert mom.shape == (nevt, npar, 4)
+    gsq, tden = np.zeros((nevt, ncomb)), np.zeros((nevt, ncomb))
+    p = (params or Params()).c()
+    if lib().oracle_invariants(process_id(process), ctypes.byref(p), nevt, _ptr(mom), _ptr(gsq), _ptr(tden)) != 0:
+        raise ValueError(f"no invariant table for {process!r}")
+    return gsq, tden
 
 
 def me(process: str, momenta, alphas=None, rnd_hel=None, rnd_col=None, params: Params | None = None,

@@ -474,20 +474,58 @@ typedef struct {
   int it;            /* particle index of the top */
 } qcd_ext;
 
-/* Minkowski square in x87 extended precision.  A propagator's momentum is a sum of
- * external momenta; when that sum is nearly light-like (a gluon almost collinear
- * with a beam or with another gluon) the plain FP64 square cancels most of its digits.
- * The invariants are therefore summed and squared in long double and rounded once;
- * every other operation of the oracle stays in FP64. */
-static long double mdot_l(const long double* a, const long double* b) {
-  return a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
+/* Propagator invariants in quadruple precision.  A propagator's momentum is a sum of
+ * external momenta; when that sum is nearly light-like (a gluon almost collinear with a
+ * beam or with another gluon) the plain FP64 square cancels most of its digits.  Each
+ * invariant is therefore formed from the FP64 inputs in __float128 (113-bit
+ * significand): the sums of a few doubles are exact there, each square rounds at
+ * 2^-113 of the summed energy squared, so even an invariant 1e10 times smaller than
+ * that keeps ~80 correct bits before its single rounding to FP64.  The invariants
+ * depend only on the kinematics, so they are formed once per event, tabulated by the
+ * set of external particles whose momenta they sum (bit i = particle i), and every
+ * other operation of the oracle stays in FP64. */
+#if !defined(__SIZEOF_FLOAT128__)
+#error "the oracle's propagator invariants need the __float128 type (gcc on x86-64 or aarch64)"
+#endif
+typedef __float128 quad;
+_Static_assert(sizeof(quad) == 16, "__float128 must be the IEEE binary128 format");
+
+typedef struct {
+  double gsq[1 << MAXPAR];  /* K^2, K = sum of the incoming momenta of the gluons in 'mask' */
+  double tden[1 << MAXPAR]; /* q^2 - mt^2, q = p_t - K(gluons in 'mask'), the top-line propagator */
+} invariants;
+
+static quad msq_q(const quad* k) { return k[0] * k[0] - k[1] * k[1] - k[2] * k[2] - k[3] * k[3]; }
+
+/* fills inv for every subset 'mask' of the gluons of process pd at momenta p
+ * (incoming gluons carry +p, outgoing -p) */
+static void event_invariants(const proc_def* pd, const double* p, double mt, invariants* inv) {
+  int npar = pd->npar, it = -1;
+  unsigned gl = 0;
+  for (int i = 0; i < npar; ++i) {
+    if (pd->role[i] == R_G_IN || pd->role[i] == R_G_OUT) gl |= 1u << i;
+    if (pd->role[i] == R_T_OUT) it = i;
+  }
+  for (unsigned mask = 0; mask < (1u << npar); ++mask) {
+    inv->gsq[mask] = 0.0;
+    inv->tden[mask] = 0.0;
+    if ((mask & ~gl) || it < 0) continue;
+    quad K[4] = {0, 0, 0, 0};
+    for (int i = 0; i < npar; ++i)
+      if (mask >> i & 1)
+        for (int m = 0; m < 4; ++m) K[m] += (pd->role[i] == R_G_IN) ? (quad)p[4 * i + m] : -(quad)p[4 * i + m];
+    quad q[4];
+    for (int m = 0; m < 4; ++m) q[m] = (quad)p[4 * it + m] - K[m];
+    inv->gsq[mask] = (double)msq_q(K);
+    inv->tden[mask] = (double)(msq_q(q) - (quad)mt * (quad)mt);
+  }
 }
 
 /* colour-ordered amplitude A(sigma) for gluons in the order sigma (gluon slots) */
-static cx amp_ordered(const qcd_ext* x, int n, const int* sigma, double gs, double mt, double wt, int zwt) {
+static cx amp_ordered(const qcd_ext* x, const invariants* inv, int n, const int* sigma, double gs, double mt,
+                      double wt, int zwt) {
   cx J[MAXG][MAXG][4];
   double K[MAXG][MAXG][4];
-  long double KL[MAXG][MAXG][4]; /* the same sums in extended precision, for invariants */
   unsigned M[MAXG][MAXG];
   for (int len = 1; len <= n; ++len) {
     for (int i = 0; i + len - 1 < n; ++i) {
@@ -496,15 +534,11 @@ static cx amp_ordered(const qcd_ext* x, int n, const int* sigma, double gs, doub
         for (int m = 0; m < 4; ++m) {
           J[i][i][m] = x->eps[sigma[i]][m];
           K[i][i][m] = x->kin[sigma[i]][m];
-          KL[i][i][m] = x->kin[sigma[i]][m];
         }
         M[i][i] = 1u << x->pidx[sigma[i]];
         continue;
       }
-      for (int m = 0; m < 4; ++m) {
-        K[i][j][m] = K[i][i][m] + K[i + 1][j][m];
-        KL[i][j][m] = KL[i][i][m] + KL[i + 1][j][m];
-      }
+      for (int m = 0; m < 4; ++m) K[i][j][m] = K[i][i][m] + K[i + 1][j][m];
       M[i][j] = M[i][i] | M[i + 1][j];
       cx cur[4] = {0, 0, 0, 0}, t[4];
       for (int k = i; k < j; ++k) {
@@ -516,7 +550,7 @@ static cx amp_ordered(const qcd_ext* x, int n, const int* sigma, double gs, doub
           v4(J[i][k], J[k + 1][l], J[l + 1][j], t);
           for (int m = 0; m < 4; ++m) cur[m] += I * gs * gs * t[m];
         }
-      double P2 = (double)mdot_l(KL[i][j], KL[i][j]);
+      double P2 = inv->gsq[M[i][j]];
       for (int m = 0; m < 4; ++m) J[i][j][m] = (-I / P2) * cur[m];
     }
   }
@@ -538,14 +572,10 @@ static cx amp_ordered(const qcd_ext* x, int n, const int* sigma, double gs, doub
     } else {
       /* propagator i(q-slash + m)/(q^2 - m^2 + i m w) with q = p_t - K(first j gluons) */
       double q[4];
-      long double qL[4];
-      for (int m = 0; m < 4; ++m) {
-        q[m] = x->pt[m] - K[0][j - 1][m];
-        qL[m] = (long double)x->pt[m] - KL[0][j - 1][m];
-      }
+      for (int m = 0; m < 4; ++m) q[m] = x->pt[m] - K[0][j - 1][m];
       unsigned mask = M[0][j - 1] | (1u << x->it);
       double w = (zwt && is_tchannel(mask)) ? 0.0 : wt;
-      cx den = (double)(mdot_l(qL, qL) - (long double)mt * mt) + I * mt * w;
+      cx den = inv->tden[M[0][j - 1]] + I * mt * w;
       cx qc[4] = {q[0], q[1], q[2], q[3]}, S[4][4];
       slash(qc, S);
       for (int r = 0; r < 4; ++r) S[r][r] += mt;
@@ -616,6 +646,8 @@ int oracle_me(int proc, const oracle_params* par, int64_t nevt, const double* mo
     double total = 0;
     double as = alphas ? alphas[e] : par->alphas;
     double gs = sqrt(4.0 * M_PI * as);
+    invariants inv;
+    if (proc != 0) event_invariants(pd, p, par->mt, &inv);
     for (int h = 0; h < ncomb; ++h) {
       int lam[MAXPAR];
       for (int i = 0; i < npar; ++i) lam[i] = ((h >> (npar - 1 - i)) & 1) ? 1 : -1;
@@ -650,7 +682,7 @@ int oracle_me(int proc, const oracle_params* par, int64_t nevt, const double* mo
           }
         }
         for (int s = 0; s < ncol; ++s)
-          A[s] = amp_ordered(&x, n, perms[s], gs, par->mt, par->wt, par->zero_width_tchan);
+          A[s] = amp_ordered(&x, &inv, n, perms[s], gs, par->mt, par->wt, par->zero_width_tchan);
       }
       double m2 = 0;
       for (int s = 0; s < ncol; ++s)
@@ -673,5 +705,27 @@ int oracle_me(int proc, const oracle_params* par, int64_t nevt, const double* mo
     if (sel_col && rnd_col) sel_col[e] = select_first_exceeding(w, ncol, rnd_col[e]);
   }
   free(Cm);
+  return 0;
+}
+
+/*
+ * oracle_invariants: the propagator invariants the recursion of oracle_me uses, for
+ * nevt events of a QCD process, indexed by particle mask (bit i = particle i):
+ *   gsq  [nevt][2^npar]  K^2 of the gluons in the mask (incoming +p, outgoing -p)
+ *   tden [nevt][2^npar]  q^2 - mt^2 with q = p_t - K(gluons in the mask)
+ * Entries whose mask holds anything but gluons are 0.  Returns 0, or -1 for a bad
+ * argument (e+ e- -> mu+ mu- has no such table).
+ */
+int oracle_invariants(int proc, const oracle_params* par, int64_t nevt, const double* mom, double* gsq,
+                      double* tden) {
+  if (proc <= 0 || proc >= NPROC || nevt < 0 || !par || (nevt > 0 && (!mom || !gsq || !tden))) return -1;
+  const proc_def* pd = &PROCS[proc];
+  int ncomb = 1 << pd->npar;
+  for (int64_t e = 0; e < nevt; ++e) {
+    invariants inv;
+    event_invariants(pd, mom + e * pd->npar * 4, par->mt, &inv);
+    memcpy(gsq + e * ncomb, inv.gsq, sizeof(double) * ncomb);
+    memcpy(tden + e * ncomb, inv.tden, sizeof(double) * ncomb);
+  }
   return 0;
 }

@@ -13,7 +13,12 @@ Feynman rules (Feynman gauge; Peskin & Schroeder Fig. 16.7 with g -> -g):
   4-gluon      -i g^2 [f^{abe}f^{cde}(g^{mu rho}g^{nu sigma} - g^{mu sigma}g^{nu rho})
                       + f^{ace}f^{bde}(g^{mu nu}g^{rho sigma} - g^{mu sigma}g^{nu rho})
                       + f^{ade}f^{bce}(g^{mu nu}g^{rho sigma} - g^{mu rho}g^{nu sigma})]
-  propagators  -i g_{mu nu} delta^{ab}/k^2,  i(qslash + m)/(q^2 - m^2)
+  propagators  -i g_{mu nu} delta^{ab}/k^2,  i(qslash + m)/(q^2 - m^2 + i m w)
+
+The top width w is either the same in every top propagator, or (zero_width_tchan)
+zero in each propagator whose momentum is in the t channel: written as a signed sum of
+external momenta, it carries exactly one of the two incoming momenta, so it separates
+the two beams.
 
 Returns the spin- and colour-summed |M|^2 (not averaged).  Slow; small n only.
 """
@@ -133,10 +138,11 @@ def set_partitions(items, nparts):
                 yield (block,) + tail
 
 
-def summed_me2(mom, mt, gs, roles):
+def summed_me2(mom, mt, gs, roles, wt=0.0, zero_width_tchan=False):
     """sum over spins, polarisations and colours of |M|^2 for g g -> t t~ + gluons.
 
-    roles: list of 'gin', 'gout', 't', 'tb' in particle order.
+    roles: list of 'gin', 'gout', 't', 'tb' in particle order; wt: top width; with
+    zero_width_tchan, no width in t-channel top propagators (see the module docstring).
     """
     gl = [i for i, r in enumerate(roles) if r in ("gin", "gout")]
     it = roles.index("t")
@@ -194,8 +200,14 @@ def summed_me2(mom, mt, gs, roles):
                     if R == allg:
                         amp = np.einsum("Ailt,t->Ail", acc, vt)
                     else:
+                        # q = p_t - sum of the incoming momenta of the gluons R on the top
+                        # side; as a sum of external momenta it holds p_in for each
+                        # incoming gluon in R
                         q = mom[it] - K[R]
-                        prop = 1j * (slash(q.astype(complex)) + mt * np.eye(4)) / (mdot(q, q) - mt * mt)
+                        n_beams = sum(1 for i in R if roles[i] == "gin")
+                        w = 0.0 if (zero_width_tchan and n_beams == 1) else wt
+                        prop = (1j * (slash(q.astype(complex)) + mt * np.eye(4))
+                                / (mdot(q, q) - mt * mt + 1j * mt * w))
                         U[R] = np.einsum("Ailt,tu->Ailu", acc, prop)
                 total += float(np.sum(np.abs(amp) ** 2))
     return total

@@ -12,6 +12,7 @@ import pytest
 
 import oracle
 from paper_2312_02898_b300 import phasespace as ps
+from tests.collinear import COLLINEAR_TERMS, collinear_events
 
 torch = pytest.importorskip("torch")
 
@@ -131,54 +132,6 @@ def test_rescue_pass_reproduces_fp64(process):
     assert ok, e
 
 
-def _top_pair(P, mt, rng):
-    """t and t~ on the mass shell, back to back in the rest frame of P, boosted to the lab"""
-    M = np.sqrt(P[0] ** 2 - P[1:] @ P[1:])
-    u = rng.normal(size=3)
-    u /= np.linalg.norm(u)
-    q = np.sqrt(M * M / 4 - mt * mt) * u
-    out = []
-    for qv in (q, -q):
-        en = (P[0] * M / 2 + P[1:] @ qv) / M
-        out.append(np.concatenate([[en], qv + P[1:] * (M / 2 + en) / (P[0] + M)]))
-    return out
-
-
-# the nearly light-like propagator momentum of the events below, as signed particles
-COLLINEAR_TERMS = {PROCS[2]: ((1, 0), (-1, 4)), PROCS[3]: ((1, 4), (1, 5))}
-
-
-def _collinear_events(process, n, seed, theta=(3e-3, 1e-2), sqrt_s=1500.0, mt=173.0):
-    """Events with a gluon propagator that is nearly on shell, at sqrt(s).
-    * g g > t t~ g g: the two final gluons are a small angle theta apart, so
-      (k1 + k2)^2 ~ E1 E2 theta^2.
-    * g g > t t~ g: the final gluon is theta from the first beam, so the t-channel
-      invariant is (p1 - k)^2 ~ -E1 E theta^2.
-    The gluons are massless, E (1, n), and the top pair balances them.  The invariant is
-    then 1e4 to 1e6 times smaller than the square of the summed energies."""
-    rng = np.random.default_rng(seed)
-    npar = 6 if process == PROCS[3] else 5
-    mom = np.zeros((n, npar, 4))
-    h = sqrt_s / 2
-    p1, p2 = np.array([h, 0, 0, h]), np.array([h, 0, 0, -h])
-    for e in range(n):
-        th = rng.uniform(*theta)
-        if process == PROCS[3]:
-            nv = rng.normal(size=3)
-            nv /= np.linalg.norm(nv)
-            m = np.cross(nv, rng.normal(size=3))
-            m /= np.linalg.norm(m)
-            n2 = np.cos(th) * nv + np.sin(th) * m
-            e1, e2 = rng.uniform(100.0, 300.0, size=2)
-            gl = [np.concatenate([[e1], e1 * nv]), np.concatenate([[e2], e2 * n2])]
-        else:
-            en, phi = rng.uniform(100.0, 300.0), rng.uniform(0, 2 * np.pi)
-            gl = [en * np.array([1.0, np.sin(th) * np.cos(phi), np.sin(th) * np.sin(phi), np.cos(th)])]
-        tops = _top_pair(p1 + p2 - sum(gl), mt, rng)
-        mom[e] = [p1, p2] + tops + gl
-    return mom
-
-
 @pytest.mark.parametrize("process", [p for p in ACTIVE if p in (PROCS[2], PROCS[3])])
 def test_nearly_collinear_gluons(process):
     """On events whose gluon propagator invariant cancels four to six digits, a plain FP64
@@ -187,7 +140,7 @@ def test_nearly_collinear_gluons(process):
     flag every such event for their FP64 rescue pass, and so return the FP64 mode's bits."""
     from fractions import Fraction
     n = 64
-    mom = _collinear_events(process, n, seed=31)
+    mom = collinear_events(process, n, seed=31)
     np.testing.assert_allclose(mom[:, 2:].sum(axis=1), mom[:, :2].sum(axis=1), rtol=0, atol=1e-9)
     rng = np.random.default_rng(32)
     rh, rc = rng.random(n), rng.random(n)

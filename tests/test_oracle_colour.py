@@ -1,8 +1,8 @@
 """Pins of the oracle's colour algebra and of its colour-ordered recursion.
 
 * The Fierz-evaluated colour matrix C_st = Tr(T^s (T^t)^dagger) equals the same trace
-  summed over explicit Gell-Mann matrices (brute force) for two and three gluons, is
-  symmetric positive semi-definite, and has the closed-form diagonal C_F^n N.
+  summed over explicit Gell-Mann matrices (brute force) entry by entry for two to five
+  gluons, is symmetric positive semi-definite, and has the closed-form diagonal C_F^n N.
 * The full spin- and colour-summed |M|^2 for g g -> t t~ and g g -> t t~ g equals an
   explicit-colour Feynman-rule computation (tests/explicit_colour.py) that uses no
   colour decomposition at all.
@@ -35,6 +35,26 @@ def brute_colour_matrix(n):
     return C
 
 
+def brute_colour_matrix_batched(n, chunk=4096):
+    """The same explicit sum over all 8^n colour assignments, vectorised: for a chunk of
+    assignments, the string products of every ordering are formed as batched 3x3
+    products and C += Re(X X^dagger) over the flattened (assignment, i, j) axis."""
+    perms = list(itertools.permutations(range(n)))
+    assign = np.array(list(itertools.product(range(8), repeat=n)), dtype=np.int64)
+    C = np.zeros((len(perms), len(perms)))
+    for a0 in range(0, len(assign), chunk):
+        a = assign[a0:a0 + chunk]
+        X = np.empty((len(perms), len(a), 9), dtype=complex)
+        for s, p in enumerate(perms):
+            m = ec.T[a[:, p[0]]]
+            for j in p[1:]:
+                m = m @ ec.T[a[:, j]]
+            X[s] = m.reshape(len(a), 9)
+        X = X.reshape(len(perms), -1)
+        C += np.real(X @ X.conj().T)
+    return C
+
+
 def test_ggtt_colour_matrix_exact(oracle_mod):
     num, den = oracle_mod.colour_matrix("g g > t t~")
     assert np.array_equal(num * (3 // den), np.array([[16, -2], [-2, 16]]))
@@ -44,6 +64,22 @@ def test_ggtt_colour_matrix_exact(oracle_mod):
 def test_colour_matrix_matches_explicit_sum(oracle_mod, n, proc):
     num, den = oracle_mod.colour_matrix(proc)
     assert np.allclose(num / den, brute_colour_matrix(n), rtol=1e-13, atol=1e-13)
+
+
+@pytest.mark.parametrize("n,proc", [(2, "g g > t t~"), (3, "g g > t t~ g"), (4, "g g > t t~ g g"),
+                                    (5, "g g > t t~ g g g")])
+def test_colour_matrix_matches_explicit_sum_every_entry(oracle_mod, n, proc):
+    """Entry by entry against the explicit Gell-Mann sum for 24 and 120 flows too, so
+    that a wrong power of 1/N in an off-diagonal entry cannot hide behind permutation
+    covariance.  The sum runs in FP64 over 8^n terms of size O(1); every exact entry
+    is a rational with denominator dividing 324."""
+    num, den = oracle_mod.colour_matrix(proc)
+    B = brute_colour_matrix_batched(n)
+    assert B.shape == num.shape
+    assert np.max(np.abs(num / den - B)) < 1e-10
+    # the brute force resolves every distinct entry: rounding it to the oracle's
+    # denominators gives back the oracle's numerators exactly
+    assert np.array_equal(np.rint(B * den).astype(np.int64), num)
 
 
 @pytest.mark.parametrize("proc", QCD)
@@ -75,3 +111,31 @@ def test_explicit_colour_brute_force(oracle_mod, proc, roles):
     for e in range(mom.shape[0]):
         ref = ec.summed_me2(mom[e], 173.0, gs, roles) / iden
         assert abs(out["me"][e] / ref - 1) < 1e-12, (e, out["me"][e], ref)
+
+
+@pytest.mark.parametrize("zwt", [0, 1])
+def test_explicit_colour_top_width_and_zero_width_tchannel(oracle_mod, zwt):
+    """g g > t t~ g at the physical top width: the oracle's width per top propagator,
+    in every one (zwt = 0) or only where the propagator is not in the t channel
+    (zwt = 1), equals the explicit-colour computation with its own per-propagator
+    width rule.  On these events the width moves |M|^2 far above the tolerance, in the
+    s-channel propagators (top + final gluon) as well as in the t-channel ones, so a
+    rule that dropped the width from the wrong propagators would fail."""
+    proc, roles = "g g > t t~ g", ["gin", "gin", "t", "tb", "gout"]
+    cand, _, _, _ = ps.make_batch(proc, 64, seed=23)
+    # the event of this seeded batch whose s-channel top propagator (top or antitop plus
+    # the final gluon) is nearest its pole, where the width matters most
+    dots = lambda a, b: a[..., 0] * b[..., 0] - np.sum(a[..., 1:] * b[..., 1:], axis=-1)
+    near = np.minimum(dots(cand[:, 2], cand[:, 4]), dots(cand[:, 3], cand[:, 4]))
+    mom = cand[np.argsort(near)[:1]]
+    wt = 1.4915
+    gs = math.sqrt(4 * math.pi * 0.118)
+    _, _, _, iden = oracle_mod.info(proc)
+    out = oracle_mod.me(proc, mom, params=oracle_mod.Params(wt=wt, zero_width_tchan=zwt))["me"]
+    for e in range(mom.shape[0]):
+        ref = ec.summed_me2(mom[e], 173.0, gs, roles, wt=wt, zero_width_tchan=bool(zwt)) / iden
+        assert abs(out[e] / ref - 1) < 1e-12, (e, out[e], ref)
+        # the other rules differ by far more than the tolerance
+        for other in ({"wt": 0.0}, {"wt": wt, "zero_width_tchan": not zwt}):
+            alt = ec.summed_me2(mom[e], 173.0, gs, roles, **other) / iden
+            assert abs(alt / ref - 1) > 1e-8, (e, other, abs(alt / ref - 1))
