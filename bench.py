@@ -7,7 +7,10 @@ path (momentum load, couplings, wavefunctions, currents, diagram closings, colou
 helicity sum, selections).  Inputs (226 MB) are larger than the 126 MB L2, so no L2
 flush is needed between steps.  Each precision mode is timed separately; the headline
 ``value`` is the mode named by --mode (default: fp64, the mode that matches the FP64
-oracle at 1e-12).
+oracle at 1e-12).  The default single-GPU run also carries the rest of the metric in the
+same JSON line: every process at its own workload size in each precision mode
+(``processes``) and a short serving stream in mixed precision and in FP64 with p50/p99
+latency (``serving``); --no-extra leaves them out.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--mode fp64|fp32|mixed]
     python bench.py --impl reference      # the FP64 CPU oracle on the host cores
@@ -40,16 +43,16 @@ METRIC = "ME evals/s per process, FP64 vs mixed at stated rel. err; serving p50/
 UNIT = "ME evals/s"
 FLOP_DTYPE = {"fp64": "f64", "fp32": "f32", "mixed": "f32+bf16"}
 ERR_BOUND = {"fp64": 1e-12, "fp32": 1e-5, "mixed": 1e-5}
-# DRAM bytes per event of each mode's default main-pass kernel, from one ncu capture of
-# 655360 events (profiles/me_kernel_*_655360.md); the traffic grows with the events
-# processed.  Keyed by the kernel's layout, so a changed default reports no traffic.
+# DRAM bytes per event of each mode's default main-pass kernel of g g > t t~ g g, from
+# one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of a 655360-event launch;
+# the traffic grows with the events processed.  Keyed by the kernel's layout, so a
+# changed default reports no traffic.
 DRAM_BYTES_PER_EVENT = {
     ("fp64", "Layout<3, 64, 1, 1, 1, 2, 2, 3, 1>"): 1.421e11 / 655360,
     ("fp32", "Layout<1, 64, 1, 0, 1, 1, 2, 3, 1>"): 9.812e8 / 655360,
-    ("mixed", "Layout<1, 128, 1, 1, 1, 2, 2, 0, 1>"): 1.492e9 / 655360,
 }
 DEFAULT_LAYOUT = {"fp64": "Layout<3, 64, 1, 1, 1, 2, 2, 3, 1>", "fp32": "Layout<1, 64, 1, 0, 1, 1, 2, 3, 1>",
-                  "mixed": "Layout<1, 128, 1, 1, 1, 2, 2, 0, 1>"}
+                  "mixed": "pipelined Layout<1, 128, 1, 0, 1, 2, 2, 3, 1>"}
 
 
 def dist_env():
@@ -288,7 +291,7 @@ def time_unweight(me, warmup, reps):
     return out
 
 
-def accuracy_sample(mode_out, host_inputs, n=48, process=None):
+def accuracy_sample(mode_out, host_inputs, n=4096, process=None):
     """max / median relative error of a mode against the FP64 oracle on sampled events"""
     import oracle
     hmom, ha, hrh, hrc = (x.numpy() for x in host_inputs)
@@ -298,6 +301,41 @@ def accuracy_sample(mode_out, host_inputs, n=48, process=None):
     got = mode_out.cpu().numpy()[idx]
     rel = np.abs(got / ref - 1)
     return float(rel.max()), float(np.median(rel)), len(idx)
+
+
+def process_row(process, nevt, alphas, modes, peaks, steps, err_n, budget_s=10.0):
+    """ME/s of one process at nevt events for each precision mode, with the achieved
+    fraction of the measured FMA peak and the error against the FP64 oracle on err_n
+    sampled events; steps adapt so that each mode's timed work stays near budget_s"""
+    import torch
+    from paper_2312_02898_b300 import binding
+    from paper_2312_02898_b300 import phasespace as ps
+    mom, a, rh, rc = ps.make_batch(process, nevt, seed=0, alphas=alphas)
+    if a is None:
+        a = np.full(nevt, 0.118)
+    host = [torch.from_numpy(x).pin_memory() for x in (mom, a, rh, rc)]
+    dev = [x.cuda(non_blocking=True) for x in host]
+    torch.cuda.synchronize()
+    row = {"events": nevt, "input_mb": round(sum(x.numel() * x.element_size() for x in host) / 1e6, 1)}
+    for mode in modes:
+        # one untimed probe call sizes the steps (and allocates the workspace)
+        try:
+            probe = time_mode(mode, dev, host, 1, 0, None, process=process, e2e=False)
+        except binding.MEError as e:
+            row[mode] = {"unavailable": str(e)}
+            continue
+        k = int(max(2, min(steps, budget_s / max(probe["ms"] * 1e-3, 1e-6))))
+        r = time_mode(mode, dev, host, k, 2 if probe["ms"] < 1000 else 0, None, process=process, e2e=False)
+        mx, med, ns = accuracy_sample(r["me"], host, n=err_n, process=process)
+        tf = r["flops_per_event"] * nevt / (r["ms"] * 1e-3) / 1e12
+        pk = peaks["fp64" if mode == "fp64" else "fp32"] / 1e12
+        row[mode] = {"me_per_s": nevt / (r["ms"] * 1e-3), "ms_per_step": r["ms"], "steps": k, "tflops": tf,
+                     "frac_of_measured_peak": tf / pk, "launches_per_step": r["launches"], "max_rel_err": mx,
+                     "median_rel_err": med, "err_sample": ns, "bound": ERR_BOUND[mode], "clocks": r["clocks"]}
+        del r, probe
+    del dev, host
+    torch.cuda.synchronize()
+    return row
 
 
 def run_gpu(args):
@@ -330,7 +368,7 @@ def run_gpu(args):
         raise SystemExit(f"headline mode {args.mode} failed: {head['error']}")
     value = world * NEVT / (head["ms"] * 1e-3)
     unw = time_unweight(head["me"], args.warmup, max(args.steps, 10))
-    testbed = time_testbed(args.mode, args.steps, args.warmup)
+    testbed = time_testbed(args.mode, min(args.steps, 3), 3)
     peaks = {p: binding.alu_peak(p, 0.3) for p in ("fp64", "fp32")}
     per_launch_ms = head["ms"] / head["launches"]
     events_per_launch = NEVT / head["launches"]
@@ -344,7 +382,7 @@ def run_gpu(args):
             if "error" in r:
                 acc[mode] = {"error": r["error"]}
                 continue
-            mx, med, ns = accuracy_sample(r["me"], host)
+            mx, med, ns = accuracy_sample(r["me"], host, n=args.err_sample)
             acc[mode] = {"value": NEVT * world / (r["ms"] * 1e-3), "ms_per_step": r["ms"],
                          "max_rel_err": mx, "median_rel_err": med, "err_sample": ns, "bound": ERR_BOUND[mode],
                          "gpu_launches_per_step": r["launches"], "clocks": r["clocks"]}
@@ -381,6 +419,11 @@ def run_gpu(args):
                 "testbed": testbed,
                 "cpu_baseline": cpu,
                 "alu_peaks_tflops": {k: v / 1e12 for k, v in peaks.items()}}
+        if world == 1 and not args.no_extra:
+            # the rest of the metric: every process at its own workload size, and the
+            # serving stream in mixed precision beside the same stream in FP64
+            line["processes"] = processes_table(args, peaks, reuse={PROCESS: (results, acc)})
+            line["serving"] = serving_table(args, quick=True)
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
@@ -392,44 +435,44 @@ PROCESS_TABLE = (("e+ e- > mu+ mu-", 16384, None), ("g g > t t~", 524288, 0.118)
                  ("g g > t t~ g g", 1048576, "uniform"), ("g g > t t~ g g g", 262144, 0.118))
 
 
-def run_processes(args):
-    """ME/s of every process and precision at its own workload size, with the achieved
-    fraction of the measured FP64 / FP32 FMA peak and the error against the oracle on
-    sampled events (one JSON line)."""
-    import torch
-    from paper_2312_02898_b300 import binding
-    from paper_2312_02898_b300 import phasespace as ps
-    torch.cuda.set_device(0)
-    peaks = {p: binding.alu_peak(p, 0.3) for p in ("fp64", "fp32")}
+def processes_table(args, peaks, reuse=None):
+    """per-process rows (process_row) for every process of PROCESS_TABLE; a process whose
+    modes were already timed at its workload size (the headline step) reuses them"""
     table = {}
     for process, nevt, alphas in PROCESS_TABLE:
         if args.only_process and args.only_process != process:
             continue
         if args.process_nevt:
             nevt = args.process_nevt
-        mom, a, rh, rc = ps.make_batch(process, nevt, seed=0, alphas=alphas)
-        if a is None:
-            a = np.full(nevt, 0.118)
-        host = [torch.from_numpy(x).pin_memory() for x in (mom, a, rh, rc)]
-        dev = [x.cuda(non_blocking=True) for x in host]
-        torch.cuda.synchronize()
-        row = {"events": nevt, "input_mb": round(sum(x.numel() * x.element_size() for x in host) / 1e6, 1)}
-        for mode in args.process_modes.split(","):
-            try:
-                r = time_mode(mode, dev, host, args.steps, args.warmup, None, process=process, e2e=False)
-            except binding.MEError as e:
-                row[mode] = {"unavailable": str(e)}
-                continue
-            mx, med, ns = accuracy_sample(r["me"], host, n=24, process=process)
-            tf = r["flops_per_event"] * nevt / (r["ms"] * 1e-3) / 1e12
-            pk = peaks["fp64" if mode == "fp64" else "fp32"] / 1e12
-            row[mode] = {"me_per_s": nevt / (r["ms"] * 1e-3), "ms_per_step": r["ms"], "tflops": tf,
-                         "frac_of_measured_peak": tf / pk, "launches_per_step": r["launches"],
-                         "max_rel_err": mx, "median_rel_err": med, "err_sample": ns, "clocks": r["clocks"]}
-            del r
-        table[process] = row
-        del dev, host
-        torch.cuda.synchronize()
+        if reuse and process in reuse and nevt == NEVT:
+            results, acc = reuse[process]
+            row = {"events": nevt, "reused": "the headline step of this run"}
+            for mode, r in results.items():
+                if "error" in r:
+                    row[mode] = {"unavailable": r["error"]}
+                    continue
+                tf = r["flops_per_event"] * nevt / (r["ms"] * 1e-3) / 1e12
+                pk = peaks["fp64" if mode == "fp64" else "fp32"] / 1e12
+                row[mode] = {"me_per_s": nevt / (r["ms"] * 1e-3), "ms_per_step": r["ms"], "tflops": tf,
+                             "frac_of_measured_peak": tf / pk, "launches_per_step": r["launches"],
+                             "max_rel_err": acc[mode]["max_rel_err"], "median_rel_err": acc[mode]["median_rel_err"],
+                             "err_sample": acc[mode]["err_sample"], "bound": ERR_BOUND[mode]}
+            table[process] = row
+            continue
+        modes = [m for m in args.process_modes.split(",")]
+        table[process] = process_row(process, nevt, alphas, modes, peaks, args.steps, args.process_err_sample)
+    return table
+
+
+def run_processes(args):
+    """ME/s of every process and precision at its own workload size, with the achieved
+    fraction of the measured FP64 / FP32 FMA peak and the error against the oracle on
+    sampled events (one JSON line)."""
+    import torch
+    from paper_2312_02898_b300 import binding
+    torch.cuda.set_device(0)
+    peaks = {p: binding.alu_peak(p, 0.3) for p in ("fp64", "fp32")}
+    table = processes_table(args, peaks)
     line = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": True, "data": "synthetic (RAMBO, Philox4x32-10 seed 0)",
             "config": {"workload": "every process at its own batch size, inputs resident, both selections"},
@@ -444,17 +487,24 @@ def _gen_request(item):
     return t, proc, mom, a, rh, rc
 
 
-def run_serving(args):
+def serving_table(args, quick=False):
     """The serving stream: Poisson arrivals of requests for all processes (weights
     0.1 / 0.15 / 0.15 / 0.4 / 0.2 for e+e- -> mu+mu-, gg -> tt~, gg -> tt~g, gg -> tt~gg,
     gg -> tt~ggg), sizes log-uniform in [256, 65536], request k from seed k.  For each
     precision: the sustained capacity with every request queued at once, then the
     open-loop stream at fractions of that capacity with p50/p99 latency (submit to
-    results on the host)."""
+    results on the host), pooled and per process.  quick: the short form the default
+    benchmark run carries (fewer requests, 70% load only, no first-come comparison)."""
     import concurrent.futures as cf
     import multiprocessing as mp
     from paper_2312_02898_b300 import serving
-    nreq = args.serving_requests + args.serving_warmup
+    if quick:
+        nmeas, nwarm, nother, loads_first, fifo = args.quick_serving_requests, 50, 100, [0.7], False
+    else:
+        nmeas, nwarm, nother, fifo = args.serving_requests, args.serving_warmup, args.serving_requests_other, True
+        loads_first = [float(x) for x in args.serving_loads.split(",")]
+    nother_warm = min(nwarm, 20) if quick else nwarm
+    nreq = nmeas + nwarm
     stream = serving.request_stream(nreq, rate_hz=1.0, seed=0)
     with cf.ProcessPoolExecutor(max_workers=min(32, os.cpu_count() or 1), mp_context=mp.get_context("spawn")) as ex:
         reqs = list(ex.map(_gen_request, stream, chunksize=8))
@@ -462,7 +512,8 @@ def run_serving(args):
     mean_events = float(np.mean([r[2].shape[0] for r in reqs]))
     out = {}
     runs = [(prec, "srpt") for prec in args.serving_precisions.split(",")]
-    runs.insert(1, (runs[0][0], "fifo"))  # the same precision with first-come scheduling, for comparison
+    if fifo:
+        runs.insert(1, (runs[0][0], "fifo"))  # the same precision with first-come scheduling, for comparison
     for prec, policy in runs:
         server = serving.Server([p for p, _ in serving.STREAM_PROCESSES], precision=prec, n_slots=args.serving_slots,
                                 policy=policy, chunk_events=args.serving_chunk)
@@ -474,19 +525,21 @@ def run_serving(args):
             warm_s = time.perf_counter() - t0
             first = not out
             same_stream = first or policy == "fifo"   # fifo replays the whole stream beside srpt
+            # the slower precisions replay a prefix of the same stream (their own warm-up)
+            warm = nwarm if same_stream else nother_warm
+            sub = reqs if same_stream else reqs[nwarm - warm: nwarm + nother]
             if policy == "fifo":
                 cap = next(iter(out.values()))["capacity_me_per_s"]
             else:
-                ncap = args.serving_warmup + (args.serving_requests // 4 if first else args.serving_requests_other // 4)
-                cap = serving.run_saturated(server, reqs[:ncap])
+                cap = serving.run_saturated(server, sub[: warm + (nmeas if same_stream else nother) // 4])
             res = {"capacity_me_per_s": cap, "graphs": len(server.buffers), "warm_s": warm_s, "policy": policy,
-                   "chunk_events": server.chunk, "precision_per_process": server.precision, "load": {}}
-            loads = [float(x) for x in args.serving_loads.split(",")] if first else [0.7]
-            # the slower precisions replay a prefix of the same stream
-            sub = reqs if same_stream else reqs[: args.serving_warmup + args.serving_requests_other]
+                   "chunk_events": server.chunk, "precision_per_process": server.precision,
+                   "workspace_bytes": server.workspace_bytes, "mem_budget_bytes": server.mem_budget,
+                   "requests_measured": len(sub) - warm, "requests_warmup": warm, "load": {}}
+            loads = loads_first if first else [0.7]
             for frac in loads:
                 rate = frac * cap / mean_events                   # requests per second
-                st = serving.run_open_loop(server, sub, rate_scale=rate, warmup=args.serving_warmup)
+                st = serving.run_open_loop(server, sub, rate_scale=rate, warmup=warm)
                 st["offered_requests_per_s"] = rate
                 st["offered_me_per_s"] = frac * cap
                 res["load"][f"{int(round(frac * 100))}%"] = st
@@ -495,16 +548,25 @@ def run_serving(args):
             server.close()
             del server
             torch.cuda.synchronize()
-    head = out[args.serving_precisions.split(",")[0]]
+    return {"slots": args.serving_slots, "buckets": list(serving.BUCKETS), "mean_events_per_request": mean_events,
+            "stream": "Poisson arrivals over the five processes, log-uniform 256-65536 events per request, "
+                      "alpha_s~U[0.10,0.13], request k from seed k; latency = submit to results on the host",
+            "precisions": out}
+
+
+def run_serving(args):
+    """the full serving study as its own JSON line (headline: p99 at 70% load)"""
+    res = serving_table(args)
+    head = next(iter(res["precisions"].values()))
     key = "70%" if "70%" in head["load"] else next(iter(head["load"]))
     line = {"metric": METRIC, "value": head["load"][key]["p99_ms"], "unit": "ms (p99 latency)",
             "higher_is_better": False, "n_gpus": 1, "steps": args.serving_requests, "warmup": args.serving_warmup,
             "data": "synthetic (RAMBO, Philox4x32-10, request k from seed k)",
             "config": {"workload": "serving stream: Poisson arrivals over the five processes, "
                                    "log-uniform 256-65536 events per request, alpha_s~U[0.10,0.13]",
-                       "slots": args.serving_slots, "buckets": list(serving.BUCKETS),
-                       "mean_events_per_request": mean_events, "headline_load": key},
-            "serving": out}
+                       "slots": args.serving_slots, "buckets": res["buckets"],
+                       "mean_events_per_request": res["mean_events_per_request"], "headline_load": key},
+            "serving": res["precisions"]}
     print(json.dumps(line), flush=True)
 
 
@@ -535,6 +597,14 @@ def main():
     ap.add_argument("--only-process", default="", help="with --processes: only this process")
     ap.add_argument("--process-nevt", type=int, default=0, help="with --processes: events instead of the workload's")
     ap.add_argument("--process-modes", default="fp64,fp32,mixed", help="with --processes: precisions to time")
+    ap.add_argument("--process-err-sample", type=int, default=256,
+                    help="oracle events per process and mode for the error of the per-process table")
+    ap.add_argument("--err-sample", type=int, default=4096,
+                    help="oracle events for the max / median error of each mode of the step")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="leave the per-process table and the serving stream out of the default run")
+    ap.add_argument("--quick-serving-requests", type=int, default=300,
+                    help="measured requests of the mixed stream in the default run (FP64: 100)")
     args = ap.parse_args()
     globals()["NEVT"] = args.nevt
     if args.serving:

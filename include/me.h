@@ -38,6 +38,15 @@
  *
  * Errors: every call returns 0 on success or a negative status; me_last_error gives
  * the message.  Non-finite momenta produce NaN in me for that event only.
+ *
+ * Device-side timeouts: the mixed-precision kernel waits for its tensor-core work with
+ * a bounded spin.  If a wait runs out (it never should), the kernel records it in a
+ * flag of the handle, sets the matrix element of every event of that main pass to NaN
+ * (its selections to 0; the FP64 rescue pass that follows may still fill in the events
+ * it re-evaluates), and exits cleanly, so the CUDA context stays usable.  The host learns
+ * of it asynchronously: me_sync_status reports it; otherwise the next me_compute or
+ * me_compute_noalloc on the handle returns ME_ERR_TIMEOUT instead of computing, and
+ * me_compute_host reports it for its own call.  Reporting clears the flag.
  */
 #ifndef ME_B300_H
 #define ME_B300_H
@@ -130,12 +139,13 @@ int me_compute_host(me_handle* h, int64_t nevt, const double* momenta, const dou
  * The kernels' scratch (helicity running sums, slot buffer, momentum table, colour
  * weights) is one fixed 32 MiB device array inside the library, held on every GPU that
  * loads the library until the process exits.  A batch that needs more scratch than that
- * is rejected with ME_ERR_ARG and a message giving the limit (for "g g > t t~ g g" in
- * FP64 about 9000 events per call).  The first call on a device looks up the array's
- * device address; make it before any stream capture.  Every call uses the same array
- * and leaves its contents behind: calls whose work overlaps on the GPU (other streams,
- * other handles) race on it, so the caller must serialise them.  Arguments, outputs and
- * the other errors are those of me_compute. */
+ * is rejected with ME_ERR_ARG and a message giving the exact largest batch that fits
+ * (for "g g > t t~ g g" in FP64 about 9000 events per call).  The first call on a device,
+ * and the first after the device's CUDA context was replaced (a device reset), looks up
+ * the array's device address; make it before any stream capture.  Every call uses the
+ * same array and leaves its contents behind: calls whose work overlaps on the GPU (other
+ * streams, other handles) race on it, so the caller must serialise them.  Arguments,
+ * outputs and the other errors are those of me_compute. */
 int me_compute_noalloc(me_handle* h, int64_t nevt, const double* momenta, const double* alphas,
                        const double* rnd_hel, const double* rnd_col, double* me, int32_t* sel_hel,
                        int32_t* sel_col, void* cuda_stream);
@@ -211,6 +221,19 @@ int me_reserve(me_handle* h, int64_t nevt, void* cuda_stream);
  * persistent grid, threads per block, resident blocks per SM of the kernel, SMs of the
  * handle's device.  Any output pointer may be NULL.  Errors: ME_ERR_ARG. */
 int me_launch_shape(const me_handle* h, int64_t nevt, int* grid, int* block, int* blocks_per_sm, int* nsm);
+
+/* Wait for cuda_stream, then report whether a device-side wait of an earlier call on
+ * this handle ran out (see "Device-side timeouts" above): ME_OK, or ME_ERR_TIMEOUT
+ * (the flag is then cleared).  Errors: ME_ERR_ARG (null handle), ME_ERR_CUDA. */
+int me_sync_status(me_handle* h, void* cuda_stream);
+
+/* Testing hook for the timeout path: the number of polls the mixed kernel's wait for
+ * its tensor-core work makes before it gives up, for later calls on this handle.
+ * polls < 0 restores the default (2^22 polls); 0 makes the wait give up at once, so
+ * that a test can drive the timeout path without any fault.  The kernel's final wait,
+ * which keeps its tensor memory allocated until every issued MMA has completed, always
+ * keeps the default limit.  Errors: ME_ERR_ARG (null handle). */
+int me_set_wait_limit(me_handle* h, int64_t polls);
 
 /* Select the kernel launch configuration (register budget, block size, placement of
  * per-thread arrays) used by later me_compute calls; 0 is the default.  Returns the

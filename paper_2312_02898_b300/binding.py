@@ -18,7 +18,8 @@ PRECISIONS = {"fp64": 0, "fp32": 1, "mixed": 2}
 # the C-ABI entry points declared in include/me.h
 EXPORTS = ("me_default_params", "me_init", "me_compute", "me_compute_host", "me_info", "me_good_helicities",
            "me_flops", "me_plan", "me_reserve", "me_launch_shape", "me_set_config", "me_last_error", "me_free",
-           "me_compute_noalloc", "me_unweight", "me_rambo", "me_uniforms", "me_probe_alu_peak")
+           "me_compute_noalloc", "me_unweight", "me_rambo", "me_uniforms", "me_probe_alu_peak", "me_sync_status",
+           "me_set_wait_limit")
 
 
 class SMParams(ctypes.Structure):
@@ -63,6 +64,8 @@ def load(path: str = LIB_PATH):
     lib.me_good_helicities.argtypes = [vp, ctypes.POINTER(ctypes.c_int32)]
     lib.me_flops.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
     lib.me_set_config.argtypes = [vp, ctypes.c_int]
+    lib.me_sync_status.argtypes = [vp, vp]
+    lib.me_set_wait_limit.argtypes = [vp, i64]
     lib.me_plan.argtypes = [vp, i64, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
     lib.me_probe_alu_peak.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
     lib.me_last_error.argtypes = [vp]
@@ -71,7 +74,7 @@ def load(path: str = LIB_PATH):
     lib.me_free.restype = None
     for f in ("me_init", "me_compute", "me_compute_host", "me_compute_noalloc", "me_info", "me_good_helicities",
               "me_flops", "me_set_config", "me_plan", "me_reserve", "me_launch_shape", "me_unweight",
-              "me_rambo", "me_uniforms", "me_probe_alu_peak"):
+              "me_rambo", "me_uniforms", "me_probe_alu_peak", "me_sync_status", "me_set_wait_limit"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -96,6 +99,25 @@ def alu_peak(precision: str, seconds: float = 0.3) -> float:
 
 def _ptr(t):
     return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _check_tensor(name, t, dtype, shape, device, required=False):
+    """raise ValueError unless t (a torch tensor, or None where allowed) has the dtype,
+    shape and device the C ABI expects and is contiguous: the library reads raw pointers,
+    and a temporary contiguous copy made here could be recycled by the caching allocator
+    before a kernel on another stream has read it"""
+    if t is None:
+        if required:
+            raise ValueError(f"{name} is required")
+        return
+    if t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, not {t.dtype}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, not {tuple(t.shape)}")
+    if t.device != device:
+        raise ValueError(f"{name} must be on {device}, not {t.device}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
 
 
 def device_uniforms(nevt, seed, first_event, stream_id, offset=0.0, scale=1.0, stream=None):
@@ -175,13 +197,30 @@ class MatrixElement:
         if rc != ME_OK:
             raise MEError(rc, self.lib.me_last_error(self.handle).decode())
 
+    def _check_args(self, momenta, alphas, rnd_hel, rnd_col, out, device):
+        """dtype, shape, device and contiguity of every tensor argument (ValueError)"""
+        import torch
+        nevt = momenta.shape[0] if momenta.dim() else -1
+        f64, i32 = torch.float64, torch.int32
+        _check_tensor("momenta", momenta, f64, (nevt, self.npar, 4), device, required=True)
+        for name, t in (("alphas", alphas), ("rnd_hel", rnd_hel), ("rnd_col", rnd_col)):
+            _check_tensor(name, t, f64, (nevt,), device)
+        me, sh, sc = out
+        _check_tensor("me", me, f64, (nevt,), device, required=True)
+        _check_tensor("sel_hel", sh, i32, (nevt,), device)
+        _check_tensor("sel_col", sc, i32, (nevt,), device)
+        if (sh is not None and rnd_hel is None) or (sc is not None and rnd_col is None):
+            raise ValueError("a selection output needs its random numbers")
+        return nevt
+
     def compute(self, momenta, alphas=None, rnd_hel=None, rnd_col=None, out=None, stream=None):
-        """Device tensors in, device tensors out (asynchronous on ``stream``)."""
+        """Device tensors in, device tensors out (asynchronous on ``stream``).  Every
+        tensor must be contiguous, of the documented dtype and length, and on the
+        device of ``momenta``."""
         import torch
         if not momenta.is_cuda:
             raise ValueError("momenta must be a CUDA tensor (use compute_host for host arrays)")
         nevt = momenta.shape[0]
-        momenta = momenta.contiguous()
         dev = momenta.device
         if out is None:
             me = torch.empty(nevt, dtype=torch.float64, device=dev)
@@ -189,6 +228,7 @@ class MatrixElement:
             sc = torch.empty(nevt, dtype=torch.int32, device=dev) if rnd_col is not None else None
         else:
             me, sh, sc = out
+        self._check_args(momenta, alphas, rnd_hel, rnd_col, (me, sh, sc), dev)
         s = stream if stream is not None else torch.cuda.current_stream(dev)
         rc = self.lib.me_compute(self.handle, nevt, _ptr(momenta), _ptr(alphas), _ptr(rnd_hel), _ptr(rnd_col),
                                  _ptr(me), _ptr(sh), _ptr(sc), ctypes.c_void_p(s.cuda_stream))
@@ -227,7 +267,8 @@ class MatrixElement:
         self._check(rc)
 
     def compute_host(self, momenta, alphas=None, rnd_hel=None, rnd_col=None, out=None, stream=None):
-        """Host (ideally pinned) tensors in and out; the copies happen inside the library."""
+        """Host (ideally pinned) tensors in and out; the copies happen inside the library.
+        Every tensor must be a contiguous CPU tensor of the documented dtype and length."""
         import torch
         nevt = momenta.shape[0]
         if out is None:
@@ -236,11 +277,23 @@ class MatrixElement:
             sc = torch.empty(nevt, dtype=torch.int32).pin_memory() if rnd_col is not None else None
         else:
             me, sh, sc = out
+        self._check_args(momenta, alphas, rnd_hel, rnd_col, (me, sh, sc), torch.device("cpu"))
         s = stream if stream is not None else torch.cuda.current_stream()
         rc = self.lib.me_compute_host(self.handle, nevt, _ptr(momenta), _ptr(alphas), _ptr(rnd_hel), _ptr(rnd_col),
                                       _ptr(me), _ptr(sh), _ptr(sc), ctypes.c_void_p(s.cuda_stream))
         self._check(rc)
         return me, sh, sc
+
+    def sync_status(self, stream=None):
+        """wait for ``stream``; raise MEError(ME_ERR_TIMEOUT) if a device-side wait of an
+        earlier call on this handle ran out (the flag is cleared by reporting it)"""
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream()
+        self._check(self.lib.me_sync_status(self.handle, ctypes.c_void_p(s.cuda_stream)))
+
+    def set_wait_limit(self, polls: int):
+        """testing hook: polls of the mixed kernel's MMA wait (negative: default; 0: give up at once)"""
+        self._check(self.lib.me_set_wait_limit(self.handle, polls))
 
     def close(self):
         if getattr(self, "handle", None):

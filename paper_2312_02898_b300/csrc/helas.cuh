@@ -53,6 +53,12 @@ template <class R> HD cx<R> times_i(cx<R> a) { return mk<R>(-a.i, a.r); }
 template <class R> HD void operator+=(cx<R>& a, cx<R> b) { a.r += b.r; a.i += b.i; }
 template <class R> HD void operator-=(cx<R>& a, cx<R> b) { a.r -= b.r; a.i -= b.i; }
 
+// J += i a  and  J -= i a  (the colour-flow accumulation of the generated code)
+template <class R> HD void acc_pi(cx<R>& J, cx<R> a) { J.r -= a.i; J.i += a.r; }
+template <class R> HD void acc_mi(cx<R>& J, cx<R> a) { J.r += a.i; J.i -= a.r; }
+// a * b + c for real types (contracted into one FMA for float and double)
+template <class R> HD R fmadd(R a, R b, R c) { return a * b + c; }
+
 template <class R> HD void copy4(cx<R>* dst, const cx<R>* src) {
 #pragma unroll
   for (int m = 0; m < 4; ++m) dst[m] = src[m];

@@ -32,6 +32,7 @@ struct me_handle {
   int* err_dev = nullptr;
   int nsm = 1;              // streaming multiprocessors of the handle's device
   int max_blocks = 0;       // cap on the persistent grid (0: as many as are resident)
+  int64_t wait_limit = -1;  // polls of the mixed kernel's MMA-completion wait (-1: default)
 };
 
 namespace meb300 {
@@ -52,6 +53,7 @@ struct CallPlan {
   int64_t chunk = 0;
   int grid = 0, block = 0;  // persistent grid of the main pass
   int hsplit = 1;           // threads per event of the main pass (helicity split)
+  int ept = 1;              // events per thread of the main pass (2: packed FP32 kernel)
   Carve main;
   bool rescue = false;
   int rescue_cap = 0, rescue_grid = 0, rescue_hsplit = 1;
@@ -69,7 +71,7 @@ int persistent_grid(const me_handle* h, const LaunchNeeds& nd, int64_t nevt);
 std::vector<double> final_masses(const ProcessOps* ops, double mt);
 cudaError_t launch_chunks(const ProcessOps* ops, int prec, int config, MeLaunch a, int64_t nevt, int64_t chunk,
                           int grid, int block, int hsplit,
-                          const Carve& cv, void* wsp, cudaStream_t s);
+                          const Carve& cv, void* wsp, cudaStream_t s, int ept);
 CallPlan plan_call(const me_handle* h, int64_t nevt, int64_t chunk, bool want_hel, bool want_col);
 cudaError_t run_call(const me_handle* h, const CallPlan& cp, const MeLaunch& a, int64_t nevt, void* wsp, cudaStream_t s);
 

@@ -22,7 +22,6 @@
 
 namespace meb300 {
 
-constexpr uint32_t kMmaWaitLimit = 1u << 22;  // bounded spin on the MMA-completion barrier
 
 template <class P, int NTERM, bool F16>
 struct MixedShape {
@@ -135,10 +134,20 @@ __global__ void __launch_bounds__(128) me_kernel_mixed(const MeLaunch a) {
     else return a.colw[c * wstride + wrow];
   };
 
-  for (int64_t tile = blockIdx.x; tile < ntile && !failed; tile += gridDim.x) {
+  for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
   const int64_t ievt_raw = tile * BLOCK + tid;
   const bool active = ievt_raw < nevt;
   const int64_t ievt = active ? ievt_raw : nevt - 1;
+  if (failed) {
+    // a wait of this block ran out: the rest of its tiles get NaN without any work
+    // (the value of 'failed' is the same in every thread of the block)
+    if (active) {
+      a.me[ievt] = __longlong_as_double(0x7ff8000000000000ll);
+      if (a.sel_hel) a.sel_hel[ievt] = 0;
+      if (a.sel_col) a.sel_col[ievt] = 0;
+    }
+    continue;
+  }
 
   // --- per-event set-up, as in me_kernel
   double pd[P::NPAR][4];
@@ -241,7 +250,7 @@ __global__ void __launch_bounds__(128) me_kernel_mixed(const MeLaunch a) {
         tc::mma_commit(s_mbar);
       }
       // completion also means the MMAs have read the A tiles: the next round may reuse them
-      const bool ok = tc::mbar_wait_bounded(s_mbar, phase, kMmaWaitLimit);
+      const bool ok = tc::mbar_wait_bounded(s_mbar, phase, a.mma_wait_limit);
       phase ^= 1u;
       block_failed = __syncthreads_or(!ok);  // the same value in every thread of the block
       if (block_failed) break;
@@ -315,10 +324,11 @@ __global__ void __launch_bounds__(128) me_kernel_mixed(const MeLaunch a) {
   }
   }  // tile loop
 
-  // --- teardown: no MMA may still be in flight when the columns are freed
+  // --- teardown: no MMA may still be in flight when the columns are freed, so the
+  // wait for the commit that the failed wait gave up on gets the full default limit
   if (failed) {
     if (tid == 0 && a.err) atomicOr(a.err, 1);
-    tc::mbar_wait_bounded(s_mbar, phase ^ 1u, kMmaWaitLimit);
+    tc::mbar_wait_bounded(s_mbar, phase ^ 1u, kMmaWaitDefault);
   }
   tc::fence_before_sync();
   __syncthreads();

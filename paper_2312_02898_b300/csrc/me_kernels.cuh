@@ -29,6 +29,8 @@
 namespace meb300 {
 
 constexpr int MAX_COMB = 128;
+// polls of a bounded spin on an mbarrier before the kernel gives up (error flag, NaN)
+constexpr uint32_t kMmaWaitDefault = 1u << 22;
 
 struct MeLaunch {
   int64_t nevt;
@@ -58,6 +60,7 @@ struct MeLaunch {
   void* dtile;       // [block][nden_g][BLOCK] real, then [block][nden_t][BLOCK] complex (denominators in global memory)
   void* jtile;       // [block][ncol][BLOCK] complex (colour-flow amplitudes in global memory)
   int* err;          // set to 1 when a bounded device-side wait runs out (mapped host memory)
+  uint32_t mma_wait_limit;  // polls of the mixed kernel's wait for its MMAs (0: give up at once)
   // precision rescue (FP32 and mixed passes): events whose conditioning kappa exceeds
   // rescue_kappa are appended, as ibase + local index, to rescue_list (capacity
   // rescue_cap, counter rescue_count) for a later FP64 pass
@@ -462,6 +465,8 @@ struct LaunchNeeds {
   bool colw_global;             // colour weights in a global [ncol][rows] array
   int block;                    // threads per block (global tiles cover whole blocks)
   int blocks_per_sm;            // resident blocks per SM (occupancy of the kernel)
+  int ept = 1;                  // events per thread (2: the packed FP32 kernel); the byte
+                                // counts above are per thread (workspace row)
 };
 
 struct ProcessOps {

@@ -140,6 +140,7 @@ std::vector<double> final_masses(const ProcessOps* ops, double mt) {
 }
 
 void fill_common(const me_handle* h, MeLaunch& a) {
+  a.mma_wait_limit = h->wait_limit < 0 ? kMmaWaitDefault : uint32_t(std::min<int64_t>(h->wait_limit, UINT32_MAX));
   a.alphas_default = h->par.alphas_default;
   a.mt = h->par.mt;
   a.wt = h->par.wt;
@@ -183,8 +184,9 @@ int get_workspace(me_handle* h, uintptr_t key, cudaStream_t s, size_t bytes, voi
 Carve carve(const ProcessOps* ops, const LaunchNeeds& nd, int ngood, int64_t rows, bool want_hel, bool want_col) {
   Carve c;
   auto up = [](size_t b) { return (b + 255) / 256 * 256; };
-  if (want_hel) c.cum = up(size_t(ngood) * rows * sizeof(double));
-  if (want_col && nd.colw_global) c.colw = up(size_t(ops->ncol) * rows * sizeof(double));
+  // running helicity sums and colour weights: one value per event of each row
+  if (want_hel) c.cum = up(size_t(ngood) * rows * nd.ept * sizeof(double));
+  if (want_col && nd.colw_global) c.colw = up(size_t(ops->ncol) * rows * nd.ept * sizeof(double));
   c.slots = up(nd.slot_bytes_per_event * rows);  // rows cover whole blocks
   c.ktab = up(nd.ktab_bytes_per_event * rows);
   c.den = up(nd.den_bytes_per_event * rows);
@@ -194,7 +196,8 @@ Carve carve(const ProcessOps* ops, const LaunchNeeds& nd, int ngood, int64_t row
 
 // Blocks of the persistent grid for nevt events: no more than are resident at once.
 int persistent_grid(const me_handle* h, const LaunchNeeds& nd, int64_t nevt) {
-  const int64_t tiles = (std::max<int64_t>(nevt, 1) + nd.block - 1) / nd.block;
+  const int64_t per_tile = int64_t(nd.block) * nd.ept;
+  const int64_t tiles = (std::max<int64_t>(nevt, 1) + per_tile - 1) / per_tile;
   int64_t resident = int64_t(h->nsm) * nd.blocks_per_sm;
   if (h->max_blocks > 0) resident = std::min<int64_t>(resident, h->max_blocks);
   return int(std::max<int64_t>(1, std::min(tiles, resident)));
@@ -203,7 +206,7 @@ int persistent_grid(const me_handle* h, const LaunchNeeds& nd, int64_t nevt) {
 // Launch 'a' over nevt events in chunks, each on at most 'grid' blocks of 'block'
 // threads with 'hsplit' threads per event, with workspace 'wsp' carved per 'cv'.
 cudaError_t launch_chunks(const ProcessOps* ops, int prec, int config, MeLaunch a, int64_t nevt, int64_t chunk,
-                          int grid, int block, int hsplit, const Carve& cv, void* wsp, cudaStream_t s) {
+                          int grid, int block, int hsplit, const Carve& cv, void* wsp, cudaStream_t s, int ept) {
   char* w = static_cast<char*>(wsp);
   double* cum = cv.cum ? reinterpret_cast<double*>(w) : a.cum;
   double* colw = cv.colw ? reinterpret_cast<double*>(w + cv.cum) : nullptr;
@@ -230,7 +233,8 @@ cudaError_t launch_chunks(const ProcessOps* ops, int prec, int config, MeLaunch 
     b.jtile = jtile;
     b.ibase = off;
     b.hsplit = hsplit;
-    b.grid_blocks = int(std::min<int64_t>(grid, (b.nevt * hsplit + block - 1) / block));
+    const int64_t per_block = int64_t(block) * ept;
+    b.grid_blocks = int(std::min<int64_t>(grid, (b.nevt * hsplit + per_block - 1) / per_block));
     cudaError_t e = ops->launch(prec, config, b, s);
     if (e != cudaSuccess) return e;
   }
@@ -261,20 +265,25 @@ CallPlan plan_call(const me_handle* h, int64_t nevt, int64_t chunk, bool want_he
   }
   cp.grid = persistent_grid(h, nd, chunk * cp.hsplit);
   cp.block = nd.block;
+  cp.ept = nd.ept;
   // the split's first lane reads the group's per-helicity values back from cum
   cp.main = carve(ops, nd, ngood, int64_t(cp.grid) * nd.block, want_hel || cp.hsplit > 1, want_col);
   size_t off = cp.main.total();
   cp.rescue = (cp.prec == ME_PREC_FP32 || cp.prec == ME_PREC_MIXED) && h->par.rescue_kappa > 0;
   if (cp.rescue) {
     const LaunchNeeds n64 = ops->needs(ME_PREC_FP64, 0);
-    const int64_t cap = std::min<int64_t>(nevt, std::max<int64_t>(1024, nevt / 16));
+    // one entry per event (4 bytes each): every flagged event is re-evaluated, however
+    // many a batch holds (a batch from a phase-space channel mapped onto a collinear
+    // region may flag most of its events)
+    const int64_t cap = nevt;
     cp.rescue_cap = int(cap);
     // few events, each far slower in FP64: every event is spread over a group of up to
     // 32 threads, which sum its helicities in the same order as one thread would
     cp.rescue_hsplit = 1;
     while (cp.rescue_hsplit < 32 && 2 * cp.rescue_hsplit <= ngood) cp.rescue_hsplit *= 2;
     // the grid walks the list tile by tile, so any size is correct: it is sized for the
-    // usual flagged fraction (well under 1%), not for the capacity
+    // usual flagged fraction (well under 1%), not for the capacity; a batch that flags
+    // more takes proportionally longer in that pass, never loses an event
     const int64_t expect = std::min<int64_t>(cap, std::max<int64_t>(64, nevt / 100));
     cp.rescue_grid = persistent_grid(h, n64, expect * cp.rescue_hsplit);
     const size_t rows = size_t(cp.rescue_grid) * n64.block;
@@ -304,7 +313,8 @@ cudaError_t run_call(const me_handle* h, const CallPlan& cp, const MeLaunch& a0,
     a.rescue_list = reinterpret_cast<int*>(w + cp.off_list);
     a.rescue_cap = cp.rescue_cap;
   }
-  cudaError_t e = launch_chunks(ops, cp.prec, cp.config, a, nevt, cp.chunk, cp.grid, cp.block, cp.hsplit, cp.main, wsp, s);
+  cudaError_t e = launch_chunks(ops, cp.prec, cp.config, a, nevt, cp.chunk, cp.grid, cp.block, cp.hsplit, cp.main, wsp,
+                                s, cp.ept);
   if (e != cudaSuccess || !cp.rescue) return e;
   // FP64 pass over the flagged events, in place: same inputs and outputs
   MeLaunch b = a0;
@@ -418,7 +428,7 @@ int me_init(const char* process, const me_sm_params* p, me_handle** out) {
     for (int i = 0; i < ops->ncomb; ++i) a.good[i] = uint8_t(i);
     a.cum = d_cum;  // [ncomb][rows] with rows == nf: one tile per block, one event per thread
     if (int64_t(fgrid) * nd.block != nf) e = cudaErrorInvalidConfiguration;
-    if (e == cudaSuccess) e = launch_chunks(ops, ME_PREC_FP64, 0, a, nf, nf, fgrid, nd.block, 1, cv, d_ws, 0);
+    if (e == cudaSuccess) e = launch_chunks(ops, ME_PREC_FP64, 0, a, nf, nf, fgrid, nd.block, 1, cv, d_ws, 0, 1);
     if (e == cudaSuccess) e = cudaMemcpy(cum.data(), d_cum, cum.size() * sizeof(double), cudaMemcpyDeviceToHost);
   }
   cudaFree(d_mom);
@@ -591,6 +601,24 @@ int me_launch_shape(const me_handle* h, int64_t nevt, int* grid, int* block, int
   if (block) *block = nd.block;
   if (blocks_per_sm) *blocks_per_sm = nd.blocks_per_sm;
   if (nsm) *nsm = h->nsm;
+  return ME_OK;
+}
+
+int me_sync_status(me_handle* h, void* cuda_stream) {
+  if (!h) return fail(nullptr, ME_ERR_ARG, "me_sync_status: null handle");
+  cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(cuda_stream));
+  if (e != cudaSuccess) return cuda_fail(h, e, "me_sync_status");
+  if (h->err_host && *h->err_host) {
+    *h->err_host = 0;
+    return fail(h, ME_ERR_TIMEOUT, "me_sync_status: a device-side wait of a call on this handle timed out; "
+                                   "the main-pass results of that call were set to NaN");
+  }
+  return ME_OK;
+}
+
+int me_set_wait_limit(me_handle* h, int64_t polls) {
+  if (!h) return fail(nullptr, ME_ERR_ARG, "me_set_wait_limit: null handle");
+  h->wait_limit = polls < 0 ? -1 : polls;
   return ME_OK;
 }
 

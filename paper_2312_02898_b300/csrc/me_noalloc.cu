@@ -9,6 +9,7 @@
 // buffer of the large processes, the per-event momentum table, colour weights) lives
 // in one fixed device array declared in this file.  It is created when the library's
 // device code is loaded on a GPU and stays there until the process exits.
+#include <cuda.h>  // CUcontext and the driver call signatures (resolved at run time)
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -33,16 +34,51 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
+// per device: the device address of the scratch and the id of the CUDA context it
+// belongs to.  A device reset (or a primary context torn down and made again) gives the
+// device a new context with a new id, and the address is then looked up again.
 void* g_scratch_addr[kMaxDevices] = {};
+unsigned long long g_scratch_ctx[kMaxDevices] = {};
 
-// Device address of the scratch on the current device, looked up once per device.
+// the unique id of the current CUDA context (0 if there is none or it cannot be read);
+// the two driver calls are resolved through the runtime, so the library does not link
+// the driver library itself
+unsigned long long current_context_id() {
+  using GetCurrent = CUresult (*)(CUcontext*);
+  using GetId = CUresult (*)(CUcontext, unsigned long long*);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static bool resolved = false;
+  if (!resolved) {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<GetCurrent>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<GetId>(f);
+    cudaGetLastError();
+    resolved = true;
+  }
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+    return 0;
+  return id;
+}
+
+// Device address of the scratch on the current device, looked up once per device and
+// context (the argument checks before this have made the device's context current).
 int scratch_address(me_handle* h, void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(h, e, "me_compute_noalloc: cudaGetDevice");
   if (dev < 0 || dev >= kMaxDevices) return fail(h, ME_ERR_ARG, "me_compute_noalloc: device index out of range");
   std::lock_guard<std::mutex> g(g_mu);
-  if (!g_scratch_addr[dev]) {
+  const unsigned long long ctx = current_context_id();
+  if (!g_scratch_addr[dev] || ctx == 0 || ctx != g_scratch_ctx[dev]) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || !p) {
@@ -51,9 +87,26 @@ int scratch_address(me_handle* h, void** out) {
                        "me_compute_noalloc: cudaGetSymbolAddress of the fixed scratch");
     }
     g_scratch_addr[dev] = p;
+    g_scratch_ctx[dev] = current_context_id();
   }
   *out = g_scratch_addr[dev];
   return ME_OK;
+}
+
+// The largest batch whose scratch fits the fixed array (0 if not even one event does).
+// The plan's scratch never shrinks as the batch grows (the main pass grows with
+// min(events, resident threads), the rescue list with the events), so a bisection over
+// the planner, host arithmetic only, finds it.
+int64_t largest_batch(const me_handle* h, bool want_hel, bool want_col) {
+  auto fits = [&](int64_t n) { return plan_call(h, n, n, want_hel, want_col).total <= kScratchBytes; };
+  if (!fits(1)) return 0;
+  int64_t lo = 1, hi = INT32_MAX;  // fits(lo); the answer is in [lo, hi]
+  if (fits(hi)) return hi;
+  while (hi - lo > 1) {
+    const int64_t mid = lo + (hi - lo) / 2;
+    (fits(mid) ? lo : hi) = mid;
+  }
+  return lo;
 }
 
 }  // namespace
@@ -85,14 +138,12 @@ extern "C" int me_compute_noalloc(me_handle* h, int64_t nevt, const double* mome
   // its scratch, one row per resident thread, must fit the fixed array
   const CallPlan cp = plan_call(h, nevt, nevt, want_hel, want_col);
   if (cp.total > kScratchBytes) {
-    const CallPlan one = plan_call(h, 1024, 1024, want_hel, want_col);
-    const double per_event = double(one.total) / 1024.0;
-    char msg[256];
+    char msg[320];
     std::snprintf(msg, sizeof msg,
-                  "me_compute_noalloc: %lld events need %zu bytes of scratch, more than the fixed %zu bytes "
-                  "(about %lld events of this process and mode per call)",
+                  "me_compute_noalloc: %lld events need %zu bytes of scratch, more than the fixed %zu bytes; "
+                  "at most %lld events of this process, mode and choice of selection outputs fit in one call",
                   static_cast<long long>(nevt), cp.total, kScratchBytes,
-                  static_cast<long long>(per_event > 0 ? double(kScratchBytes) / per_event : 0));
+                  static_cast<long long>(largest_batch(h, want_hel, want_col)));
     return fail(h, ME_ERR_ARG, msg);
   }
   void* scratch = nullptr;

@@ -6,6 +6,7 @@
 // The first layout of each precision is the default; the others are alternatives for
 // tuning sweeps (me_set_config / ME_B300_CONFIG).
 #include "generated/proc_ggttg.cuh"
+#include "me_kernel_x2.cuh"
 #include "me_kernels.cuh"
 
 namespace meb300 {
@@ -22,6 +23,11 @@ template <> struct Cfg<1, 1> { using R = float; using L = Layout<0, 128, false, 
 template <> struct Cfg<1, 2> { using R = float; using L = Layout<0, 128, false, false, 0, 0, 1>; };
 template <> struct Cfg<1, 3> { using R = float; using L = Layout<0, 128, 0, 0, 0, 0, 1, 3, 4>; };
 
+// FP32 on packed pairs, two events per thread (me_kernel_x2), everything in registers:
+// correct, a little slower than the scalar kernel here (measured)
+template <int C> struct X2Cfg;
+template <> struct X2Cfg<0> { using L = Layout<0, 128, 0, 0, 0, 0, 1, 3>; };
+
 LaunchNeeds needs(int prec, int config) {
   switch (prec * 8 + config) {
     case 0: return needs_of<P, Cfg<0, 0>::R, Cfg<0, 0>::L>();
@@ -30,6 +36,7 @@ LaunchNeeds needs(int prec, int config) {
     case 9: return needs_of<P, Cfg<1, 1>::R, Cfg<1, 1>::L>();
     case 10: return needs_of<P, Cfg<1, 2>::R, Cfg<1, 2>::L>();
     case 11: return needs_of<P, Cfg<1, 3>::R, Cfg<1, 3>::L>();
+    case 12: return needs_x2_of<P, X2Cfg<0>::L>();
     default: return LaunchNeeds{0, 0, 0, 0, false, 128, 1};
   }
 }
@@ -42,12 +49,13 @@ cudaError_t launch(int prec, int config, const MeLaunch& a, cudaStream_t s) {
     case 9: return launch_me<P, Cfg<1, 1>::R, Cfg<1, 1>::L>(a, s);
     case 10: return launch_me<P, Cfg<1, 2>::R, Cfg<1, 2>::L>(a, s);
     case 11: return launch_me<P, Cfg<1, 3>::R, Cfg<1, 3>::L>(a, s);
+    case 12: return launch_x2<P, X2Cfg<0>::L>(a, s);
     default: return cudaErrorNotSupported;
   }
 }
 }  // namespace
 
 extern const ProcessOps ops_ggttg = {P::NAME, P::NPAR, P::NCOMB, P::NCOL, P::NDIAG, P::NAMP, P::IDEN,
-                                   P::FLOPS_AMP, P::FLOPS_COL, /*has_mixed=*/false, {2, 4, 0},
+                                   P::FLOPS_AMP, P::FLOPS_COL, /*has_mixed=*/false, {2, 5, 0},
                                    needs, launch};
 }  // namespace meb300

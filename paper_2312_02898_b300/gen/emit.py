@@ -290,9 +290,9 @@ class Emitter:
                 elif abs(v + 1) < 1e-12:
                     ops.append(f"J[{c}] -= a;")
                 elif abs(v - 1j) < 1e-12:
-                    ops.append(f"J[{c}] += times_i(a);")
+                    ops.append(f"acc_pi(J[{c}], a);")
                 elif abs(v + 1j) < 1e-12:
-                    ops.append(f"J[{c}] -= times_i(a);")
+                    ops.append(f"acc_mi(J[{c}], a);")
                 else:
                     raise ValueError(f"unexpected colour coefficient {v}")
                 flop("add")
@@ -405,17 +405,25 @@ class Emitter:
 
         cs = []
         csflops = 0
+
+        def fused(terms):
+            # sum of products as a chain of fused multiply-adds: fmadd(a, b, fmadd(c, d, e * f))
+            e = f"{terms[-1][0]} * {terms[-1][1]}"
+            for a_, b_ in reversed(terms[:-1]):
+                e = f"fmadd({a_}, {b_}, {e})"
+            return e
+
         for i in range(ncol):
             tr, ti = [], []
             for j in range(i, ncol):
                 c = int(cf[i, j]) * (1 if j == i else 2)
                 if c == 0:
                     continue
-                tr.append(f"{_lit(c)} * J[{j}].r")
-                ti.append(f"{_lit(c)} * J[{j}].i")
+                tr.append((_lit(c), f"J[{j}].r"))
+                ti.append((_lit(c), f"J[{j}].i"))
                 csflops += 4
-            cs.append(f"  {{ const R tr = {' + '.join(tr)}; const R ti = {' + '.join(ti)};")
-            cs.append(f"    s += J[{i}].r * tr + J[{i}].i * ti; }}")
+            cs.append(f"  {{ const R tr = {fused(tr)}; const R ti = {fused(ti)};")
+            cs.append(f"    s = fmadd(J[{i}].r, tr, fmadd(J[{i}].i, ti, s)); }}")
             csflops += 4
 
         ngden, ntden = max(1, len(gmask_idx)), max(1, len(tmask_idx))
@@ -438,9 +446,9 @@ class Emitter:
                f"CF_FP16_EXACT = {'true' if _exact(cf, 11) else 'false'};  // colour matrix exact in 16-bit",
                "static constexpr bool QCD = true;", "",
                f"static constexpr int NKVEC = {nk};  // momentum vectors in the per-event table",
-               "template <int S, class R, class DG, class DT>",
+               "template <int S, class R, class DG, class DT, class KT>",
                "static HD double precompute(const double (*p)[4], double mt, double wt, int zwt, DG& dg, DT& dt,"
-               " R* kt) {"]
+               " KT kt) {"]
         out += den
         out.append("  return kappa;")
         out.append("}")
@@ -514,8 +522,8 @@ class Emitter:
                f"static constexpr long FLOPS_AMP = {fa}, FLOPS_COL = 4;",
                "static constexpr bool QCD = false;",
                "// Photon and Z in the s channel.  dg[0] = 1/s;  dt[0] = 1/(s - mZ^2 + i mZ wZ).",
-               "template <int S, class R, class DG, class DT>",
-               "static HD double precompute(const double (*p)[4], double mZ, double wZ, int, DG& dg, DT& dt, R* kt) {",
+               "template <int S, class R, class DG, class DT, class KT>",
+               "static HD double precompute(const double (*p)[4], double mZ, double wZ, int, DG& dg, DT& dt, KT kt) {",
                "  for (int i = 0; i < 4; ++i)",
                "    for (int m = 0; m < 4; ++m) kt[i * S + m] = R(p[i][m]);",
                "  double q[4];",

@@ -6,8 +6,9 @@ Section 3) -- are queued on the host and admitted onto the GPU as soon as a stre
 and device memory are free, so work from many requests overlaps on the device.
 
 * Every process keeps one handle (helicity list, couplings, colour matrix resident).
-* A chunk is padded to a size bucket (powers of two from 256 events up to the chunk
-  size) by repeating its last event; events are independent, so padding does not
+* A chunk is padded to a size bucket (powers of two and 1.5 times powers of two, from
+  256 events up to the chunk size, so padding adds at most half) by repeating its last
+  event; events are independent, so padding does not
   change any result, and a request's results are the same alone and in any mix.
 * Each (slot, process, bucket) owns pinned host staging, device buffers and, once used,
   a captured CUDA graph of [copy in -> me_compute -> copy out] that is replayed.
@@ -17,7 +18,9 @@ and device memory are free, so work from many requests overlaps on the device.
   process's flops per event ("srpt"), so that small requests need not wait behind a
   large one.
 * Admission: a chunk starts when a slot is idle and the device bytes of all running
-  chunks plus its own stay within the memory budget.
+  chunks plus its own, on top of the per-stream workspaces the handles hold for the
+  largest chunk, stay within the budget: by default 80% of the device memory that is
+  free once those workspaces exist.
 * Latency is measured from submit() to the moment all of a request's results are on
   the host.
 
@@ -36,11 +39,13 @@ import numpy as np
 
 from .phasespace import make_batch
 
-BUCKETS = tuple(2 ** k for k in range(8, 17))  # 256 .. 65536
+# 256, 384, 512, 768, ..., 49152, 65536: a chunk is padded by at most half of itself
+BUCKETS = tuple(sorted({2 ** k for k in range(8, 17)} | {3 * 2 ** (k - 1) for k in range(8, 16)}))
 
 
 def bucket_for(n: int, buckets=BUCKETS) -> int:
-    """smallest bucket holding n events (n <= largest bucket)"""
+    """smallest bucket holding n events (n <= largest bucket): a power of two or 1.5
+    times one"""
     for b in buckets:
         if n <= b:
             return b
@@ -74,14 +79,19 @@ def pick_next(queue, policy):
 
 
 class MemoryAdmission:
-    """Device-byte budget shared by running requests (host-side accounting)."""
+    """Device-byte budget shared by running requests (host-side accounting).
 
-    def __init__(self, budget_bytes: int):
+    ``reserved`` is what the server holds whatever runs (the handles' per-stream
+    workspaces); a chunk is admitted while reserved + running chunks + itself fit the
+    budget, except that a chunk alone on the device always starts."""
+
+    def __init__(self, budget_bytes: int, reserved: int = 0):
         self.budget = budget_bytes
+        self.reserved = reserved
         self.used = 0
 
     def try_take(self, nbytes: int) -> bool:
-        if self.used + nbytes > self.budget and self.used > 0:
+        if self.reserved + self.used + nbytes > self.budget and self.used > 0:
             return False
         self.used += nbytes
         return True
@@ -137,7 +147,7 @@ class _Buffers:
 
 
 class Server:
-    def __init__(self, processes, precision="mixed", n_slots=4, mem_budget_bytes=8 << 30, use_graphs=True,
+    def __init__(self, processes, precision="mixed", n_slots=4, mem_budget_bytes=None, use_graphs=True,
                  device=0, params=None, policy="srpt", chunk_events=16384):
         if policy not in ("fifo", "srpt"):
             raise ValueError(f"unknown scheduling policy {policy!r}")
@@ -161,15 +171,20 @@ class Server:
                 self.handles[p] = MatrixElement(p, precision="fp32", **(params or {}))
                 self.precision[p] = "fp32"
         self.streams = [torch.cuda.Stream(self.device) for _ in range(n_slots)]
-        # size every (process, stream) workspace for the largest bucket up front, so no
+        # size every (process, stream) workspace for the largest chunk up front, so no
         # later call moves a workspace that a captured graph points into
+        self.workspace_bytes = 0
         for m in self.handles.values():
             for s in self.streams:
-                m.reserve(BUCKETS[-1], s)
+                m.reserve(self.chunk, s)
+                self.workspace_bytes += m.plan(self.chunk)[1]
         torch.cuda.synchronize()
+        free, _ = torch.cuda.mem_get_info(self.device)
+        room = int(0.8 * free) if mem_budget_bytes is None else min(int(mem_budget_bytes), int(0.8 * free))
+        self.mem_budget = self.workspace_bytes + room
         self.slot_busy = [None] * n_slots           # (request, buffers, event, nbytes)
         self.buffers = {}                           # (slot, process, bucket) -> _Buffers
-        self.admission = MemoryAdmission(mem_budget_bytes)
+        self.admission = MemoryAdmission(self.mem_budget, reserved=self.workspace_bytes)
         self.use_graphs = use_graphs
         self.queue = collections.deque()
         self.lock = threading.Lock()
@@ -419,5 +434,9 @@ def run_open_loop(server, reqs, rate_scale=1.0, warmup=0):
     kept = [x for x in server.done if x[4] >= warmup]
     lat = [x[2] * 1e3 for x in kept]
     ev = sum(x[1] for x in kept)
+    per_process = {}
+    for proc in sorted({x[0] for x in kept}):
+        lp = [x[2] * 1e3 for x in kept if x[0] == proc]
+        per_process[proc] = {"requests": len(lp), "p50_ms": percentile(lp, 50), "p99_ms": percentile(lp, 99)}
     return {"requests": len(kept), "events": int(ev), "p50_ms": percentile(lat, 50), "p99_ms": percentile(lat, 99),
-            "mean_ms": float(np.mean(lat)), "me_per_s": ev / (t_last - t_first)}
+            "mean_ms": float(np.mean(lat)), "me_per_s": ev / (t_last - t_first), "per_process": per_process}

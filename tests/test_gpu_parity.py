@@ -357,3 +357,87 @@ def test_persistent_grid_walks_many_tiles_per_block(process, monkeypatch):
                 assert boundary_ok(sh, ref["sel_hel"], ref["me_hel"], rh, 1e-10)[0]
                 assert boundary_ok(sc, ref["sel_col"], ref["colw"], rc, 1e-10)[0]
         m.close()
+
+
+@pytest.mark.skipif(PROCS[2] not in ACTIVE, reason="process not selected")
+def test_rescue_is_lossless_when_every_event_is_flagged():
+    """With a threshold below every event's conditioning, every one of 40000 events is
+    flagged (far more than the max(1024, nevt/16) = 2500 entries the list once held):
+    each is re-evaluated in FP64, so the FP32 handle returns the FP64 handle's matrix
+    elements and helicity selections bit for bit, and colour selections equal up to
+    running-sum boundaries (the rescue pass sums colour weights over helicity lanes)."""
+    p = PROCS[2]
+    n = 40000
+    mom, a, rh, rc = ps.make_batch(p, n, seed=41, alphas="uniform")
+    r64 = run_gpu(mk(p, "fp64"), mom, a, rh, rc)
+    r32 = run_gpu(mk(p, "fp32", rescue_kappa=1e-300), mom, a, rh, rc)
+    assert np.array_equal(r64[0], r32[0])
+    assert np.array_equal(r64[1], r32[1])
+    diff = np.nonzero(r64[2] != r32[2])[0]
+    if diff.size:
+        ref = oracle.me(p, mom[diff], alphas=a[diff], want_colw=True)
+        ok, e = boundary_ok(r32[2][diff], r64[2][diff], ref["colw"], rc[diff], 1e-10)
+        assert ok, e
+
+
+@pytest.mark.skipif(PROCS[3] not in ACTIVE, reason="process not selected")
+def test_rescue_is_lossless_in_the_mixed_mode():
+    p = PROCS[3]
+    n = 3000
+    mom, a, rh, rc = ps.make_batch(p, n, seed=42, alphas="uniform")
+    r64 = run_gpu(mk(p, "fp64"), mom, a, rh, rc)
+    rmx = run_gpu(mk(p, "mixed", rescue_kappa=1e-300), mom, a, rh, rc)
+    assert np.array_equal(r64[0], rmx[0])
+    assert np.array_equal(r64[1], rmx[1])
+
+
+@pytest.mark.skipif(PROCS[3] not in ACTIVE, reason="process not selected")
+def test_mixed_wait_timeout_is_reported_and_the_handle_recovers():
+    """The mixed kernel's bounded wait for its MMAs, driven to give up at once through
+    the testing hook (no fault is involved: the wait simply makes zero polls): every event
+    of the call becomes NaN with selections 0, the kernel keeps its tensor memory until
+    the issued MMAs complete, the host sees ME_ERR_TIMEOUT (from me_sync_status, or from
+    the next me_compute, which then does not compute), and a later call with the default
+    limit returns the oracle's values on the same handle."""
+    from paper_2312_02898_b300.binding import ME_ERR_TIMEOUT, MEError
+    p = PROCS[3]
+    m = mk(p, "mixed", rescue_kappa=0.0)
+    mom, a, rh, rc = ps.make_batch(p, 1000, seed=43, alphas="uniform")
+    dev = to_dev(mom, a, rh, rc)
+    m.set_wait_limit(0)
+    me, sh, sc = m.compute(*dev)
+    with pytest.raises(MEError) as ei:
+        m.sync_status()
+    assert ei.value.code == ME_ERR_TIMEOUT
+    assert torch.isnan(me).all() and (sh == 0).all() and (sc == 0).all()
+    m.sync_status()  # reporting cleared the flag
+    # the same failure reported by the next compute call, which does not run
+    m.compute(*dev)
+    torch.cuda.synchronize()
+    with pytest.raises(MEError) as ei:
+        m.compute(*dev)
+    assert ei.value.code == ME_ERR_TIMEOUT
+    m.set_wait_limit(-1)
+    me, sh, sc = run_gpu(m, mom, a, rh, rc)
+    m.sync_status()
+    ref = oracle.me(p, mom, alphas=a)["me"]
+    assert np.abs(me / ref - 1).max() <= MIXED_BOUND
+
+
+@pytest.mark.skipif(PROCS[1] not in ACTIVE, reason="process not selected")
+def test_binding_rejects_tensors_the_abi_would_misread():
+    m = mk(PROCS[1])
+    mom, a, rh, rc = to_dev(*ps.make_batch(PROCS[1], 64, seed=9, alphas="uniform"))
+    strided = torch.empty((64, 4, 8), dtype=torch.float64, device="cuda")[:, :, :4]
+    strided.copy_(mom)
+    cases = [dict(momenta=mom.float()), dict(momenta=strided), dict(momenta=mom[:, :3]),
+             dict(alphas=a[:63]), dict(alphas=a.float()), dict(rnd_hel=rh.cpu()), dict(rnd_col=rc[::2])]
+    for bad in cases:
+        args = dict(momenta=mom, alphas=a, rnd_hel=rh, rnd_col=rc)
+        args.update(bad)
+        with pytest.raises(ValueError):
+            m.compute(**args)
+    out = (torch.empty(64, dtype=torch.float64, device="cuda"), torch.empty(64, dtype=torch.int64, device="cuda"),
+           torch.empty(64, dtype=torch.int32, device="cuda"))
+    with pytest.raises(ValueError):
+        m.compute(mom, a, rh, rc, out=out)

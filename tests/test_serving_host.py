@@ -9,13 +9,18 @@ import pytest
 from paper_2312_02898_b300 import serving
 
 
-def test_bucket_is_smallest_power_of_two_holding_the_batch():
+def test_bucket_is_smallest_power_of_two_or_one_and_a_half_times_one_holding_the_batch():
     assert serving.bucket_for(1) == 256
     assert serving.bucket_for(256) == 256
-    assert serving.bucket_for(257) == 512
+    assert serving.bucket_for(257) == 384
+    assert serving.bucket_for(385) == 512
+    assert serving.bucket_for(8193) == 12288
     assert serving.bucket_for(65536) == 65536
     with pytest.raises(ValueError):
         serving.bucket_for(65537)
+    # padding never adds more than half of a batch
+    for n in range(256, 65537, 97):
+        assert serving.bucket_for(n) <= 1.5 * n
 
 
 def test_padding_repeats_the_last_event_and_keeps_the_rest():
@@ -47,6 +52,11 @@ def test_admission_blocks_beyond_budget_but_never_starves_an_empty_device():
     assert a.try_take(500)          # alone on the device a request always starts
     assert not a.try_take(1)
     a.give(500)
+    # the reserved workspaces count against the budget
+    r = serving.MemoryAdmission(100, reserved=70)
+    assert r.try_take(20)
+    assert not r.try_take(20)
+    assert r.try_take(10) and r.used == 30
 
 
 def test_request_stream_follows_weights_sizes_and_poisson_arrivals():

@@ -69,3 +69,11 @@ def test_noalloc_rejects_batches_beyond_the_fixed_scratch():
     assert rc_ == -1
     msg = m.lib.me_last_error(m.handle).decode()
     assert "fixed" in msg and "scratch" in msg and "33554432" in msg
+    # the limit it states is exact: that many events are accepted, one more is not
+    limit = int(msg.split("at most ")[1].split()[0])
+    assert 0 < limit < nevt
+    for n, want in ((limit, 0), (limit + 1, -1)):
+        rc_ = f(m.handle, n, mom.data_ptr(), a.data_ptr(), rh.data_ptr(), rc.data_ptr(), me.data_ptr(),
+                sh.data_ptr(), sc.data_ptr(), None)
+        assert rc_ == want, (n, m.lib.me_last_error(m.handle))
+    torch.cuda.synchronize()
