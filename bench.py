@@ -41,8 +41,8 @@ PROCESS = "g g > t t~ g g"
 NEVT = 1048576
 METRIC = "ME evals/s per process, FP64 vs mixed at stated rel. err; serving p50/p99 ms"
 UNIT = "ME evals/s"
-FLOP_DTYPE = {"fp64": "f64", "fp32": "f32", "mixed": "f32+bf16"}
-ERR_BOUND = {"fp64": 1e-12, "fp32": 1e-5, "mixed": 1e-5}
+FLOP_DTYPE = {"fp64": "f64", "fp32": "f32", "mixed": "f32+bf16", "dfloat": "f32 pairs (double-float)"}
+ERR_BOUND = {"fp64": 1e-12, "fp32": 1e-5, "mixed": 1e-5, "dfloat": 1e-10}
 # DRAM bytes per event of each mode's default main-pass kernel of g g > t t~ g g, from
 # one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of a 655360-event launch;
 # the traffic grows with the events processed.  Keyed by the kernel's layout, so a
@@ -328,7 +328,8 @@ def process_row(process, nevt, alphas, modes, peaks, steps, err_n, budget_s=10.0
         r = time_mode(mode, dev, host, k, 2 if probe["ms"] < 1000 else 0, None, process=process, e2e=False)
         mx, med, ns = accuracy_sample(r["me"], host, n=err_n, process=process)
         tf = r["flops_per_event"] * nevt / (r["ms"] * 1e-3) / 1e12
-        pk = peaks["fp64" if mode == "fp64" else "fp32"] / 1e12
+        # the double-float mode is rated against the FP64 peak it emulates
+        pk = peaks["fp64" if mode in ("fp64", "dfloat") else "fp32"] / 1e12
         row[mode] = {"me_per_s": nevt / (r["ms"] * 1e-3), "ms_per_step": r["ms"], "steps": k, "tflops": tf,
                      "frac_of_measured_peak": tf / pk, "launches_per_step": r["launches"], "max_rel_err": mx,
                      "median_rel_err": med, "err_sample": ns, "bound": ERR_BOUND[mode], "clocks": r["clocks"]}
@@ -423,6 +424,7 @@ def run_gpu(args):
             # the rest of the metric: every process at its own workload size, and the
             # serving stream in mixed precision beside the same stream in FP64
             line["processes"] = processes_table(args, peaks, reuse={PROCESS: (results, acc)})
+            line["dispatch"] = dispatch_table(args)
             line["serving"] = serving_table(args, quick=True)
         print(json.dumps(line), flush=True)
     if dist:
@@ -433,6 +435,60 @@ def run_gpu(args):
 # the per-process workloads: (process, events, alpha_s)
 PROCESS_TABLE = (("e+ e- > mu+ mu-", 16384, None), ("g g > t t~", 524288, 0.118), ("g g > t t~ g", 524288, 0.118),
                  ("g g > t t~ g g", 1048576, "uniform"), ("g g > t t~ g g g", 262144, 0.118))
+
+
+DISPATCH_CHANNELS = (("g g > t t~", 0.90), ("u u~ > t t~", 0.05), ("u~ u > t t~", 0.05))
+
+
+def dispatch_table(args, nevt=524288):
+    """p p -> t t~ with per-event channel dispatch (me_compute_channels): one batch of
+    2 -> 2 RAMBO events (massless beams, massive tops: valid for every channel), each
+    event assigned a channel with the fractions of DISPATCH_CHANNELS (synthetic, close to
+    the g g / q q~ shares of top-pair production at the LHC); ME/s of the mixed batch
+    beside the g g channel alone, and the error of each channel against its oracle."""
+    import torch
+    import oracle
+    from paper_2312_02898_b300 import phasespace as ps
+    from paper_2312_02898_b300.binding import MatrixElement, compute_channels
+    mom, a, rh, rc = (torch.from_numpy(x).cuda() for x in
+                      ps.make_batch(DISPATCH_CHANNELS[0][0], nevt, seed=0, alphas="uniform"))
+    rng = np.random.default_rng(0)
+    ch_np = rng.choice(len(DISPATCH_CHANNELS), size=nevt, p=[f for _, f in DISPATCH_CHANNELS]).astype(np.int32)
+    ch = torch.from_numpy(ch_np).cuda()
+    out = {"events": nevt, "channels": {p: float(f) for p, f in DISPATCH_CHANNELS}}
+    for prec in ("fp64", "fp32"):
+        hs = [MatrixElement(p, precision=prec) for p, _ in DISPATCH_CHANNELS]
+        res = (torch.empty(nevt, dtype=torch.float64, device="cuda"), torch.empty(nevt, dtype=torch.int32, device="cuda"),
+               torch.empty(nevt, dtype=torch.int32, device="cuda"))
+
+        def timed(fn, steps):
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(steps):
+                fn()
+            e1.record()
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / steps
+
+        ms = timed(lambda: compute_channels(hs, ch, mom, a, rh, rc, out=res), args.steps)
+        ms_gg = timed(lambda: hs[0].compute(mom, a, rh, rc, out=res), args.steps)
+        compute_channels(hs, ch, mom, a, rh, rc, out=res)
+        torch.cuda.synchronize()
+        got = res[0].cpu().numpy()
+        errs = {}
+        for c, (p, _) in enumerate(DISPATCH_CHANNELS):
+            idx = np.nonzero(ch_np == c)[0][:512]
+            ref = oracle.me(p, mom[idx].cpu().numpy(), alphas=a[idx].cpu().numpy())["me"]
+            errs[p] = float(np.max(np.abs(got[idx] / ref - 1)))
+        out[prec] = {"me_per_s": nevt / (ms * 1e-3), "ms_per_step": ms, "gg_alone_me_per_s": nevt / (ms_gg * 1e-3),
+                     "max_rel_err_per_channel": errs, "err_sample_per_channel": 512,
+                     "launches_per_step": 2 + sum(h.plan(nevt)[0] for h in hs)}
+        for h in hs:
+            h.close()
+    return out
 
 
 def processes_table(args, peaks, reuse=None):
@@ -596,7 +652,7 @@ def main():
     ap.add_argument("--processes", action="store_true", help="per-process ME/s table instead of the step")
     ap.add_argument("--only-process", default="", help="with --processes: only this process")
     ap.add_argument("--process-nevt", type=int, default=0, help="with --processes: events instead of the workload's")
-    ap.add_argument("--process-modes", default="fp64,fp32,mixed", help="with --processes: precisions to time")
+    ap.add_argument("--process-modes", default="fp64,fp32,mixed,dfloat", help="with --processes: precisions to time")
     ap.add_argument("--process-err-sample", type=int, default=256,
                     help="oracle events per process and mode for the error of the per-process table")
     ap.add_argument("--err-sample", type=int, default=4096,

@@ -20,6 +20,8 @@
  *   "g g > t t~ g"         16 diagrams,             32 helicities,   6
  *   "g g > t t~ g g"       123 diagrams,            64 helicities,  24
  *   "g g > t t~ g g g"     1240 diagrams,          128 helicities, 120
+ *   "u u~ > t t~"          1 diagram,               16 helicities,   2 (a light quark
+ *   "u~ u > t t~"          from either beam: the quark-initiated channel of p p -> t t~)
  *
  * Conventions:
  *   momenta   (E, px, py, pz) in GeV, FP64, array-of-structures [nevt][npar][4];
@@ -68,6 +70,11 @@ extern "C" {
 #define ME_PREC_FP32 1   /* FP32 amplitudes and colour sum; FP64 inputs, denominators, helicity sum */
 #define ME_PREC_MIXED 2  /* FP32 amplitudes, colour sum on tensor cores (split BF16/FP16 operands,
                             FP32 accumulation); FP64 inputs, denominators, helicity sum */
+#define ME_PREC_DFLOAT 3 /* FP64-emulating amplitudes and colour sum in double-float arithmetic
+                            (hi + lo FP32 pairs, about 48 significant bits, FP32 exponent range)
+                            on the FP32 pipe; FP64 inputs, error-free invariants and helicity sum
+                            as in FP64 mode.  Built for "g g > t t~" and "g g > t t~ g";
+                            ME_ERR_MODE elsewhere */
 
 typedef struct me_handle me_handle;
 
@@ -79,7 +86,7 @@ typedef struct {
   double aEWM1;             /* 1/alpha_EM */
   double Gf;                /* Fermi constant [GeV^-2] */
   double alphas_default;    /* alpha_s when me_compute gets alphas == NULL */
-  int precision;            /* ME_PREC_* */
+  int precision;            /* ME_PREC_* (ME_ERR_MODE from me_init where a mode is not built) */
   int zero_width_tchan;     /* 1: no width in t-channel propagators (those that separate
                                the two incoming particles); Section 3, Tables 1-2 */
   double rescue_kappa;      /* FP32 and mixed modes: an event whose conditioning
@@ -149,6 +156,27 @@ int me_compute_host(me_handle* h, int64_t nevt, const double* momenta, const dou
 int me_compute_noalloc(me_handle* h, int64_t nevt, const double* momenta, const double* alphas,
                        const double* rnd_hel, const double* rnd_col, double* me, int32_t* sel_hel,
                        int32_t* sel_col, void* cuda_stream);
+
+/* Per-event subprocess dispatch.  A hadronic process is a sum of channels (for
+ * p p -> t t~: g g -> t t~, u u~ -> t t~ and u~ u -> t t~, each light flavour having the
+ * same matrix element), and an event generator produces the events of all channels in one
+ * batch; the paper's outlook (Section 5) names this multi-subprocess case.  Event e of
+ * the batch belongs to channel channel[e] and is evaluated by handle hs[channel[e]]:
+ *   hs       host array of nchan (1 to 16) handles, all with the same number of
+ *            particles, each in FP64 or FP32 (ME_ERR_MODE otherwise)
+ *   channel  device, int32 [nevt]; an index outside [0, nchan) gives that event NaN in
+ *            me and selections 0
+ * and the other arguments as in me_compute (momenta in the particle order of the event's
+ * channel).  Each event's results are those of me_compute with its channel's handle.
+ * The partition by channel happens on the device; the call does not wait for it.  At
+ * most 2^30 events per call.  Uses the first handle's workspace on cuda_stream for the
+ * partition and each handle's own workspace for its channel.
+ * Errors: ME_ERR_ARG (null or mismatched handles, nevt < 0, host pointers, misaligned
+ * momenta), ME_ERR_MODE, ME_ERR_NOMEM, ME_ERR_CUDA, ME_ERR_TIMEOUT; messages on hs[0]. */
+int me_compute_channels(me_handle* const* hs, int nchan, int64_t nevt, const int32_t* channel,
+                        const double* momenta, const double* alphas, const double* rnd_hel,
+                        const double* rnd_col, double* me, int32_t* sel_hel, int32_t* sel_col,
+                        void* cuda_stream);
 
 /* GPU-assisted batch unweighting (Section 3, Table 2): with the whole batch's largest
  * weight known before any decision, hit-or-miss needs no provisional storage.

@@ -37,6 +37,8 @@ PROCESSES = (
     "g g > t t~ g",
     "g g > t t~ g g",
     "g g > t t~ g g g",
+    "u u~ > t t~",
+    "u~ u > t t~",
 )
 
 

@@ -25,7 +25,11 @@
  *     the Fierz identity sum_a T^a_ij T^a_kl = (d_il d_kj - d_ij d_kl / N)/2.
  *
  * For e+ e- -> mu+ mu- the two s-channel diagrams (photon, Z) are written out with
- * explicit 4x4 gamma matrices.
+ * explicit 4x4 gamma matrices.  For q qbar -> t tbar (a light quark of either beam; the
+ * quark-initiated channel of p p -> t tbar) the one s-channel gluon diagram is written
+ * out with explicit colour indices and explicit Gell-Mann matrices T^a = lambda^a / 2:
+ * |M|^2 is summed over all 81 colour assignments, and the colour-flow amplitudes are the
+ * coefficients of the amplitude on the two flow tensors (a 2 x 2 Gram system).
  *
  * Conventions shared with the product only through their published definitions:
  *   * momenta [nevt][npar][4] = (E, px, py, pz); particle order of the process string;
@@ -47,7 +51,7 @@
 
 typedef double complex cx;
 
-#define NPROC 5
+#define NPROC 7
 #define MAXPAR 7
 #define MAXG 5
 #define MAXCOL 120
@@ -58,23 +62,30 @@ typedef struct {
 } oracle_params;
 
 /* roles of external particles */
-enum { R_EBAR_IN, R_E_IN, R_MUBAR_OUT, R_MU_OUT, R_G_IN, R_G_OUT, R_T_OUT, R_TBAR_OUT };
+enum { R_EBAR_IN, R_E_IN, R_MUBAR_OUT, R_MU_OUT, R_G_IN, R_G_OUT, R_T_OUT, R_TBAR_OUT, R_Q_IN, R_QB_IN };
 
+/* kind: 0 e+ e- -> mu+ mu-; 1 g g -> t tbar + gluons (Berends-Giele); 2 q qbar -> t tbar
+ * (explicit colour) */
 typedef struct {
   const char* name;
   int npar;
   int ngluon;
   int iden;
   int role[MAXPAR];
+  int kind;
+  int ncol;
 } proc_def;
 
 static const proc_def PROCS[NPROC] = {
-    {"e+ e- > mu+ mu-", 4, 0, 4, {R_EBAR_IN, R_E_IN, R_MUBAR_OUT, R_MU_OUT}},
-    {"g g > t t~", 4, 2, 256, {R_G_IN, R_G_IN, R_T_OUT, R_TBAR_OUT}},
-    {"g g > t t~ g", 5, 3, 256, {R_G_IN, R_G_IN, R_T_OUT, R_TBAR_OUT, R_G_OUT}},
-    {"g g > t t~ g g", 6, 4, 512, {R_G_IN, R_G_IN, R_T_OUT, R_TBAR_OUT, R_G_OUT, R_G_OUT}},
+    {"e+ e- > mu+ mu-", 4, 0, 4, {R_EBAR_IN, R_E_IN, R_MUBAR_OUT, R_MU_OUT}, 0, 1},
+    {"g g > t t~", 4, 2, 256, {R_G_IN, R_G_IN, R_T_OUT, R_TBAR_OUT}, 1, 2},
+    {"g g > t t~ g", 5, 3, 256, {R_G_IN, R_G_IN, R_T_OUT, R_TBAR_OUT, R_G_OUT}, 1, 6},
+    {"g g > t t~ g g", 6, 4, 512, {R_G_IN, R_G_IN, R_T_OUT, R_TBAR_OUT, R_G_OUT, R_G_OUT}, 1, 24},
     {"g g > t t~ g g g", 7, 5, 1536,
-     {R_G_IN, R_G_IN, R_T_OUT, R_TBAR_OUT, R_G_OUT, R_G_OUT, R_G_OUT}},
+     {R_G_IN, R_G_IN, R_T_OUT, R_TBAR_OUT, R_G_OUT, R_G_OUT, R_G_OUT}, 1, 120},
+    /* IDEN = 4 initial spin states x 9 initial colour states */
+    {"u u~ > t t~", 4, 0, 36, {R_Q_IN, R_QB_IN, R_T_OUT, R_TBAR_OUT}, 2, 2},
+    {"u~ u > t t~", 4, 0, 36, {R_QB_IN, R_Q_IN, R_T_OUT, R_TBAR_OUT}, 2, 2},
 };
 
 static int factorial(int n) { return n <= 1 ? 1 : n * factorial(n - 1); }
@@ -91,7 +102,7 @@ int oracle_info(int proc, int* npar, int* ncomb, int* ncol, int* iden) {
   if (proc < 0 || proc >= NPROC) return -1;
   *npar = PROCS[proc].npar;
   *ncomb = 1 << PROCS[proc].npar;
-  *ncol = PROCS[proc].ngluon ? factorial(PROCS[proc].ngluon) : 1;
+  *ncol = PROCS[proc].ncol;
   *iden = PROCS[proc].iden;
   return 0;
 }
@@ -207,8 +218,24 @@ static void perm_unrank(int n, int r, int* out) {
 }
 
 /* C_{st} = Tr(T^{s_1}...T^{s_n} T^{t_n}...T^{t_1}) as num[ncol*ncol] / den[ncol*ncol]. */
+static double qq_flow_tensor(int n, int i, int j, int k, int l);
+
 int oracle_colour_matrix_exact(int proc, int64_t* num, int64_t* den) {
   if (proc < 0 || proc >= NPROC) return -1;
+  if (PROCS[proc].kind == 2) {
+    /* C_nm = sum over all colour indices of c_n c_m (the flow tensors are real, 0 or 1) */
+    for (int n = 0; n < 2; ++n)
+      for (int m = 0; m < 2; ++m) {
+        int64_t c = 0;
+        for (int i = 0; i < NC; ++i)
+          for (int j = 0; j < NC; ++j)
+            for (int k = 0; k < NC; ++k)
+              for (int l = 0; l < NC; ++l) c += (int64_t)(qq_flow_tensor(n, i, j, k, l) * qq_flow_tensor(m, i, j, k, l));
+        num[n * 2 + m] = c;
+        den[n * 2 + m] = 1;
+      }
+    return 0;
+  }
   int n = PROCS[proc].ngluon;
   if (n == 0) { num[0] = 1; den[0] = 1; return 0; }
   int ncol = factorial(n);
@@ -588,6 +615,83 @@ static cx amp_ordered(const qcd_ext* x, const invariants* inv, int n, const int*
 }
 
 /* ------------------------------------------------------------------------- */
+/* q qbar -> t tbar : one s-channel gluon, explicit colour                    */
+/* ------------------------------------------------------------------------- */
+static cx TGM[8][NC][NC]; /* T^a = lambda^a / 2 (Gell-Mann) */
+static int tgm_ready = 0;
+
+static void tgm_init(void) {
+  if (tgm_ready) return;
+  memset(TGM, 0, sizeof TGM);
+  TGM[0][0][1] = TGM[0][1][0] = 0.5;
+  TGM[1][0][1] = -0.5 * I; TGM[1][1][0] = 0.5 * I;
+  TGM[2][0][0] = 0.5; TGM[2][1][1] = -0.5;
+  TGM[3][0][2] = TGM[3][2][0] = 0.5;
+  TGM[4][0][2] = -0.5 * I; TGM[4][2][0] = 0.5 * I;
+  TGM[5][1][2] = TGM[5][2][1] = 0.5;
+  TGM[6][1][2] = -0.5 * I; TGM[6][2][1] = 0.5 * I;
+  TGM[7][0][0] = TGM[7][1][1] = 0.5 / sqrt(3.0); TGM[7][2][2] = -1.0 / sqrt(3.0);
+  tgm_ready = 1;
+}
+
+/* flow tensors of q(i) qbar(j) -> t(k) tbar(l): c_0 = d_ki d_jl (the top takes the
+ * quark's colour, the antitop the antiquark's), c_1 = d_ji d_kl */
+static double qq_flow_tensor(int n, int i, int j, int k, int l) {
+  return n == 0 ? (double)(k == i && j == l) : (double)(j == i && k == l);
+}
+
+/* colour-stripped amplitude A with M(i,j,k,l) = A sum_a T^a_{ji} T^a_{kl}:
+ *   [vbar(p_qb) (-i gs gamma^mu T^a) u(p_q)] (-i g_{mu nu} / s) [ubar(p_t) (-i gs gamma^nu T^a) v(p_tb)] */
+static cx amp_qqbar_tt(const double* mom, const int* lam, const proc_def* pd, double gs, double mt) {
+  int iq = -1, iqb = -1, it = -1, itb = -1;
+  for (int i = 0; i < pd->npar; ++i) {
+    if (pd->role[i] == R_Q_IN) iq = i;
+    if (pd->role[i] == R_QB_IN) iqb = i;
+    if (pd->role[i] == R_T_OUT) it = i;
+    if (pd->role[i] == R_TBAR_OUT) itb = i;
+  }
+  cx u[4], v[4], vb[4], ut[4], ubt[4], vt[4], lq[4], lt[4];
+  spinor_u(mom + 4 * iq, 0.0, lam[iq], u);
+  spinor_v(mom + 4 * iqb, 0.0, lam[iqb], v);
+  dirac_bar(v, vb);
+  spinor_u(mom + 4 * it, mt, lam[it], ut);
+  dirac_bar(ut, ubt);
+  spinor_v(mom + 4 * itb, mt, lam[itb], vt);
+  vector_current(vb, u, 1.0, 1.0, lq);
+  vector_current(ubt, vt, 1.0, 1.0, lt);
+  double P[4];
+  for (int m = 0; m < 4; ++m) P[m] = mom[4 * iq + m] + mom[4 * iqb + m];
+  double s = mdot_r(P, P);
+  return (-I * gs) * (-I * gs) * (-I / s) * mdot_c(lq, lt);
+}
+
+/* explicit colour sum of |M|^2 and the flow amplitudes J (M = sum_n J_n c_n): the
+ * projections P_n = sum c_n M over all indices, then J = G^{-1} P with the Gram matrix
+ * G_nm = sum c_n c_m */
+static double qq_colour_sum(cx A, cx* J) {
+  double m2 = 0;
+  cx P[2] = {0, 0};
+  double G[2][2] = {{0, 0}, {0, 0}};
+  for (int i = 0; i < NC; ++i)
+    for (int j = 0; j < NC; ++j)
+      for (int k = 0; k < NC; ++k)
+        for (int l = 0; l < NC; ++l) {
+          cx col = 0;
+          for (int a = 0; a < 8; ++a) col += TGM[a][j][i] * TGM[a][k][l];
+          cx M = A * col;
+          m2 += creal(M) * creal(M) + cimag(M) * cimag(M);
+          for (int n = 0; n < 2; ++n) {
+            P[n] += qq_flow_tensor(n, i, j, k, l) * M;
+            for (int m = 0; m < 2; ++m) G[n][m] += qq_flow_tensor(n, i, j, k, l) * qq_flow_tensor(m, i, j, k, l);
+          }
+        }
+  double det = G[0][0] * G[1][1] - G[0][1] * G[1][0];
+  J[0] = (G[1][1] * P[0] - G[0][1] * P[1]) / det;
+  J[1] = (G[0][0] * P[1] - G[1][0] * P[0]) / det;
+  return m2;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Driver                                                                     */
 /* ------------------------------------------------------------------------- */
 static int select_first_exceeding(const double* w, int n, double r) {
@@ -622,9 +726,10 @@ int oracle_me(int proc, const oracle_params* par, int64_t nevt, const double* mo
               double* colw, int32_t* sel_hel, int32_t* sel_col, int gauge_leg) {
   if (proc < 0 || proc >= NPROC || nevt < 0 || !par || (nevt > 0 && (!mom || !me))) return -1;
   gamma_init();
+  tgm_init();
   const proc_def* pd = &PROCS[proc];
   int npar = pd->npar, ncomb = 1 << npar, n = pd->ngluon;
-  int ncol = n ? factorial(n) : 1;
+  int ncol = pd->ncol;
   sm_derived sm;
   sm_derive(par, &sm);
   double* Cm = (double*)malloc(sizeof(double) * ncol * ncol);
@@ -635,7 +740,7 @@ int oracle_me(int proc, const oracle_params* par, int64_t nevt, const double* mo
   free(cn);
   free(cd);
   int perms[MAXCOL][MAXG];
-  for (int s = 0; s < ncol && n; ++s) perm_unrank(n, s, perms[s]);
+  for (int s = 0; s < ncol && n && pd->kind == 1; ++s) perm_unrank(n, s, perms[s]);
 
 #pragma omp parallel for schedule(dynamic, 4)
   for (int64_t e = 0; e < nevt; ++e) {
@@ -647,13 +752,18 @@ int oracle_me(int proc, const oracle_params* par, int64_t nevt, const double* mo
     double as = alphas ? alphas[e] : par->alphas;
     double gs = sqrt(4.0 * M_PI * as);
     invariants inv;
-    if (proc != 0) event_invariants(pd, p, par->mt, &inv);
+    if (pd->kind == 1) event_invariants(pd, p, par->mt, &inv);
     for (int h = 0; h < ncomb; ++h) {
       int lam[MAXPAR];
       for (int i = 0; i < npar; ++i) lam[i] = ((h >> (npar - 1 - i)) & 1) ? 1 : -1;
       cx A[MAXCOL];
-      if (proc == 0) {
+      double m2 = 0;
+      int explicit_colour = 0;
+      if (pd->kind == 0) {
         A[0] = amp_eemumu(p, lam, par, &sm);
+      } else if (pd->kind == 2) {
+        m2 = qq_colour_sum(amp_qqbar_tt(p, lam, pd, gs, par->mt), A);
+        explicit_colour = 1;
       } else {
         qcd_ext x;
         int g = 0;
@@ -684,9 +794,9 @@ int oracle_me(int proc, const oracle_params* par, int64_t nevt, const double* mo
         for (int s = 0; s < ncol; ++s)
           A[s] = amp_ordered(&x, &inv, n, perms[s], gs, par->mt, par->wt, par->zero_width_tchan);
       }
-      double m2 = 0;
-      for (int s = 0; s < ncol; ++s)
-        for (int t = 0; t < ncol; ++t) m2 += Cm[s * ncol + t] * creal(conj(A[s]) * A[t]);
+      if (!explicit_colour)
+        for (int s = 0; s < ncol; ++s)
+          for (int t = 0; t < ncol; ++t) m2 += Cm[s * ncol + t] * creal(conj(A[s]) * A[t]);
       mh[h] = m2;
       total += m2;
       for (int s = 0; s < ncol; ++s) w[s] += creal(A[s]) * creal(A[s]) + cimag(A[s]) * cimag(A[s]);
@@ -718,7 +828,7 @@ int oracle_me(int proc, const oracle_params* par, int64_t nevt, const double* mo
  */
 int oracle_invariants(int proc, const oracle_params* par, int64_t nevt, const double* mom, double* gsq,
                       double* tden) {
-  if (proc <= 0 || proc >= NPROC || nevt < 0 || !par || (nevt > 0 && (!mom || !gsq || !tden))) return -1;
+  if (proc <= 0 || proc >= NPROC || PROCS[proc].kind != 1 || nevt < 0 || !par || (nevt > 0 && (!mom || !gsq || !tden))) return -1;
   const proc_def* pd = &PROCS[proc];
   int ncomb = 1 << pd->npar;
   for (int64_t e = 0; e < nevt; ++e) {

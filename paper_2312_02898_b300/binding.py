@@ -13,13 +13,13 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libme_b300.so")
 
 ME_OK, ME_ERR_ARG, ME_ERR_MODE, ME_ERR_NOMEM, ME_ERR_CUDA, ME_ERR_TIMEOUT = 0, -1, -2, -3, -4, -5
-PRECISIONS = {"fp64": 0, "fp32": 1, "mixed": 2}
+PRECISIONS = {"fp64": 0, "fp32": 1, "mixed": 2, "dfloat": 3}
 
 # the C-ABI entry points declared in include/me.h
 EXPORTS = ("me_default_params", "me_init", "me_compute", "me_compute_host", "me_info", "me_good_helicities",
            "me_flops", "me_plan", "me_reserve", "me_launch_shape", "me_set_config", "me_last_error", "me_free",
            "me_compute_noalloc", "me_unweight", "me_rambo", "me_uniforms", "me_probe_alu_peak", "me_sync_status",
-           "me_set_wait_limit")
+           "me_set_wait_limit", "me_compute_channels")
 
 
 class SMParams(ctypes.Structure):
@@ -65,6 +65,7 @@ def load(path: str = LIB_PATH):
     lib.me_flops.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
     lib.me_set_config.argtypes = [vp, ctypes.c_int]
     lib.me_sync_status.argtypes = [vp, vp]
+    lib.me_compute_channels.argtypes = [ctypes.POINTER(vp), ctypes.c_int, i64] + [vp] * 9
     lib.me_set_wait_limit.argtypes = [vp, i64]
     lib.me_plan.argtypes = [vp, i64, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
     lib.me_probe_alu_peak.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
@@ -74,7 +75,8 @@ def load(path: str = LIB_PATH):
     lib.me_free.restype = None
     for f in ("me_init", "me_compute", "me_compute_host", "me_compute_noalloc", "me_info", "me_good_helicities",
               "me_flops", "me_set_config", "me_plan", "me_reserve", "me_launch_shape", "me_unweight",
-              "me_rambo", "me_uniforms", "me_probe_alu_peak", "me_sync_status", "me_set_wait_limit"):
+              "me_rambo", "me_uniforms", "me_probe_alu_peak", "me_sync_status", "me_set_wait_limit",
+              "me_compute_channels"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -130,6 +132,34 @@ def device_uniforms(nevt, seed, first_event, stream_id, offset=0.0, scale=1.0, s
     if rc != ME_OK:
         raise MEError(rc, load().me_last_error(None).decode())
     return out
+
+
+def compute_channels(handles, channel, momenta, alphas=None, rnd_hel=None, rnd_col=None, out=None, stream=None):
+    """Per-event subprocess dispatch (me_compute_channels): event e is evaluated by
+    handles[channel[e]] (MatrixElement objects with the same number of particles, FP64 or
+    FP32).  Device tensors in and out, asynchronous on ``stream``."""
+    import torch
+    if not handles:
+        raise ValueError("at least one channel handle is required")
+    h0 = handles[0]
+    if not momenta.is_cuda:
+        raise ValueError("momenta must be a CUDA tensor")
+    nevt = momenta.shape[0]
+    dev = momenta.device
+    _check_tensor("channel", channel, torch.int32, (nevt,), dev, required=True)
+    if out is None:
+        me = torch.empty(nevt, dtype=torch.float64, device=dev)
+        sh = torch.empty(nevt, dtype=torch.int32, device=dev) if rnd_hel is not None else None
+        sc = torch.empty(nevt, dtype=torch.int32, device=dev) if rnd_col is not None else None
+    else:
+        me, sh, sc = out
+    h0._check_args(momenta, alphas, rnd_hel, rnd_col, (me, sh, sc), dev)
+    arr = (ctypes.c_void_p * len(handles))(*[h.handle.value for h in handles])
+    s = stream if stream is not None else torch.cuda.current_stream(dev)
+    h0._check(h0.lib.me_compute_channels(arr, len(handles), nevt, _ptr(channel), _ptr(momenta), _ptr(alphas),
+                                         _ptr(rnd_hel), _ptr(rnd_col), _ptr(me), _ptr(sh), _ptr(sc),
+                                         ctypes.c_void_p(s.cuda_stream)))
+    return me, sh, sc
 
 
 class MatrixElement:

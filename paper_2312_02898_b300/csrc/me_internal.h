@@ -66,6 +66,8 @@ int fail(me_handle* h, int code, const std::string& msg);
 int cuda_fail(me_handle* h, cudaError_t e, const char* where);
 void fill_common(const me_handle* h, MeLaunch& a);
 bool is_device_ptr(const void* p);
+// stream-ordered workspace of the handle under key, grown to at least bytes
+int get_workspace(me_handle* h, uintptr_t key, cudaStream_t s, size_t bytes, void** out);
 Carve carve(const ProcessOps* ops, const LaunchNeeds& nd, int ngood, int64_t rows, bool want_hel, bool want_col);
 int persistent_grid(const me_handle* h, const LaunchNeeds& nd, int64_t nevt);
 std::vector<double> final_masses(const ProcessOps* ops, double mt);

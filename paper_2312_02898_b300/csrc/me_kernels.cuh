@@ -474,7 +474,8 @@ struct ProcessOps {
   int npar, ncomb, ncol, ndiag, namp, iden;
   long flops_amp, flops_col;
   bool has_mixed;
-  int nconfig[3];  // launch configurations available per precision (index 0 is the default)
+  int nconfig[4];  // launch configurations available per precision (index 0 is the default;
+                   // 0 configurations: the precision is not built for this process)
   LaunchNeeds (*needs)(int prec, int config);
   cudaError_t (*launch)(int prec, int config, const MeLaunch& a, cudaStream_t s);
 };

@@ -29,12 +29,14 @@ extern const ProcessOps ops_ggtt __attribute__((weak));
 extern const ProcessOps ops_ggttg __attribute__((weak));
 extern const ProcessOps ops_ggttgg __attribute__((weak));
 extern const ProcessOps ops_ggttggg __attribute__((weak));
+extern const ProcessOps ops_qqtt __attribute__((weak));
+extern const ProcessOps ops_qxqtt __attribute__((weak));
 }
 using namespace meb300;
 
 namespace {
 
-const ProcessOps* const kProcs[] = {&ops_eemumu, &ops_ggtt, &ops_ggttg, &ops_ggttgg, &ops_ggttggg};
+const ProcessOps* const kProcs[] = {&ops_eemumu, &ops_ggtt, &ops_ggttg, &ops_ggttgg, &ops_ggttggg, &ops_qqtt, &ops_qxqtt};
 
 thread_local std::string g_init_error;
 
@@ -364,9 +366,11 @@ int me_init(const char* process, const me_sm_params* p, me_handle** out) {
   if (!(p->mZ > 0 && p->wZ >= 0 && p->mt > 0 && p->wt >= 0 && p->aEWM1 > 0 && p->Gf > 0 && p->alphas_default > 0 &&
         p->rescue_kappa >= 0))
     return fail(nullptr, ME_ERR_ARG, "me_init: parameters must be positive (widths non-negative)");
-  if (p->precision < 0 || p->precision > 2) return fail(nullptr, ME_ERR_ARG, "me_init: unknown precision mode");
+  if (p->precision < 0 || p->precision > 3) return fail(nullptr, ME_ERR_ARG, "me_init: unknown precision mode");
   if (p->precision == ME_PREC_MIXED && !ops->has_mixed)
     return fail(nullptr, ME_ERR_MODE, "me_init: mixed precision is not available for this process");
+  if (ops->nconfig[p->precision] <= 0)
+    return fail(nullptr, ME_ERR_MODE, "me_init: this precision mode is not built for this process");
   const double alpha = 1.0 / p->aEWM1;
   const double mz2 = p->mZ * p->mZ;
   const double disc = mz2 * mz2 / 4.0 - M_PI * alpha * mz2 / (std::sqrt(2.0) * p->Gf);

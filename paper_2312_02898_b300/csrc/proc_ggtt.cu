@@ -6,6 +6,7 @@
 // The first layout of each precision is the default; the others are alternatives for
 // tuning sweeps (me_set_config / ME_B300_CONFIG).
 #include "generated/proc_ggtt.cuh"
+#include "dfloat.cuh"
 #include "me_kernel_x2.cuh"
 #include "me_kernels.cuh"
 
@@ -22,6 +23,9 @@ template <> struct Cfg<1, 2> { using R = float; using L = Layout<0, 128, 0, 0, 0
 
 // FP32 on packed pairs, two events per thread (me_kernel_x2), everything in registers:
 // correct, a little slower than the scalar kernel here (measured)
+// FP64-emulating double-float amplitudes: the FP64 default layout (same 8-byte storage)
+template <> struct Cfg<3, 0> { using R = dfloat; using L = Layout<0, 128, 0, 0, 0, 0, 1>; };
+
 template <int C> struct X2Cfg;
 template <> struct X2Cfg<0> { using L = Layout<0, 128, 0, 0, 0, 0, 1, 0, 3>; };
 
@@ -32,6 +36,7 @@ LaunchNeeds needs(int prec, int config) {
     case 9: return needs_of<P, Cfg<1, 1>::R, Cfg<1, 1>::L>();
     case 10: return needs_of<P, Cfg<1, 2>::R, Cfg<1, 2>::L>();
     case 11: return needs_x2_of<P, X2Cfg<0>::L>();
+    case 24: return needs_of<P, Cfg<3, 0>::R, Cfg<3, 0>::L>();
     default: return LaunchNeeds{0, 0, 0, 0, false, 128, 1};
   }
 }
@@ -43,12 +48,13 @@ cudaError_t launch(int prec, int config, const MeLaunch& a, cudaStream_t s) {
     case 9: return launch_me<P, Cfg<1, 1>::R, Cfg<1, 1>::L>(a, s);
     case 10: return launch_me<P, Cfg<1, 2>::R, Cfg<1, 2>::L>(a, s);
     case 11: return launch_x2<P, X2Cfg<0>::L>(a, s);
+    case 24: return launch_me<P, Cfg<3, 0>::R, Cfg<3, 0>::L>(a, s);
     default: return cudaErrorNotSupported;
   }
 }
 }  // namespace
 
 extern const ProcessOps ops_ggtt = {P::NAME, P::NPAR, P::NCOMB, P::NCOL, P::NDIAG, P::NAMP, P::IDEN,
-                                   P::FLOPS_AMP, P::FLOPS_COL, /*has_mixed=*/false, {1, 4, 0},
+                                   P::FLOPS_AMP, P::FLOPS_COL, /*has_mixed=*/false, {1, 4, 0, 1},
                                    needs, launch};
 }  // namespace meb300

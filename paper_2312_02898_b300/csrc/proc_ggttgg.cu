@@ -120,6 +120,6 @@ cudaError_t launch(int prec, int config, const MeLaunch& a, cudaStream_t s) {
 }  // namespace
 
 extern const ProcessOps ops_ggttgg = {P::NAME, P::NPAR, P::NCOMB, P::NCOL, P::NDIAG, P::NAMP, P::IDEN,
-                                   P::FLOPS_AMP, P::FLOPS_COL, /*has_mixed=*/true, {4, 13, 6},
+                                   P::FLOPS_AMP, P::FLOPS_COL, /*has_mixed=*/true, {4, 13, 6, 0},
                                    needs, launch};
 }  // namespace meb300

@@ -48,6 +48,6 @@ cudaError_t launch(int prec, int config, const MeLaunch& a, cudaStream_t s) {
 }  // namespace
 
 extern const ProcessOps ops_ggttggg = {P::NAME, P::NPAR, P::NCOMB, P::NCOL, P::NDIAG, P::NAMP, P::IDEN,
-                                   P::FLOPS_AMP, P::FLOPS_COL, /*has_mixed=*/true, {1, 1, 1},
+                                   P::FLOPS_AMP, P::FLOPS_COL, /*has_mixed=*/true, {1, 1, 1, 0},
                                    needs, launch};
 }  // namespace meb300

@@ -103,40 +103,46 @@ __global__ void __launch_bounds__(kThreads) rambo_kernel(const RamboArgs a) {
     const double b[3] = {-Q[1] / M, -Q[2] / M, -Q[3] / M};
     const double gam = Q[0] / M, aa = 1.0 / (1.0 + gam), x = a.sqrt_s / M;
     double p[kMaxFinal][4];
-    bool massive = false;
     for (int k = 0; k < n; ++k) {
       const double bq = b[0] * q[k][1] + b[1] * q[k][2] + b[2] * q[k][3];
       p[k][0] = x * (gam * q[k][0] + bq);
       for (int m = 1; m < 4; ++m) p[k][m] = x * (q[k][m] + b[m - 1] * q[k][0] + aa * bq * b[m - 1]);
-      massive |= a.mass[k] > 0.0;
     }
-    bool ok = true;
-    if (massive) {
-      double msum = 0.0;
-      for (int k = 0; k < n; ++k) msum += a.mass[k];
-      const double r0 = 1.0 - (msum / a.sqrt_s) * (msum / a.sqrt_s);
-      double xi = sqrt(r0 > 0.0 ? r0 : 0.0);
-      ok = false;
-      for (int it = 0; it < kNewtonSteps; ++it) {
-        double rsum = 0.0, fp = 0.0;
-        for (int k = 0; k < n; ++k) {
-          const double e = xi * p[k][0];
-          const double r = sqrt(a.mass[k] * a.mass[k] + e * e);
-          rsum += r;
-          fp += xi * p[k][0] * p[k][0] / r;
-        }
-        const double f = rsum - a.sqrt_s;
-        if (fabs(f) <= 1e-15 * a.sqrt_s) {
-          ok = true;
-          break;
-        }
-        xi -= f / fp;
-      }
+    // The boost multiplies the rounding of the massless vectors by up to its gamma
+    // factor, so the residual of the three-momentum sum is taken out in equal parts, each
+    // vector is put on the light cone (E = |p|), the rescaling xi solves
+    // sum_i sqrt(m_i^2 + xi^2 |p_i|^2) = sqrt(s) (massless final states too), and each
+    // final energy comes from its final three-momentum: momentum conservation and every
+    // mass shell hold to rounding.
+    for (int m = 1; m < 4; ++m) {
+      double r = 0.0;
+      for (int k = 0; k < n; ++k) r += p[k][m];
+      for (int k = 0; k < n; ++k) p[k][m] -= r / n;
+    }
+    for (int k = 0; k < n; ++k) p[k][0] = sqrt(p[k][1] * p[k][1] + p[k][2] * p[k][2] + p[k][3] * p[k][3]);
+    double msum = 0.0;
+    for (int k = 0; k < n; ++k) msum += a.mass[k];
+    const double r0 = 1.0 - (msum / a.sqrt_s) * (msum / a.sqrt_s);
+    double xi = sqrt(r0 > 0.0 ? r0 : 0.0);
+    bool ok = false;
+    for (int it = 0; it < kNewtonSteps; ++it) {
+      double rsum = 0.0, fp = 0.0;
       for (int k = 0; k < n; ++k) {
         const double e = xi * p[k][0];
-        for (int m = 1; m < 4; ++m) p[k][m] *= xi;
-        p[k][0] = sqrt(a.mass[k] * a.mass[k] + e * e);
+        const double r = sqrt(a.mass[k] * a.mass[k] + e * e);
+        rsum += r;
+        fp += xi * p[k][0] * p[k][0] / r;
       }
+      const double f = rsum - a.sqrt_s;
+      if (fabs(f) <= 1e-15 * a.sqrt_s) {
+        ok = true;
+        break;
+      }
+      xi -= f / fp;
+    }
+    for (int k = 0; k < n; ++k) {
+      for (int m = 1; m < 4; ++m) p[k][m] *= xi;
+      p[k][0] = sqrt(a.mass[k] * a.mass[k] + (p[k][1] * p[k][1] + p[k][2] * p[k][2] + p[k][3] * p[k][3]));
     }
     double* out = a.mom + i * (n + 2) * 4;
     const double half = 0.5 * a.sqrt_s, nan = __longlong_as_double(0x7ff8000000000000ll);

@@ -33,6 +33,9 @@ PROCESSES = {
     "g g > t t~ g": dict(tag="ggttg", roles=("g_in", "g_in", "t", "tb", "g_out")),
     "g g > t t~ g g": dict(tag="ggttgg", roles=("g_in", "g_in", "t", "tb", "g_out", "g_out")),
     "g g > t t~ g g g": dict(tag="ggttggg", roles=("g_in", "g_in", "t", "tb", "g_out", "g_out", "g_out")),
+    # the quark-initiated channel of p p -> t t~ (any light flavour; either beam order)
+    "u u~ > t t~": dict(tag="qqtt", roles=("q_in", "qb_in", "t", "tb")),
+    "u~ u > t t~": dict(tag="qxqtt", roles=("qb_in", "q_in", "t", "tb")),
 }
 
 # jamps variants per process: (register budget, diagram-group size).  The budget is the
@@ -566,9 +569,81 @@ class Emitter:
                      col_den=1, max_live=2)
         return "\n".join(out) + "\n", stats
 
+    # ------------------------------------------------------------------ q q~ -> t t~
+    def emit_qqtt(self):
+        """q qbar -> t tbar through one s-channel gluon.  With the quark-gluon vertex
+        -i g T^a gamma^mu and the gluon propagator -i g_{mu nu} / s the amplitude is
+        i g^2 (L_q . L_t) / s times the colour factor sum_a T^a_{ji} T^a_{kl} =
+        (c_0 - c_1 / 3) / 2, c_0 = d_ki d_jl and c_1 = d_ji d_kl (i, j: quark and antiquark
+        colours; k, l: top and antitop).  The flows are carried scaled by 6, J = (3, -1) x
+        i (L_q . L_t) / s, with the colour matrix sum c_n c_m = [[9, 3], [3, 9]] over 36."""
+        iq, iqb = self.roles.index("q_in"), self.roles.index("qb_in")
+        fa = 4 * FLOPS["ext_u"] + 2 * FLOPS["pj"] + FLOPS["dot"] + 2 + 2 + 2
+        cf = [[9, 3], [3, 9]]
+        cs = []
+        csflops = 0
+        for i in range(2):
+            tr = [f"{_lit(cf[i][j] * (1 if j == i else 2))} * J[{j}].r" for j in range(i, 2)]
+            ti = [f"{_lit(cf[i][j] * (1 if j == i else 2))} * J[{j}].i" for j in range(i, 2)]
+            csflops += 4 * len(tr) + 4
+            cs.append(f"  {{ const R tr = {' + '.join(tr)}; const R ti = {' + '.join(ti)};")
+            cs.append(f"    s = fmadd(J[{i}].r, tr, fmadd(J[{i}].i, ti, s)); }}")
+        tag = self.tag
+        out = [f"// Generated by paper_2312_02898_b300/gen/emit.py for '{self.process}'. Do not edit.",
+               "#pragma once", '#include "../helas.cuh"', "namespace meb300 {", f"struct proc_{tag} {{",
+               f'static constexpr const char* NAME = "{self.process}";',
+               "// NGLUON counts the powers of g_s^2 in |M|^2 (two quark-gluon vertices)",
+               "static constexpr int NPAR = 4, NCOMB = 16, NCOL = 2, NDIAG = 1, NAMP = 1, NNODE = 2, IDEN = 36, NGLUON = 2;",
+               "static constexpr int NDEN_G = 1, NDEN_T = 1, COL_DEN = 36, NCOLPAIR = 2, MAX_LIVE = 2, NKVEC = 4;",
+               f"static constexpr long FLOPS_AMP = {fa}, FLOPS_COL = {csflops};",
+               "static constexpr bool QCD = true;",
+               "static constexpr bool CF_BF16_EXACT = true, CF_FP16_EXACT = true;",
+               "// dg[0] = 1/s of the s-channel gluon; no top propagator (dt unused)",
+               "template <int S, class R, class DG, class DT, class KT>",
+               "static HD double precompute(const double (*p)[4], double, double, int, DG& dg, DT& dt, KT kt) {",
+               "  for (int i = 0; i < 4; ++i)",
+               "    for (int m = 0; m < 4; ++m) kt[i * S + m] = R(p[i][m]);",
+               "  double q[4];",
+               f"  for (int m = 0; m < 4; ++m) q[m] = p[{iq}][m] + p[{iqb}][m];",
+               "  const double s = q[0] * q[0] - q[1] * q[1] - q[2] * q[2] - q[3] * q[3];",
+               "  dg[0] = R(1.0 / s);",
+               "  dt[0] = mk<R>(R(0), R(0));",
+               "  return 0.0;",
+               "}",
+               "static constexpr int NVARIANT = 1;",
+               "static constexpr int NSLOT[1] = {0};",
+               "template <int V> static HD constexpr int nslot() { return 0; }",
+               "template <int V> static HD constexpr bool grouped() { return false; }",
+               "static constexpr int BUDGET[1] = {-1};",
+               "template <int V, int S, class R, int SYNC = 0, class DG, class DT, class JA>",
+               "static HD void jamps(int h, R mt, const DG& dg, const DT&, JA& J, cx<R>*, const R* kt) {",
+               "  int lam[4];",
+               "  for (int i = 0; i < 4; ++i) lam[i] = ((h >> (3 - i)) & 1) ? 1 : -1;",
+               "  cx<R> xq[4], xqb[4], xt[4], xtb[4];",
+               f"  ext_u<R>(kt + {iq} * S, R(0), lam[{iq}], xq);        // incoming quark",
+               f"  ext_vbar<R>(kt + {iqb} * S, R(0), lam[{iqb}], xqb);  // incoming antiquark",
+               "  ext_ubar<R>(kt + 2 * S, mt, lam[2], xt);         // outgoing top",
+               "  ext_v<R>(kt + 3 * S, mt, lam[3], xtb);           // outgoing antitop",
+               "  cx<R> lq[4], lt[4];",
+               "  pair_current<R>(xqb, xq, lq);",
+               "  pair_current<R>(xt, xtb, lt);",
+               "  const cx<R> a = dg[0] * mdot(lq, lt);",
+               "  acc_pi(J[0], R(3) * a);",
+               "  acc_mi(J[1], a);",
+               "}",
+               "template <class R, class JA>",
+               "static HD R colour_sum(JA& J) {", "  R s = R(0);"] + cs + ["  return s;", "}", "};",
+               f"constexpr int proc_{tag}_CF[4] = {{9, 3, 3, 9}};",
+               "}  // namespace meb300"]
+        stats = dict(ndiag=1, namp=1, nnode=2, ncol=2, pairs=2, flops_amp=fa, flops_col=csflops, nden_g=1, nden_t=1,
+                     col_den=36, max_live=2)
+        return "\n".join(out) + "\n", stats
+
     def emit(self):
         if self.tag == "eemumu":
             return self.emit_eemumu()
+        if self.tag in ("qqtt", "qxqtt"):
+            return self.emit_qqtt()
         return self.emit_qcd(budgets=VARIANTS.get(self.tag, ((None, None),)))
 
 

@@ -113,22 +113,34 @@ def rambo(sqrt_s: float, masses_final, seed: int, nevt: int, first_event: int = 
     p[:, :, 0] = x[:, None] * (gam[:, None] * q[:, :, 0] + bq)
     p[:, :, 1:] = x[:, None, None] * (q[:, :, 1:] + b[:, None, :] * q[:, :, 0:1]
                                       + a[:, None, None] * bq[:, :, None] * b[:, None, :])
-    if np.any(masses > 0.0):
-        E = p[:, :, 0].copy()
-        xi = np.full(nevt, np.sqrt(max(0.0, 1.0 - (masses.sum() / sqrt_s) ** 2)))
-        done = np.zeros(nevt, dtype=bool)
-        for _ in range(max_newton):
-            r = np.sqrt(masses[None, :] ** 2 + (xi[:, None] * E) ** 2)
-            f = r.sum(axis=1) - sqrt_s
-            done |= np.abs(f) <= 1e-15 * sqrt_s
-            if done.all():
-                break
-            fp = (xi[:, None] * E * E / r).sum(axis=1)
-            xi = np.where(done, xi, xi - f / fp)
-        if not done.all():
-            raise RuntimeError("RAMBO mass rescaling did not converge")
-        p[:, :, 1:] *= xi[:, None, None]
-        p[:, :, 0] = np.sqrt(masses[None, :] ** 2 + (xi[:, None] * E) ** 2)
+    # The boost multiplies the rounding of the massless vectors by up to its gamma factor,
+    # which could leave a particle off its mass shell, the three-momenta not summing to
+    # zero or the energies off sqrt(s) by 1e-11 relative -- enough to separate two exact
+    # FP64 evaluations of a matrix element (which may route a propagator's momentum from
+    # either side) by 1e-12.  So the residual of the three-momentum sum is taken out in
+    # equal parts, each vector is put on the light cone (E = |p|), the rescaling xi solves
+    # sum_i sqrt(m_i^2 + xi^2 |p_i|^2) = sqrt(s) for massless and massive final states
+    # alike, and each final energy comes from its final three-momentum: momentum
+    # conservation and every mass shell hold to rounding.
+    resid = p[:, :, 1:].sum(axis=1)
+    p[:, :, 1:] -= resid[:, None, :] / n
+    E = np.sqrt(p[:, :, 1] * p[:, :, 1] + p[:, :, 2] * p[:, :, 2] + p[:, :, 3] * p[:, :, 3])
+    xi = np.full(nevt, np.sqrt(max(0.0, 1.0 - (masses.sum() / sqrt_s) ** 2)))
+    done = np.zeros(nevt, dtype=bool)
+    for _ in range(max_newton):
+        r = np.sqrt(masses[None, :] ** 2 + (xi[:, None] * E) ** 2)
+        f = r.sum(axis=1) - sqrt_s
+        done |= np.abs(f) <= 1e-15 * sqrt_s
+        if done.all():
+            break
+        fp = (xi[:, None] * E * E / r).sum(axis=1)
+        xi = np.where(done, xi, xi - f / fp)
+    if not done.all():
+        raise RuntimeError("RAMBO mass rescaling did not converge")
+    p[:, :, 1:] *= xi[:, None, None]
+    p3 = p[:, :, 1:]
+    p[:, :, 0] = np.sqrt(masses[None, :] ** 2 + (p3[..., 0] * p3[..., 0] + p3[..., 1] * p3[..., 1]
+                                                 + p3[..., 2] * p3[..., 2]))
     out = np.empty((nevt, n + 2, 4))
     half = 0.5 * sqrt_s
     out[:, 0] = (half, 0.0, 0.0, half)
@@ -146,6 +158,8 @@ PROCESS_FINAL_MASSES = {
     "g g > t t~ g": lambda mt: (mt, mt, 0.0),
     "g g > t t~ g g": lambda mt: (mt, mt, 0.0, 0.0),
     "g g > t t~ g g g": lambda mt: (mt, mt, 0.0, 0.0, 0.0),
+    "u u~ > t t~": lambda mt: (mt, mt),
+    "u~ u > t t~": lambda mt: (mt, mt),
 }
 
 

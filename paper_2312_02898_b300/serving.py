@@ -173,17 +173,22 @@ class Server:
         self.streams = [torch.cuda.Stream(self.device) for _ in range(n_slots)]
         # size every (process, stream) workspace for the largest chunk up front, so no
         # later call moves a workspace that a captured graph points into
+        # (every bucket up to the chunk: a call's workspace need not grow with its size,
+        # e.g. a smaller batch may spread each event over more threads)
         self.workspace_bytes = 0
+        sizes = [b for b in BUCKETS if b <= self.chunk]
         for m in self.handles.values():
             for s in self.streams:
-                m.reserve(self.chunk, s)
-                self.workspace_bytes += m.plan(self.chunk)[1]
+                for b in sizes:
+                    m.reserve(b, s)
+                self.workspace_bytes += max(m.plan(b)[1] for b in sizes)
         torch.cuda.synchronize()
         free, _ = torch.cuda.mem_get_info(self.device)
         room = int(0.8 * free) if mem_budget_bytes is None else min(int(mem_budget_bytes), int(0.8 * free))
         self.mem_budget = self.workspace_bytes + room
         self.slot_busy = [None] * n_slots           # (request, buffers, event, nbytes)
         self.buffers = {}                           # (slot, process, bucket) -> _Buffers
+        self._warmed = set()                        # processes whose kernels have run once
         self.admission = MemoryAdmission(self.mem_budget, reserved=self.workspace_bytes)
         self.use_graphs = use_graphs
         self.queue = collections.deque()
@@ -248,9 +253,12 @@ class Server:
         b.d_rh.fill_(0.5)
         b.d_rc.fill_(0.5)
         torch.cuda.synchronize()
-        # warm-up on the slot's stream grows that stream's workspace before capture
-        self._run(m, b, s, bucket)
-        s.synchronize()
+        # one uncaptured call per process loads its kernels before the first capture (the
+        # workspaces were reserved for the largest chunk when the server started)
+        if process not in self._warmed:
+            self._run(m, b, s, bucket)
+            s.synchronize()
+            self._warmed.add(process)
         if self.use_graphs:
             g = torch.cuda.CUDAGraph()
             with torch.cuda.graph(g, stream=s, capture_error_mode="relaxed"):

@@ -441,3 +441,44 @@ def test_binding_rejects_tensors_the_abi_would_misread():
            torch.empty(64, dtype=torch.int32, device="cuda"))
     with pytest.raises(ValueError):
         m.compute(mom, a, rh, rc, out=out)
+
+
+DFLOAT = [p for p in ACTIVE if p in (PROCS[1], PROCS[2])]
+DFLOAT_BOUND = 1e-10
+
+
+@pytest.mark.parametrize("process", DFLOAT)
+def test_dfloat_parity(process):
+    """FP64-emulating double-float amplitudes (about 48 significant bits on the FP32
+    pipe), with FP64 inputs, error-free invariants and FP64 helicity sum: every event
+    within the stated bound of the FP64 oracle (max and median printed), and the
+    selections equal except at running-sum boundaries."""
+    mom, a, rh, rc, ref = reference(process, NEV[process])
+    m = mk(process, "dfloat")
+    me, sh, sc = run_gpu(m, mom, a, rh, rc)
+    rel = np.abs(me / ref["me"] - 1)
+    print(f"{process} dfloat: max rel {rel.max():.3e} median {np.median(rel):.3e}")
+    assert rel.max() <= DFLOAT_BOUND
+    ok, e = boundary_ok(sh, ref["sel_hel"], ref["me_hel"], rh, 1e-8)
+    assert ok, ("sel_hel", e)
+    ok, e = boundary_ok(sc, ref["sel_col"], ref["colw"], rc, 1e-8)
+    assert ok, ("sel_col", e)
+
+
+@pytest.mark.skipif(PROCS[2] not in ACTIVE, reason="process not selected")
+def test_dfloat_on_nearly_collinear_gluons():
+    """The double-float mode forms its invariants error-free like the FP64 mode, so
+    nearly collinear gluons stay within its bound without any rescue pass."""
+    mom = collinear_events(PROCS[2], 64, seed=31)
+    ref = oracle.me(PROCS[2], mom)["me"]
+    me = mk(PROCS[2], "dfloat").compute(to_dev(mom)[0])[0].cpu().numpy()
+    rel = np.abs(me / ref - 1)
+    print(f"collinear dfloat: max rel {rel.max():.3e}")
+    assert rel.max() <= DFLOAT_BOUND
+
+
+def test_dfloat_is_not_built_for_the_large_processes():
+    from paper_2312_02898_b300.binding import MEError
+    with pytest.raises(MEError) as ei:
+        mk(PROCS[3], "dfloat")
+    assert ei.value.code == -2

@@ -63,3 +63,17 @@ def test_make_batch_alphas_streams():
     assert not np.array_equal(rh, rc)
     _, a2, _, _ = ps.make_batch("g g > t t~ g g", 1000, seed=0, alphas=0.118)
     assert np.all(a2 == 0.118)
+
+
+@pytest.mark.parametrize("process", ["g g > t t~", "g g > t t~ g g", "e+ e- > mu+ mu-"])
+def test_rambo_particles_on_shell_to_rounding(process):
+    """Every final particle is on its mass shell to the rounding of its own components,
+    and the final momenta add up to (sqrt(s), 0, 0, 0) to rounding, also on the rare
+    events whose RAMBO boost amplifies the rounding of the massless vectors."""
+    mom, _, _, _ = ps.make_batch(process, 20000, seed=51)
+    masses = np.array(ps.PROCESS_FINAL_MASSES[process](173.0))
+    p = mom[:, 2:]
+    m2 = p[..., 0] ** 2 - np.sum(p[..., 1:] ** 2, axis=-1)
+    assert np.max(np.abs(m2 - masses ** 2) / p[..., 0] ** 2) <= 4e-16
+    assert np.max(np.abs(p[..., 0].sum(axis=1) - 1500.0)) <= 4e-15 * 1500.0
+    assert np.max(np.abs(p[..., 1:].sum(axis=1))) <= 4e-15 * 1500.0
