@@ -288,7 +288,47 @@ def time_unweight(me, warmup, reps):
                           "accepted": int(r[3].item()), "launches_per_call": 2}
     m.close()
     out["note"] = "inputs resident (L2-sized); bound by launch latency at madevent's batch size"
+    out["fused"] = time_fused_unweight(warmup, reps)
     return out
+
+
+def time_fused_unweight(warmup, reps, n=16384):
+    """me_compute_unweight (weights and batch maximum in the matrix-element kernel's
+    epilogue, then one accept pass) against me_compute followed by me_unweight, per call
+    of a madevent-sized batch, for a cheap and an expensive process (FP64)"""
+    import torch
+    from paper_2312_02898_b300 import phasespace as ps
+    from paper_2312_02898_b300.binding import MatrixElement
+    from paper_2312_02898_b300.phasespace import uniforms
+    res = {}
+    for process in ("e+ e- > mu+ mu-", PROCESS):
+        m = MatrixElement(process, precision="fp64")
+        mom, a, rh, rc = ps.make_batch(process, n, seed=3, alphas="uniform")
+        u = uniforms(7, np.arange(n, dtype=np.uint64), 0, 2)
+        d = [torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in (mom, a, rh, rc, u[:, 0], u[:, 1])]
+
+        def fused():
+            return m.compute_unweight(*d)
+
+        def separate():
+            me, _, _ = m.compute(*d[:4])
+            return m.unweight(me, d[4], d[5])
+
+        times = {}
+        for name, fn in (("fused", fused), ("separate", separate)):
+            for _ in range(warmup):
+                fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                fn()
+            e1.record()
+            torch.cuda.synchronize()
+            times[name] = e0.elapsed_time(e1) * 1e3 / reps
+        res[process] = {"events": n, "us_per_call_fused": times["fused"], "us_per_call_separate": times["separate"]}
+        m.close()
+    return res
 
 
 def accuracy_sample(mode_out, host_inputs, n=4096, process=None):

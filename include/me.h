@@ -196,6 +196,24 @@ int me_compute_channels(me_handle* const* hs, int nchan, int64_t nevt, const int
 int me_unweight(me_handle* h, int64_t nevt, const double* me, const double* wgt, const double* rnd,
                 double* w, uint8_t* accept, double* w_max, int64_t* n_accept, void* cuda_stream);
 
+/* me_compute and me_unweight in one call: the event weight w_i = me_i * wgt_i and the
+ * batch maximum are formed in the epilogue of the matrix-element kernel (the step that
+ * writes me and the selections), the reduction the paper places beside the event
+ * selection (Section 3, Table 2); then one pass decides accept_i = w_i > rnd_i * w_max.
+ * Arguments as in me_compute, then:
+ *   wgt, rnd     device, FP64 [nevt]   as in me_unweight (rnd needed for accept/n_accept)
+ *   w, accept    device outputs as in me_unweight, or NULL
+ *   w_max        device, one FP64, 8-byte aligned (output, required)
+ *   n_accept     device, one int64, or NULL
+ * The outputs equal those of me_compute followed by me_unweight on its results, bit for
+ * bit.  In the FP32 and mixed modes an event re-evaluated by the FP64 rescue pass enters
+ * w and w_max with its FP64 value only.  Errors: those of me_compute and me_unweight;
+ * ME_ERR_MODE for a launch configuration with two events per thread. */
+int me_compute_unweight(me_handle* h, int64_t nevt, const double* momenta, const double* alphas,
+                        const double* rnd_hel, const double* rnd_col, const double* wgt, const double* rnd,
+                        double* me, int32_t* sel_hel, int32_t* sel_col, double* w, uint8_t* accept,
+                        double* w_max, int64_t* n_accept, void* cuda_stream);
+
 /* Synthetic inputs generated on the device, for the standalone multi-event testbed
  * (Section 2, Fig. 1b): a batch of test events is made and evaluated without a host
  * round trip.  The numbers are those of the counter-based definition (Philox4x32-10,

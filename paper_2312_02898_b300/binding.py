@@ -19,7 +19,7 @@ PRECISIONS = {"fp64": 0, "fp32": 1, "mixed": 2, "dfloat": 3}
 EXPORTS = ("me_default_params", "me_init", "me_compute", "me_compute_host", "me_info", "me_good_helicities",
            "me_flops", "me_plan", "me_reserve", "me_launch_shape", "me_set_config", "me_last_error", "me_free",
            "me_compute_noalloc", "me_unweight", "me_rambo", "me_uniforms", "me_probe_alu_peak", "me_sync_status",
-           "me_set_wait_limit", "me_compute_channels")
+           "me_set_wait_limit", "me_compute_channels", "me_compute_unweight")
 
 
 class SMParams(ctypes.Structure):
@@ -66,6 +66,7 @@ def load(path: str = LIB_PATH):
     lib.me_set_config.argtypes = [vp, ctypes.c_int]
     lib.me_sync_status.argtypes = [vp, vp]
     lib.me_compute_channels.argtypes = [ctypes.POINTER(vp), ctypes.c_int, i64] + [vp] * 9
+    lib.me_compute_unweight.argtypes = [vp, i64] + [vp] * 14
     lib.me_set_wait_limit.argtypes = [vp, i64]
     lib.me_plan.argtypes = [vp, i64, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
     lib.me_probe_alu_peak.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
@@ -76,7 +77,7 @@ def load(path: str = LIB_PATH):
     for f in ("me_init", "me_compute", "me_compute_host", "me_compute_noalloc", "me_info", "me_good_helicities",
               "me_flops", "me_set_config", "me_plan", "me_reserve", "me_launch_shape", "me_unweight",
               "me_rambo", "me_uniforms", "me_probe_alu_peak", "me_sync_status", "me_set_wait_limit",
-              "me_compute_channels"):
+              "me_compute_channels", "me_compute_unweight"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -279,6 +280,29 @@ class MatrixElement:
         self._check(self.lib.me_unweight(self.handle, n, _ptr(me), _ptr(wgt), _ptr(rnd), _ptr(w), _ptr(acc),
                                          _ptr(wmax), _ptr(nacc), ctypes.c_void_p(s.cuda_stream)))
         return w, acc, wmax, nacc
+
+    def compute_unweight(self, momenta, alphas, rnd_hel, rnd_col, wgt, rnd, stream=None):
+        """me_compute_unweight on device tensors: (me, sel_hel, sel_col, w, accept, w_max,
+        n_accept), asynchronous on ``stream``"""
+        import torch
+        nevt = momenta.shape[0]
+        dev = momenta.device
+        out = (torch.empty(nevt, dtype=torch.float64, device=dev),
+               torch.empty(nevt, dtype=torch.int32, device=dev) if rnd_hel is not None else None,
+               torch.empty(nevt, dtype=torch.int32, device=dev) if rnd_col is not None else None)
+        self._check_args(momenta, alphas, rnd_hel, rnd_col, out, dev)
+        _check_tensor("wgt", wgt, torch.float64, (nevt,), dev, required=True)
+        _check_tensor("rnd", rnd, torch.float64, (nevt,), dev)
+        w = torch.empty(nevt, dtype=torch.float64, device=dev)
+        acc = torch.empty(nevt, dtype=torch.uint8, device=dev) if rnd is not None else None
+        wmax = torch.empty(1, dtype=torch.float64, device=dev)
+        nacc = torch.empty(1, dtype=torch.int64, device=dev) if rnd is not None else None
+        s = stream if stream is not None else torch.cuda.current_stream(dev)
+        self._check(self.lib.me_compute_unweight(self.handle, nevt, _ptr(momenta), _ptr(alphas), _ptr(rnd_hel),
+                                                 _ptr(rnd_col), _ptr(wgt), _ptr(rnd), _ptr(out[0]), _ptr(out[1]),
+                                                 _ptr(out[2]), _ptr(w), _ptr(acc), _ptr(wmax), _ptr(nacc),
+                                                 ctypes.c_void_p(s.cuda_stream)))
+        return out + (w, acc, wmax, nacc)
 
     def rambo(self, nevt, seed=0, first_event=0, sqrt_s=1500.0, stream=None):
         """RAMBO momenta for this process generated on the device: a [nevt][npar][4] tensor"""

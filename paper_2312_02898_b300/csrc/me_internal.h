@@ -76,6 +76,11 @@ cudaError_t launch_chunks(const ProcessOps* ops, int prec, int config, MeLaunch 
                           const Carve& cv, void* wsp, cudaStream_t s, int ept);
 CallPlan plan_call(const me_handle* h, int64_t nevt, int64_t chunk, bool want_hel, bool want_col);
 cudaError_t run_call(const me_handle* h, const CallPlan& cp, const MeLaunch& a, int64_t nevt, void* wsp, cudaStream_t s);
+// the body of me_compute for checked device arguments; with wgt, the fused unweighting
+// outputs w (may be null) and the batch maximum's bit pattern (cleared by the caller)
+int compute_device(me_handle* h, int64_t nevt, const double* momenta, const double* alphas, const double* rnd_hel,
+                   const double* rnd_col, double* me, int32_t* sel_hel, int32_t* sel_col, cudaStream_t s,
+                   const double* wgt, double* w, unsigned long long* wmax_bits);
 
 }  // namespace detail
 }  // namespace meb300

@@ -134,6 +134,7 @@ __global__ void __launch_bounds__(128) me_kernel_mixed(const MeLaunch a) {
     else return a.colw[c * wstride + wrow];
   };
 
+  double wmax_t = 0.0;  // fused unweighting: this thread's largest valid weight
   for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
   const int64_t ievt_raw = tile * BLOCK + tid;
   const bool active = ievt_raw < nevt;
@@ -160,7 +161,8 @@ __global__ void __launch_bounds__(128) me_kernel_mixed(const MeLaunch a) {
     }
   }
   const double kappa = P::template precompute<BLOCK * 4, R>(pd, a.mt, a.wt, a.zwt, v_dg, v_dt, kt);
-  if (active && a.rescue_list && kappa > a.rescue_kappa) {
+  const bool flagged = a.rescue_list && kappa > a.rescue_kappa;
+  if (active && flagged) {
     const int slot = atomicAdd(a.rescue_count, 1);
     if (slot < a.rescue_cap) a.rescue_list[slot] = int(a.ibase + ievt);
   }
@@ -285,6 +287,7 @@ __global__ void __launch_bounds__(128) me_kernel_mixed(const MeLaunch a) {
 
   if (!active) continue;
   a.me[ievt] = failed ? __longlong_as_double(0x7ff8000000000000ll) : total / double(P::IDEN);
+  if (!failed) fuse_weight(a, ievt, total / double(P::IDEN), flagged, wmax_t);
   if (a.sel_hel && a.cum && !a.cum_mode) {
     int sel = 0;
     if (total > 0.0 && !failed) {
@@ -323,6 +326,8 @@ __global__ void __launch_bounds__(128) me_kernel_mixed(const MeLaunch a) {
     a.sel_col[ievt] = sel;
   }
   }  // tile loop
+
+  flush_wmax(a, wmax_t);
 
   // --- teardown: no MMA may still be in flight when the columns are freed, so the
   // wait for the commit that the failed wait gave up on gets the full default limit

@@ -209,6 +209,7 @@ __global__ void __launch_bounds__(128) me_kernel_mixed_pipe(const MeLaunch a) {
     else return a.colw[c * wstride + wrow];
   };
 
+  double wmax_t = 0.0;  // fused unweighting: this thread's largest valid weight
   for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
     const int64_t ievt_raw = tile * BLOCK + tid;
     const bool active = ievt_raw < nevt;
@@ -234,7 +235,8 @@ __global__ void __launch_bounds__(128) me_kernel_mixed_pipe(const MeLaunch a) {
       }
     }
     const double kappa = P::template precompute<BLOCK * 4, R>(pd, a.mt, a.wt, a.zwt, v_dg, v_dt, kt);
-    if (active && a.rescue_list && kappa > a.rescue_kappa) {
+    const bool flagged = a.rescue_list && kappa > a.rescue_kappa;
+    if (active && flagged) {
       const int slot = atomicAdd(a.rescue_count, 1);
       if (slot < a.rescue_cap) a.rescue_list[slot] = int(a.ibase + ievt);
     }
@@ -312,6 +314,7 @@ __global__ void __launch_bounds__(128) me_kernel_mixed_pipe(const MeLaunch a) {
 
     if (!active) continue;
     a.me[ievt] = failed ? __longlong_as_double(0x7ff8000000000000ll) : total / double(P::IDEN);
+    if (!failed) fuse_weight(a, ievt, total / double(P::IDEN), flagged, wmax_t);
     if (a.sel_hel && a.cum) {
       int sel = 0;
       if (total > 0.0 && !failed) {
@@ -350,6 +353,8 @@ __global__ void __launch_bounds__(128) me_kernel_mixed_pipe(const MeLaunch a) {
       a.sel_col[ievt] = sel;
     }
   }  // tile loop
+
+  flush_wmax(a, wmax_t);
 
   // --- teardown: the commit whose wait ran out may still be in flight; wait for it with
   // the default limit before the columns are freed

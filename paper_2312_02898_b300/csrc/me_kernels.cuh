@@ -59,6 +59,11 @@ struct MeLaunch {
   void* ktab;        // [block][nkvec][BLOCK][4] real (momentum table in global memory)
   void* dtile;       // [block][nden_g][BLOCK] real, then [block][nden_t][BLOCK] complex (denominators in global memory)
   void* jtile;       // [block][ncol][BLOCK] complex (colour-flow amplitudes in global memory)
+  // fused batch unweighting (me_compute_unweight): w = me * wgt per event and the batch
+  // maximum of the valid weights, formed in the epilogue (null when not requested)
+  const double* wgt;
+  double* w;
+  unsigned long long* wmax_bits;  // the maximum as the bit pattern of a non-negative double
   int* err;          // set to 1 when a bounded device-side wait runs out (mapped host memory)
   uint32_t mma_wait_limit;  // polls of the mixed kernel's wait for its MMAs (0: give up at once)
   // precision rescue (FP32 and mixed passes): events whose conditioning kappa exceeds
@@ -82,6 +87,36 @@ struct MeLaunch {
   // latency of one event is spread over many threads.
   int hsplit;
 };
+
+// Fused unweighting, epilogue part: the event weight w = me * wgt and this thread's
+// running maximum of the valid weights (finite and >= 0).  An event that the FP32 and
+// mixed main passes flag for the FP64 rescue is left to the rescue pass, so that its
+// reduced-precision value never enters the maximum.
+__device__ __forceinline__ void fuse_weight(const MeLaunch& a, int64_t ievt, double me, bool flagged, double& wmax) {
+  if (!a.wgt || flagged) return;
+  const double wi = me * a.wgt[ievt];
+  if (a.w) a.w[ievt] = wi;
+  if (isfinite(wi) && wi >= 0.0) wmax = fmax(wmax, wi);
+}
+// The block maximum of the threads' running maxima and one 64-bit atomicMax per block on
+// its bit pattern (non-negative IEEE doubles order like their bit patterns).  Every
+// thread of the block calls it, once, after its tile loop.
+static __device__ __noinline__ void flush_wmax(const MeLaunch& a, double wmax) {
+  if (!a.wmax_bits) return;  // the same for the whole block
+  __shared__ double s_m[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) wmax = fmax(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
+  const int warp = threadIdx.x >> 5, nwarp = (blockDim.x + 31) >> 5;
+  if ((threadIdx.x & 31) == 0) s_m[warp] = wmax;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    wmax = threadIdx.x < nwarp ? s_m[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) wmax = fmax(wmax, __shfl_xor_sync(0xffffffffu, wmax, o));
+    if (threadIdx.x == 0 && wmax > 0.0)
+      atomicMax(a.wmax_bits, static_cast<unsigned long long>(__double_as_longlong(wmax)));
+  }
+}
 
 // view of an array laid out [index][S]
 template <class T, int S>
@@ -212,6 +247,7 @@ __global__ void __launch_bounds__(L::BLOCK, L::minb) me_kernel(const MeLaunch a)
   // event and writes nothing, so every thread reaches every block barrier.
   // A group of G threads never straddles the end of the batch (nunit is a multiple of G
   // and BLOCK of 32), so the shuffles below always see whole groups.
+  double wmax_t = 0.0;  // fused unweighting: this thread's largest valid weight
   for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
   const int64_t unit = tile * BLOCK + tid;
   const bool active = unit < nunit;
@@ -284,7 +320,8 @@ __global__ void __launch_bounds__(L::BLOCK, L::minb) me_kernel(const MeLaunch a)
     else kappa = P::template precompute<BLOCK * 4, R>(pd, a.zc[2], a.zc[3], 0, r_dg, r_dt, kt);
     gfac = a.coup / double(P::COL_DEN);
   }
-  if (active && lane == 0 && a.rescue_list && kappa > a.rescue_kappa) {
+  const bool flagged = a.rescue_list && kappa > a.rescue_kappa;
+  if (active && lane == 0 && flagged) {
     const int slot = atomicAdd(a.rescue_count, 1);
     if (slot < a.rescue_cap) a.rescue_list[slot] = int(a.ibase + ievt);
   }
@@ -404,6 +441,7 @@ __global__ void __launch_bounds__(L::BLOCK, L::minb) me_kernel(const MeLaunch a)
   }
   if (!active || lane != 0) continue;
   a.me[ievt] = total / double(P::IDEN);
+  fuse_weight(a, ievt, total / double(P::IDEN), flagged, wmax_t);
   if (G > 1 && a.sel_hel) {
     a.sel_hel[ievt] = sel_split;
   } else if (a.sel_hel && a.cum && !a.cum_mode) {
@@ -451,6 +489,7 @@ __global__ void __launch_bounds__(L::BLOCK, L::minb) me_kernel(const MeLaunch a)
     a.sel_col[ievt] = sel;
   }
   }  // tile loop
+  flush_wmax(a, wmax_t);
 }
 
 // ---------------------------------------------------------------------------

@@ -453,9 +453,13 @@ int me_init(const char* process, const me_sm_params* p, me_handle** out) {
   return ME_OK;
 }
 
-static int compute_device(me_handle* h, int64_t nevt, const double* momenta, const double* alphas,
-                          const double* rnd_hel, const double* rnd_col, double* me, int32_t* sel_hel,
-                          int32_t* sel_col, cudaStream_t s) {
+}  // extern "C"
+
+namespace meb300 {
+namespace detail {
+int compute_device(me_handle* h, int64_t nevt, const double* momenta, const double* alphas, const double* rnd_hel,
+                   const double* rnd_col, double* me, int32_t* sel_hel, int32_t* sel_col, cudaStream_t s,
+                   const double* wgt, double* w, unsigned long long* wmax_bits) {
   if (h->err_host && *h->err_host) {
     *h->err_host = 0;
     return fail(h, ME_ERR_TIMEOUT, "me_compute: a device-side wait of an earlier call on this handle timed out; "
@@ -466,6 +470,8 @@ static int compute_device(me_handle* h, int64_t nevt, const double* momenta, con
   const bool want_hel = sel_hel && rnd_hel;
   const bool want_col = sel_col && rnd_col;
   const LaunchNeeds nd = ops->needs(h->par.precision, h->config);
+  if (wgt && nd.ept != 1)
+    return fail(h, ME_ERR_MODE, "fused unweighting: the selected launch configuration carries two events per thread");
   const CallPlan cp = plan_call(h, nevt, chunk_for(nd, nevt), want_hel, want_col);
   void* wsp = nullptr;
   if (cp.total) {
@@ -484,10 +490,17 @@ static int compute_device(me_handle* h, int64_t nevt, const double* momenta, con
   a.sel_col = want_col ? sel_col : nullptr;
   a.ngood = ngood;
   for (int i = 0; i < ngood; ++i) a.good[i] = uint8_t(h->good[i]);
+  a.wgt = wgt;
+  a.w = w;
+  a.wmax_bits = wmax_bits;
   cudaError_t e = run_call(h, cp, a, nevt, wsp, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "me_compute launch");
   return ME_OK;
 }
+}  // namespace detail
+}  // namespace meb300
+
+extern "C" {
 
 int me_reserve(me_handle* h, int64_t nevt, void* cuda_stream) {
   if (!h) return fail(nullptr, ME_ERR_ARG, "me_reserve: null handle");
@@ -514,7 +527,7 @@ int me_compute(me_handle* h, int64_t nevt, const double* momenta, const double* 
   for (const void* p : ptrs)
     if (p && !is_device_ptr(p)) return fail(h, ME_ERR_ARG, "me_compute: arrays must be device memory");
   return compute_device(h, nevt, momenta, alphas, rnd_hel, rnd_col, me, sel_hel, sel_col,
-                        static_cast<cudaStream_t>(cuda_stream));
+                        static_cast<cudaStream_t>(cuda_stream), nullptr, nullptr, nullptr);
 }
 
 int me_compute_host(me_handle* h, int64_t nevt, const double* momenta, const double* alphas,
@@ -548,7 +561,7 @@ int me_compute_host(me_handle* h, int64_t nevt, const double* momenta, const dou
   if (e == cudaSuccess && rnd_col) e = cudaMemcpyAsync(d_rc, rnd_col, nevt * 8, cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "me_compute_host H2D");
   rc = compute_device(h, nevt, d_mom, alphas ? d_as : nullptr, rnd_hel ? d_rh : nullptr, rnd_col ? d_rc : nullptr,
-                      d_me, sel_hel ? d_sh : nullptr, sel_col ? d_sc : nullptr, s);
+                      d_me, sel_hel ? d_sh : nullptr, sel_col ? d_sc : nullptr, s, nullptr, nullptr, nullptr);
   if (rc) return rc;
   e = cudaMemcpyAsync(me, d_me, nevt * 8, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess && sel_hel) e = cudaMemcpyAsync(sel_hel, d_sh, nevt * 4, cudaMemcpyDeviceToHost, s);

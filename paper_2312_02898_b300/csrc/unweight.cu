@@ -109,3 +109,44 @@ extern "C" int me_unweight(me_handle* h, int64_t nevt, const double* me, const d
   if (e != cudaSuccess) return cuda_fail(h, e, "me_unweight launch");
   return ME_OK;
 }
+
+// me_compute and me_unweight in one call, with the weight and the batch maximum formed in
+// the matrix-element kernel's epilogue (the selection step of the kernel), so the only
+// extra work is the accept/reject pass, which needs the finished maximum.
+extern "C" int me_compute_unweight(me_handle* h, int64_t nevt, const double* momenta, const double* alphas,
+                                   const double* rnd_hel, const double* rnd_col, const double* wgt, const double* rnd,
+                                   double* me, int32_t* sel_hel, int32_t* sel_col, double* w, uint8_t* accept,
+                                   double* w_max, int64_t* n_accept, void* cuda_stream) {
+  if (!h) return fail(nullptr, ME_ERR_ARG, "me_compute_unweight: null handle");
+  if (nevt < 0) return fail(h, ME_ERR_ARG, "me_compute_unweight: nevt < 0");
+  if (nevt == 0) return ME_OK;
+  if (nevt > INT32_MAX) return fail(h, ME_ERR_ARG, "me_compute_unweight: more than 2^31 - 1 events in one call");
+  if (!momenta || !me || !wgt || !w_max)
+    return fail(h, ME_ERR_ARG, "me_compute_unweight: momenta, me, wgt and w_max are required");
+  if (reinterpret_cast<uintptr_t>(momenta) % 16)
+    return fail(h, ME_ERR_ARG, "me_compute_unweight: momenta must be 16-byte aligned");
+  if ((sel_hel && !rnd_hel) || (sel_col && !rnd_col))
+    return fail(h, ME_ERR_ARG, "me_compute_unweight: a selection output needs its random numbers");
+  if ((accept || n_accept) && !rnd) return fail(h, ME_ERR_ARG, "me_compute_unweight: accept/n_accept need rnd");
+  if (reinterpret_cast<uintptr_t>(w_max) % 8 || reinterpret_cast<uintptr_t>(n_accept) % 8)
+    return fail(h, ME_ERR_ARG, "me_compute_unweight: w_max and n_accept must be 8-byte aligned");
+  const void* ptrs[] = {momenta, me, alphas, rnd_hel, rnd_col, sel_hel, sel_col, wgt, rnd, w, accept, w_max, n_accept};
+  for (const void* p : ptrs)
+    if (p && !is_device_ptr(p)) return fail(h, ME_ERR_ARG, "me_compute_unweight: arrays must be device memory");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  auto* bits = reinterpret_cast<unsigned long long*>(w_max);
+  auto* cnt = reinterpret_cast<unsigned long long*>(n_accept);
+  cudaError_t e = cudaMemsetAsync(bits, 0, sizeof(double), s);  // +0.0
+  if (e == cudaSuccess && cnt) e = cudaMemsetAsync(cnt, 0, sizeof(int64_t), s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "me_compute_unweight: clearing the outputs");
+  int rc = compute_device(h, nevt, momenta, alphas, rnd_hel, rnd_col, me, sel_hel, sel_col, s, wgt, w, bits);
+  if (rc) return rc;
+  if (accept || cnt) {
+    const int64_t want = (nevt + kThreads - 1) / kThreads;
+    const int blocks = int(want < kMaxBlocks ? want : kMaxBlocks);
+    unweight_accept<<<blocks, kThreads, 0, s>>>(nevt, me, wgt, rnd, bits, accept, cnt);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(h, e, "me_compute_unweight: accept launch");
+  }
+  return ME_OK;
+}

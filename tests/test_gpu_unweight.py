@@ -89,3 +89,29 @@ def test_full_batch_sampled(handle):
     ow, oacc, owmax, onacc = oracle_unweight(me, wgt, rnd)
     assert wmax == owmax and nacc == onacc
     np.testing.assert_array_equal(acc, oacc)
+
+
+@pytest.mark.parametrize("process,precision,kappa", [("g g > t t~ g", "fp64", None), ("g g > t t~ g", "fp32", 1e-300),
+                                                     ("g g > t t~ g", "fp32", None), ("g g > t t~ g g", "mixed", None),
+                                                     ("e+ e- > mu+ mu-", "fp64", None)])
+def test_fused_unweighting_equals_compute_then_unweight(process, precision, kappa):
+    """me_compute_unweight forms the weights and the batch maximum in the matrix-element
+    kernel's epilogue; its outputs equal me_compute followed by me_unweight bit for bit,
+    also when the FP32 rescue pass re-evaluates every event (kappa below every event's)."""
+    import torch
+    from paper_2312_02898_b300 import phasespace as ps
+    from paper_2312_02898_b300.binding import MatrixElement
+    n = 3001 if process != "g g > t t~ g g" else 1501
+    mom, a, rh, rc = ps.make_batch(process, n, seed=61, alphas="uniform")
+    u = ps.uniforms(62, np.arange(n, dtype=np.uint64), 0, 2)
+    wgt, rnd = u[:, 0] * 1e3, u[:, 1]
+    d = [torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in (mom, a, rh, rc, wgt, rnd)]
+    kw = {} if kappa is None else {"rescue_kappa": kappa}
+    m = MatrixElement(process, precision=precision, **kw)
+    me, sh, sc, w, acc, wmax, nacc = m.compute_unweight(*d)
+    me2, sh2, sc2 = m.compute(*d[:4])
+    w2, acc2, wmax2, nacc2 = m.unweight(me2, d[4], d[5])
+    torch.cuda.synchronize()
+    for x, y in ((me, me2), (sh, sh2), (sc, sc2), (w, w2), (acc, acc2), (wmax, wmax2), (nacc, nacc2)):
+        assert torch.equal(x, y)
+    assert wmax.item() > 0 and 0 < nacc.item() < n
