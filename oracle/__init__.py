@@ -17,6 +17,13 @@ normalisation of the recursion for gg -> ttbar gg and gg -> ttbar ggg.  What the
 massless limit leaves open there (the massive spinors and top propagators at 4-5
 gluons) is pinned by the same code being exact for gg -> ttbar against its closed
 form, and by gauge invariance and Bose symmetry at the physical top mass.
+
+The one-jet quark channels of p p -> t tbar + jet (q qbar -> t tbar g, q g -> t tbar q,
+qbar g -> t tbar qbar, in either beam order) are pinned by gauge invariance, the
+soft-gluon limit with colour correlators from an explicit Gell-Mann sum, the
+initial-state collinear limits with the Altarelli-Parisi splitting functions (onto the
+closed-form-pinned q qbar -> t tbar and g g -> t tbar), charge conjugation, beam order,
+Lorentz invariance and their flow colour matrix.
 """
 from __future__ import annotations
 
@@ -39,6 +46,12 @@ PROCESSES = (
     "g g > t t~ g g g",
     "u u~ > t t~",
     "u~ u > t t~",
+    "u u~ > t t~ g",
+    "u~ u > t t~ g",
+    "u g > t t~ u",
+    "g u > t t~ u",
+    "u~ g > t t~ u~",
+    "g u~ > t t~ u~",
 )
 
 

@@ -29,7 +29,10 @@
  * quark-initiated channel of p p -> t tbar) the one s-channel gluon diagram is written
  * out with explicit colour indices and explicit Gell-Mann matrices T^a = lambda^a / 2:
  * |M|^2 is summed over all 81 colour assignments, and the colour-flow amplitudes are the
- * coefficients of the amplitude on the two flow tensors (a 2 x 2 Gram system).
+ * coefficients of the amplitude on the two flow tensors (a 2 x 2 Gram system).  Its
+ * one-jet crossings (q qbar -> t tbar g, q g -> t tbar q, qbar g -> t tbar qbar) are the
+ * five Feynman diagrams of one light-quark line, the top line and one gluon, summed the
+ * same way over all 648 colour assignments and projected onto four flow tensors.
  *
  * Conventions shared with the product only through their published definitions:
  *   * momenta [nevt][npar][4] = (E, px, py, pz); particle order of the process string;
@@ -51,7 +54,7 @@
 
 typedef double complex cx;
 
-#define NPROC 7
+#define NPROC 13
 #define MAXPAR 7
 #define MAXG 5
 #define MAXCOL 120
@@ -62,10 +65,12 @@ typedef struct {
 } oracle_params;
 
 /* roles of external particles */
-enum { R_EBAR_IN, R_E_IN, R_MUBAR_OUT, R_MU_OUT, R_G_IN, R_G_OUT, R_T_OUT, R_TBAR_OUT, R_Q_IN, R_QB_IN };
+enum { R_EBAR_IN, R_E_IN, R_MUBAR_OUT, R_MU_OUT, R_G_IN, R_G_OUT, R_T_OUT, R_TBAR_OUT, R_Q_IN, R_QB_IN,
+       R_Q_OUT, R_QB_OUT };
 
 /* kind: 0 e+ e- -> mu+ mu-; 1 g g -> t tbar + gluons (Berends-Giele); 2 q qbar -> t tbar
- * (explicit colour) */
+ * (explicit colour); 3 q qbar -> t tbar g and its crossings with one light quark line, a
+ * top line and one gluon (explicit colour, five Feynman diagrams) */
 typedef struct {
   const char* name;
   int npar;
@@ -86,6 +91,13 @@ static const proc_def PROCS[NPROC] = {
     /* IDEN = 4 initial spin states x 9 initial colour states */
     {"u u~ > t t~", 4, 0, 36, {R_Q_IN, R_QB_IN, R_T_OUT, R_TBAR_OUT}, 2, 2},
     {"u~ u > t t~", 4, 0, 36, {R_QB_IN, R_Q_IN, R_T_OUT, R_TBAR_OUT}, 2, 2},
+    /* one extra jet: IDEN = 4 x 9 (q qbar) or 4 x 3 x 8 (q g) initial states */
+    {"u u~ > t t~ g", 5, 0, 36, {R_Q_IN, R_QB_IN, R_T_OUT, R_TBAR_OUT, R_G_OUT}, 3, 4},
+    {"u~ u > t t~ g", 5, 0, 36, {R_QB_IN, R_Q_IN, R_T_OUT, R_TBAR_OUT, R_G_OUT}, 3, 4},
+    {"u g > t t~ u", 5, 0, 96, {R_Q_IN, R_G_IN, R_T_OUT, R_TBAR_OUT, R_Q_OUT}, 3, 4},
+    {"g u > t t~ u", 5, 0, 96, {R_G_IN, R_Q_IN, R_T_OUT, R_TBAR_OUT, R_Q_OUT}, 3, 4},
+    {"u~ g > t t~ u~", 5, 0, 96, {R_QB_IN, R_G_IN, R_T_OUT, R_TBAR_OUT, R_QB_OUT}, 3, 4},
+    {"g u~ > t t~ u~", 5, 0, 96, {R_G_IN, R_QB_IN, R_T_OUT, R_TBAR_OUT, R_QB_OUT}, 3, 4},
 };
 
 static int factorial(int n) { return n <= 1 ? 1 : n * factorial(n - 1); }
@@ -220,8 +232,26 @@ static void perm_unrank(int n, int r, int* out) {
 /* C_{st} = Tr(T^{s_1}...T^{s_n} T^{t_n}...T^{t_1}) as num[ncol*ncol] / den[ncol*ncol]. */
 static double qq_flow_tensor(int n, int i, int j, int k, int l);
 
+static void qg_colour_init(void);
+static void qg_gram(cx G[4][4]);
+
 int oracle_colour_matrix_exact(int proc, int64_t* num, int64_t* den) {
   if (proc < 0 || proc >= NPROC) return -1;
+  if (PROCS[proc].kind == 3) {
+    /* C_nm = sum over all colour assignments of conj(c_n) c_m, with explicit Gell-Mann
+     * matrices; the sums are integers (traces of pairs of generators) */
+    cx G[4][4];
+    qg_colour_init();
+    qg_gram(G);
+    for (int n = 0; n < 4; ++n)
+      for (int m = 0; m < 4; ++m) {
+        double r = round(creal(G[n][m]));
+        if (fabs(creal(G[n][m]) - r) > 1e-9 || fabs(cimag(G[n][m])) > 1e-9) return -1;
+        num[n * 4 + m] = (int64_t)r;
+        den[n * 4 + m] = 1;
+      }
+    return 0;
+  }
   if (PROCS[proc].kind == 2) {
     /* C_nm = sum over all colour indices of c_n c_m (the flow tensors are real, 0 or 1) */
     for (int n = 0; n < 2; ++n)
@@ -692,6 +722,277 @@ static double qq_colour_sum(cx A, cx* J) {
 }
 
 /* ------------------------------------------------------------------------- */
+/* q qbar -> t tbar g and its crossings: five Feynman diagrams, explicit colour */
+/* ------------------------------------------------------------------------- */
+/* The process has a light-quark line (its row end B_L -- vbar of an incoming antiquark
+ * or ubar of an outgoing quark -- and its column end K_L -- u of an incoming quark or v
+ * of an outgoing antiquark), the top line (ubar(p_t) ... v(p_tbar)) and one gluon of
+ * colour a.  With the rules of the gg processes (quark-gluon vertex -i g_s gamma^mu T^a,
+ * fermion propagator i(qslash + m)/(q^2 - m^2 + i m w) with q along the fermion arrow,
+ * gluon propagator -i g_{mu nu}/K^2, three-gluon vertex -g_s f^{abc} V^{mu nu rho}(k1,
+ * k2, k3) with all momenta incoming) the diagrams are, with L = B_L gamma K_L and
+ * H = ubar gamma v:
+ *   D1  gluon on the light line next to K_L:  i g^3 [B_L gamma^mu q1slash epsslash K_L]
+ *       H_mu / (q1^2 s_H),       colour (T^b T^a)_{B_L K_L} T^b_{t tbar}
+ *   D2  next to B_L:                          i g^3 [B_L epsslash q2slash gamma^mu K_L]
+ *       H_mu / (q2^2 s_H),       colour (T^a T^b)_{B_L K_L} T^b_{t tbar}
+ *   D3  on the top line next to the top:      i g^3 L_mu [ubar epsslash (q3slash + m)
+ *       gamma^mu v] / (D3 s_L),  colour T^b_{B_L K_L} (T^a T^b)_{t tbar}
+ *   D4  next to the antitop:                  i g^3 L_mu [ubar gamma^mu (q4slash + m)
+ *       epsslash v] / (D4 s_L),  colour T^b_{B_L K_L} (T^b T^a)_{t tbar}
+ *   D5  three-gluon vertex:  -g^3 V(L, k1; H, k2; eps, k3) / (s_L s_H),
+ *       colour f^{b c a} T^b_{B_L K_L} T^c_{t tbar}
+ * where P_i is the incoming momentum of particle i (+p incoming, -p outgoing),
+ * q1 = P_{K_L} + P_g, q2 = -(P_{B_L} + P_g), q3 = -(P_t + P_g), q4 = P_tbar + P_g,
+ * k1 = P_{B_L} + P_{K_L}, k2 = P_t + P_tbar, k3 = P_g, s_L = k1^2, s_H = k2^2 and
+ * V = (L.H)(k1-k2).eps + (H.eps)(k2-k3).L + (eps.L)(k3-k1).H.  |M|^2 is summed over all
+ * 3^4 x 8 colour assignments.  Colour flows (the basis of the selection weights):
+ *   c_0 = T^a_{B_L tbar} d_{t K_L},  c_1 = T^a_{t K_L} d_{B_L tbar},
+ *   c_2 = T^a_{B_L K_L} d_{t tbar},  c_3 = T^a_{t tbar} d_{B_L K_L}
+ * (indices: B_L, K_L, t, tbar colours; row index first). */
+#define Q3_NCOLIDX (NC * NC * NC * NC * 8)
+static cx QG_DCOL[5][Q3_NCOLIDX]; /* colour factor of each diagram per assignment */
+static cx QG_FLOW[4][Q3_NCOLIDX]; /* flow tensors per assignment */
+static int qg_colour_ready = 0;
+
+/* assignment index of (B_L, K_L, t, tbar, a) colours */
+static int qg_cidx(int bl, int kl, int t, int tb, int a) { return (((bl * NC + kl) * NC + t) * NC + tb) * 8 + a; }
+
+static void qg_colour_init(void) {
+  if (qg_colour_ready) return;
+  tgm_init();
+  /* f^{abc} = -2 i Tr([T^a, T^b] T^c), from [T^a, T^b] = i f^{abc} T^c and Tr(T^a T^b) = d^{ab}/2 */
+  static double F[8][8][8];
+  for (int a = 0; a < 8; ++a)
+    for (int b = 0; b < 8; ++b)
+      for (int c = 0; c < 8; ++c) {
+        cx tr = 0;
+        for (int i = 0; i < NC; ++i)
+          for (int j = 0; j < NC; ++j)
+            for (int k = 0; k < NC; ++k)
+              tr += (TGM[a][i][j] * TGM[b][j][k] - TGM[b][i][j] * TGM[a][j][k]) * TGM[c][k][i];
+        F[a][b][c] = creal(-2.0 * I * tr);
+      }
+  for (int bl = 0; bl < NC; ++bl)
+    for (int kl = 0; kl < NC; ++kl)
+      for (int t = 0; t < NC; ++t)
+        for (int tb = 0; tb < NC; ++tb)
+          for (int a = 0; a < 8; ++a) {
+            int x = qg_cidx(bl, kl, t, tb, a);
+            cx c[5] = {0, 0, 0, 0, 0};
+            for (int b = 0; b < 8; ++b) {
+              cx ba = 0, ab = 0, hab = 0, hba = 0; /* (T^b T^a), (T^a T^b) on each line */
+              for (int m = 0; m < NC; ++m) {
+                ba += TGM[b][bl][m] * TGM[a][m][kl];
+                ab += TGM[a][bl][m] * TGM[b][m][kl];
+                hab += TGM[a][t][m] * TGM[b][m][tb];
+                hba += TGM[b][t][m] * TGM[a][m][tb];
+              }
+              c[0] += ba * TGM[b][t][tb];
+              c[1] += ab * TGM[b][t][tb];
+              c[2] += TGM[b][bl][kl] * hab;
+              c[3] += TGM[b][bl][kl] * hba;
+              for (int cc = 0; cc < 8; ++cc) c[4] += F[b][cc][a] * TGM[b][bl][kl] * TGM[cc][t][tb];
+            }
+            for (int d = 0; d < 5; ++d) QG_DCOL[d][x] = c[d];
+            QG_FLOW[0][x] = TGM[a][bl][tb] * (double)(t == kl);
+            QG_FLOW[1][x] = TGM[a][t][kl] * (double)(bl == tb);
+            QG_FLOW[2][x] = TGM[a][bl][kl] * (double)(t == tb);
+            QG_FLOW[3][x] = TGM[a][t][tb] * (double)(bl == kl);
+          }
+  qg_colour_ready = 1;
+}
+
+/* Gram matrix of the flow tensors, G_nm = sum over assignments of conj(c_n) c_m */
+static void qg_gram(cx G[4][4]) {
+  for (int n = 0; n < 4; ++n)
+    for (int m = 0; m < 4; ++m) {
+      cx s = 0;
+      for (int x = 0; x < Q3_NCOLIDX; ++x) s += conj(QG_FLOW[n][x]) * QG_FLOW[m][x];
+      G[n][m] = s;
+    }
+}
+
+typedef struct {
+  int bl, kl, g, t, tb;    /* particle indices: light row end, light column end, gluon, top, antitop */
+  double den[4];           /* q1^2, q2^2, q3^2 - mt^2, q4^2 - mt^2 */
+  double sL, sH;           /* k1^2, k2^2 */
+  int tch3, tch4;          /* the top propagators of D3, D4 separate the incoming particles */
+} qg_kin;
+
+/* incoming momentum of particle i, as quads */
+static void qg_pin(const proc_def* pd, const double* mom, int i, quad* P) {
+  int in = pd->role[i] == R_Q_IN || pd->role[i] == R_QB_IN || pd->role[i] == R_G_IN;
+  for (int m = 0; m < 4; ++m) P[m] = in ? (quad)mom[4 * i + m] : -(quad)mom[4 * i + m];
+}
+
+/* roles and the propagator invariants of one event, formed in quadruple precision (as
+ * for the gg processes: exact sums of the FP64 inputs, one rounding at the end) */
+static void qg_kinematics(const proc_def* pd, const double* mom, double mt, qg_kin* k) {
+  k->bl = k->kl = k->g = k->t = k->tb = 0;
+  for (int i = 0; i < pd->npar; ++i) {
+    int r = pd->role[i];
+    if (r == R_QB_IN || r == R_Q_OUT) k->bl = i;
+    if (r == R_Q_IN || r == R_QB_OUT) k->kl = i;
+    if (r == R_G_IN || r == R_G_OUT) k->g = i;
+    if (r == R_T_OUT) k->t = i;
+    if (r == R_TBAR_OUT) k->tb = i;
+  }
+  quad Pbl[4], Pkl[4], Pg[4], Pt[4], Ptb[4], v[4];
+  qg_pin(pd, mom, k->bl, Pbl);
+  qg_pin(pd, mom, k->kl, Pkl);
+  qg_pin(pd, mom, k->g, Pg);
+  qg_pin(pd, mom, k->t, Pt);
+  qg_pin(pd, mom, k->tb, Ptb);
+  quad mt2 = (quad)mt * (quad)mt;
+  for (int m = 0; m < 4; ++m) v[m] = Pkl[m] + Pg[m];
+  k->den[0] = (double)msq_q(v);
+  for (int m = 0; m < 4; ++m) v[m] = -(Pbl[m] + Pg[m]);
+  k->den[1] = (double)msq_q(v);
+  for (int m = 0; m < 4; ++m) v[m] = -(Pt[m] + Pg[m]);
+  k->den[2] = (double)(msq_q(v) - mt2);
+  for (int m = 0; m < 4; ++m) v[m] = Ptb[m] + Pg[m];
+  k->den[3] = (double)(msq_q(v) - mt2);
+  for (int m = 0; m < 4; ++m) v[m] = Pbl[m] + Pkl[m];
+  k->sL = (double)msq_q(v);
+  for (int m = 0; m < 4; ++m) v[m] = Pt[m] + Ptb[m];
+  k->sH = (double)msq_q(v);
+  k->tch3 = is_tchannel((1u << k->t) | (1u << k->g));
+  k->tch4 = is_tchannel((1u << k->tb) | (1u << k->g));
+}
+
+/* the five diagrams' colour-stripped values A_d at one helicity */
+static void qg_diagrams(const double* mom, const int* lam, const proc_def* pd, const qg_kin* k, double gs,
+                        double mt, double wt, int zwt, int gauge_leg, cx* A) {
+  cx BL[4], KL[4], BH[4], KH[4], eps[4], tmp[4];
+  const double *pbl = mom + 4 * k->bl, *pkl = mom + 4 * k->kl, *pg = mom + 4 * k->g;
+  if (pd->role[k->bl] == R_QB_IN) { spinor_v(pbl, 0.0, lam[k->bl], tmp); dirac_bar(tmp, BL); }
+  else { spinor_u(pbl, 0.0, lam[k->bl], tmp); dirac_bar(tmp, BL); }
+  if (pd->role[k->kl] == R_Q_IN) spinor_u(pkl, 0.0, lam[k->kl], KL);
+  else spinor_v(pkl, 0.0, lam[k->kl], KL);
+  spinor_u(mom + 4 * k->t, mt, lam[k->t], tmp);
+  dirac_bar(tmp, BH);
+  spinor_v(mom + 4 * k->tb, mt, lam[k->tb], KH);
+  polvec(pg, lam[k->g], eps);
+  if (pd->role[k->g] == R_G_OUT)
+    for (int m = 0; m < 4; ++m) eps[m] = conj(eps[m]);
+  if (k->g == gauge_leg)
+    for (int m = 0; m < 4; ++m) eps[m] = pg[m] / pg[0];
+  /* incoming momenta (FP64) */
+  double P[MAXPAR][4];
+  for (int i = 0; i < pd->npar; ++i) {
+    int in = pd->role[i] == R_Q_IN || pd->role[i] == R_QB_IN || pd->role[i] == R_G_IN;
+    for (int m = 0; m < 4; ++m) P[i][m] = in ? mom[4 * i + m] : -mom[4 * i + m];
+  }
+  double q1[4], q2[4], q3[4], q4[4], k1[4], k2[4], k3[4];
+  for (int m = 0; m < 4; ++m) {
+    q1[m] = P[k->kl][m] + P[k->g][m];
+    q2[m] = -(P[k->bl][m] + P[k->g][m]);
+    q3[m] = -(P[k->t][m] + P[k->g][m]);
+    q4[m] = P[k->tb][m] + P[k->g][m];
+    k1[m] = P[k->bl][m] + P[k->kl][m];
+    k2[m] = P[k->t][m] + P[k->tb][m];
+    k3[m] = P[k->g][m];
+  }
+  cx E[4][4], S[4][4], x[4], y[4];
+  slash(eps, E);
+  cx L[4], H[4], L1[4], L2[4], H3[4], H4[4];
+  vector_current(BL, KL, 1.0, 1.0, L);
+  vector_current(BH, KH, 1.0, 1.0, H);
+  /* D1: B_L gamma^mu q1slash epsslash K_L */
+  {
+    cx qc[4] = {q1[0], q1[1], q1[2], q1[3]};
+    slash(qc, S);
+    for (int r = 0; r < 4; ++r) { x[r] = 0; for (int c = 0; c < 4; ++c) x[r] += E[r][c] * KL[c]; }
+    for (int r = 0; r < 4; ++r) { y[r] = 0; for (int c = 0; c < 4; ++c) y[r] += S[r][c] * x[c]; }
+    vector_current(BL, y, 1.0, 1.0, L1);
+  }
+  /* D2: B_L epsslash q2slash gamma^mu K_L */
+  {
+    cx qc[4] = {q2[0], q2[1], q2[2], q2[3]};
+    slash(qc, S);
+    bra_mat(BL, E, x);
+    bra_mat(x, S, y);
+    vector_current(y, KL, 1.0, 1.0, L2);
+  }
+  /* D3: ubar epsslash (q3slash + m) gamma^mu v */
+  {
+    cx qc[4] = {q3[0], q3[1], q3[2], q3[3]};
+    slash(qc, S);
+    for (int r = 0; r < 4; ++r) S[r][r] += mt;
+    bra_mat(BH, E, x);
+    bra_mat(x, S, y);
+    vector_current(y, KH, 1.0, 1.0, H3);
+  }
+  /* D4: ubar gamma^mu (q4slash + m) epsslash v */
+  {
+    cx qc[4] = {q4[0], q4[1], q4[2], q4[3]};
+    slash(qc, S);
+    for (int r = 0; r < 4; ++r) S[r][r] += mt;
+    for (int r = 0; r < 4; ++r) { x[r] = 0; for (int c = 0; c < 4; ++c) x[r] += E[r][c] * KH[c]; }
+    for (int r = 0; r < 4; ++r) { y[r] = 0; for (int c = 0; c < 4; ++c) y[r] += S[r][c] * x[c]; }
+    vector_current(BH, y, 1.0, 1.0, H4);
+  }
+  cx D3 = k->den[2] + I * mt * ((zwt && k->tch3) ? 0.0 : wt);
+  cx D4 = k->den[3] + I * mt * ((zwt && k->tch4) ? 0.0 : wt);
+  cx g3 = gs * gs * gs;
+  A[0] = I * g3 * mdot_c(L1, H) / (k->den[0] * k->sH);
+  A[1] = I * g3 * mdot_c(L2, H) / (k->den[1] * k->sH);
+  A[2] = I * g3 * mdot_c(L, H3) / (D3 * k->sL);
+  A[3] = I * g3 * mdot_c(L, H4) / (D4 * k->sL);
+  double d12[4], d23[4], d31[4];
+  for (int m = 0; m < 4; ++m) {
+    d12[m] = k1[m] - k2[m];
+    d23[m] = k2[m] - k3[m];
+    d31[m] = k3[m] - k1[m];
+  }
+  cx ed12 = eps[0] * d12[0] - eps[1] * d12[1] - eps[2] * d12[2] - eps[3] * d12[3];
+  cx ld23 = L[0] * d23[0] - L[1] * d23[1] - L[2] * d23[2] - L[3] * d23[3];
+  cx hd31 = H[0] * d31[0] - H[1] * d31[1] - H[2] * d31[2] - H[3] * d31[3];
+  cx V = mdot_c(L, H) * ed12 + mdot_c(H, eps) * ld23 + mdot_c(eps, L) * hd31;
+  A[4] = -g3 * V / (k->sL * k->sH);
+}
+
+/* explicit colour sum of |M|^2 at one helicity and the flow amplitudes J (M = sum_n J_n
+ * c_n, from the projections onto the flow tensors and their Gram matrix) */
+static double qg_colour_sum(const cx* A, const cx Ginv[4][4], cx* J) {
+  double m2 = 0;
+  cx Pr[4] = {0, 0, 0, 0};
+  for (int x = 0; x < Q3_NCOLIDX; ++x) {
+    cx M = 0;
+    for (int d = 0; d < 5; ++d) M += A[d] * QG_DCOL[d][x];
+    m2 += creal(M) * creal(M) + cimag(M) * cimag(M);
+    for (int n = 0; n < 4; ++n) Pr[n] += conj(QG_FLOW[n][x]) * M;
+  }
+  for (int n = 0; n < 4; ++n) {
+    J[n] = 0;
+    for (int m = 0; m < 4; ++m) J[n] += Ginv[n][m] * Pr[m];
+  }
+  return m2;
+}
+
+/* inverse of a 4 x 4 complex matrix by Gauss-Jordan elimination with partial pivoting */
+static void inv4(const cx G[4][4], cx Ginv[4][4]) {
+  cx a[4][8];
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 8; ++j) a[i][j] = j < 4 ? G[i][j] : (cx)(j - 4 == i);
+  for (int c = 0; c < 4; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < 4; ++r) if (cabs(a[r][c]) > cabs(a[piv][c])) piv = r;
+    for (int j = 0; j < 8; ++j) { cx t = a[c][j]; a[c][j] = a[piv][j]; a[piv][j] = t; }
+    cx d = a[c][c];
+    for (int j = 0; j < 8; ++j) a[c][j] /= d;
+    for (int r = 0; r < 4; ++r)
+      if (r != c) {
+        cx f = a[r][c];
+        for (int j = 0; j < 8; ++j) a[r][j] -= f * a[c][j];
+      }
+  }
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) Ginv[i][j] = a[i][4 + j];
+}
+
+/* ------------------------------------------------------------------------- */
 /* Driver                                                                     */
 /* ------------------------------------------------------------------------- */
 static int select_first_exceeding(const double* w, int n, double r) {
@@ -741,6 +1042,13 @@ int oracle_me(int proc, const oracle_params* par, int64_t nevt, const double* mo
   free(cd);
   int perms[MAXCOL][MAXG];
   for (int s = 0; s < ncol && n && pd->kind == 1; ++s) perm_unrank(n, s, perms[s]);
+  cx Ginv[4][4];
+  if (pd->kind == 3) {
+    cx G[4][4];
+    qg_colour_init();
+    qg_gram(G);
+    inv4(G, Ginv);
+  }
 
 #pragma omp parallel for schedule(dynamic, 4)
   for (int64_t e = 0; e < nevt; ++e) {
@@ -752,7 +1060,10 @@ int oracle_me(int proc, const oracle_params* par, int64_t nevt, const double* mo
     double as = alphas ? alphas[e] : par->alphas;
     double gs = sqrt(4.0 * M_PI * as);
     invariants inv;
+    qg_kin qk;
     if (pd->kind == 1) event_invariants(pd, p, par->mt, &inv);
+    memset(&qk, 0, sizeof qk);
+    if (pd->kind == 3) qg_kinematics(pd, p, par->mt, &qk);
     for (int h = 0; h < ncomb; ++h) {
       int lam[MAXPAR];
       for (int i = 0; i < npar; ++i) lam[i] = ((h >> (npar - 1 - i)) & 1) ? 1 : -1;
@@ -763,6 +1074,11 @@ int oracle_me(int proc, const oracle_params* par, int64_t nevt, const double* mo
         A[0] = amp_eemumu(p, lam, par, &sm);
       } else if (pd->kind == 2) {
         m2 = qq_colour_sum(amp_qqbar_tt(p, lam, pd, gs, par->mt), A);
+        explicit_colour = 1;
+      } else if (pd->kind == 3) {
+        cx D[5];
+        qg_diagrams(p, lam, pd, &qk, gs, par->mt, par->wt, par->zero_width_tchan, gauge_leg, D);
+        m2 = qg_colour_sum(D, Ginv, A);
         explicit_colour = 1;
       } else {
         qcd_ext x;

@@ -160,6 +160,12 @@ PROCESS_FINAL_MASSES = {
     "g g > t t~ g g g": lambda mt: (mt, mt, 0.0, 0.0, 0.0),
     "u u~ > t t~": lambda mt: (mt, mt),
     "u~ u > t t~": lambda mt: (mt, mt),
+    "u u~ > t t~ g": lambda mt: (mt, mt, 0.0),
+    "u~ u > t t~ g": lambda mt: (mt, mt, 0.0),
+    "u g > t t~ u": lambda mt: (mt, mt, 0.0),
+    "g u > t t~ u": lambda mt: (mt, mt, 0.0),
+    "u~ g > t t~ u~": lambda mt: (mt, mt, 0.0),
+    "g u~ > t t~ u~": lambda mt: (mt, mt, 0.0),
 }
 
 
