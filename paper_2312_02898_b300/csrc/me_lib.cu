@@ -31,12 +31,20 @@ extern const ProcessOps ops_ggttgg __attribute__((weak));
 extern const ProcessOps ops_ggttggg __attribute__((weak));
 extern const ProcessOps ops_qqtt __attribute__((weak));
 extern const ProcessOps ops_qxqtt __attribute__((weak));
+extern const ProcessOps ops_qqttg __attribute__((weak));
+extern const ProcessOps ops_qxqttg __attribute__((weak));
+extern const ProcessOps ops_qgttq __attribute__((weak));
+extern const ProcessOps ops_gqttq __attribute__((weak));
+extern const ProcessOps ops_qxgttqx __attribute__((weak));
+extern const ProcessOps ops_gqxttqx __attribute__((weak));
 }
 using namespace meb300;
 
 namespace {
 
-const ProcessOps* const kProcs[] = {&ops_eemumu, &ops_ggtt, &ops_ggttg, &ops_ggttgg, &ops_ggttggg, &ops_qqtt, &ops_qxqtt};
+const ProcessOps* const kProcs[] = {&ops_eemumu, &ops_ggtt,   &ops_ggttg,  &ops_ggttgg,  &ops_ggttggg,
+                                    &ops_qqtt,   &ops_qxqtt,  &ops_qqttg,  &ops_qxqttg,  &ops_qgttq,
+                                    &ops_gqttq,  &ops_qxgttqx, &ops_gqxttqx};
 
 thread_local std::string g_init_error;
 

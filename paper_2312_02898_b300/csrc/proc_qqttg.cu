@@ -1,0 +1,34 @@
+// Kernel instantiations and launch table for the process in generated/proc_qqttg.cuh
+// (u u~ > t t~ g, a one-jet quark channel of p p -> t t~ + jet): everything in registers, one
+// event per thread, in FP64 and FP32.
+#include "generated/proc_qqttg.cuh"
+#include "me_kernels.cuh"
+
+namespace meb300 {
+namespace {
+using P = proc_qqttg;
+template <int PREC, int C> struct Cfg;
+template <> struct Cfg<0, 0> { using R = double; using L = Layout<0, 128, 0, 0, 0, 0, 1>; };
+template <> struct Cfg<1, 0> { using R = float; using L = Layout<0, 128, 0, 0, 0, 0, 1>; };
+
+LaunchNeeds needs(int prec, int config) {
+  switch (prec * 8 + config) {
+    case 0: return needs_of<P, Cfg<0, 0>::R, Cfg<0, 0>::L>();
+    case 8: return needs_of<P, Cfg<1, 0>::R, Cfg<1, 0>::L>();
+    default: return LaunchNeeds{0, 0, 0, 0, false, 128, 1};
+  }
+}
+
+cudaError_t launch(int prec, int config, const MeLaunch& a, cudaStream_t s) {
+  switch (prec * 8 + config) {
+    case 0: return launch_me<P, Cfg<0, 0>::R, Cfg<0, 0>::L>(a, s);
+    case 8: return launch_me<P, Cfg<1, 0>::R, Cfg<1, 0>::L>(a, s);
+    default: return cudaErrorNotSupported;
+  }
+}
+}  // namespace
+
+extern const ProcessOps ops_qqttg = {P::NAME, P::NPAR, P::NCOMB, P::NCOL, P::NDIAG, P::NAMP, P::IDEN,
+                                   P::FLOPS_AMP, P::FLOPS_COL, /*has_mixed=*/false, {1, 1, 0, 0},
+                                   needs, launch};
+}  // namespace meb300

@@ -36,7 +36,15 @@ PROCESSES = {
     # the quark-initiated channel of p p -> t t~ (any light flavour; either beam order)
     "u u~ > t t~": dict(tag="qqtt", roles=("q_in", "qb_in", "t", "tb")),
     "u~ u > t t~": dict(tag="qxqtt", roles=("qb_in", "q_in", "t", "tb")),
+    # the one-jet quark channels of p p -> t t~ + jet (with g g -> t t~ g)
+    "u u~ > t t~ g": dict(tag="qqttg", roles=("q_in", "qb_in", "t", "tb", "g_out")),
+    "u~ u > t t~ g": dict(tag="qxqttg", roles=("qb_in", "q_in", "t", "tb", "g_out")),
+    "u g > t t~ u": dict(tag="qgttq", roles=("q_in", "g_in", "t", "tb", "q_out")),
+    "g u > t t~ u": dict(tag="gqttq", roles=("g_in", "q_in", "t", "tb", "q_out")),
+    "u~ g > t t~ u~": dict(tag="qxgttqx", roles=("qb_in", "g_in", "t", "tb", "qb_out")),
+    "g u~ > t t~ u~": dict(tag="gqxttqx", roles=("g_in", "qb_in", "t", "tb", "qb_out")),
 }
+QUARK_JET_TAGS = ("qqttg", "qxqttg", "qgttq", "gqttq", "qxgttqx", "gqxttqx")
 
 # jamps variants per process: (register budget, diagram-group size).  The budget is the
 # number of currents kept in registers (None: all); a group size splits the emission
@@ -639,7 +647,200 @@ class Emitter:
                      col_den=36, max_live=2)
         return "\n".join(out) + "\n", stats
 
+    # ------------------------------------------------------------------ q q~ -> t t~ g and crossings
+    def emit_quark_jet(self):
+        """One light-quark line, the top line and one gluon: q qbar -> t tbar g, q g ->
+        t tbar q, qbar g -> t tbar qbar.  Five diagrams (raw values r_d, no couplings):
+          D1  gluon on the light line next to its column end K:  (B g.. K current) . H / s_H
+          D2  next to its row end B,  D3/D4  on the top line next to the top / antitop
+              (light current . top-line current / s_L),
+          D5  the three-gluon vertex, eps . V3(L, k1; H, k2) / (s_L s_H);
+        with the quark-gluon vertex -i g_s gamma T^a, fermion propagators i(qslash + m)/D,
+        gluon propagators -i g/K^2 and the three-gluon vertex -g_s f^{abc} V, the amplitude
+        is g_s^3 (i (r1 c1 + ... + r4 c4) - r5 c5) with c_d the diagrams' colour tensors.
+        Each c_d is a fixed combination of four flow tensors (gen/colour.py); the flows are
+        carried scaled by 6, which makes every coefficient a Gaussian integer."""
+        roles = self.roles
+        ib = next(i for i, r in enumerate(roles) if r in ("qb_in", "q_out"))  # light row end
+        ik = next(i for i, r in enumerate(roles) if r in ("q_in", "qb_out"))  # light column end
+        ig = next(i for i, r in enumerate(roles) if r in ("g_in", "g_out"))
+        it, itb = roles.index("t"), roles.index("tb")
+
+        def P(i):
+            return [("+" if roles[i].endswith("_in") else "-", i)]
+
+        def neg(parts):
+            return [("-" if s == "+" else "+", i) for s, i in parts]
+
+        vecs = [("q1", P(ik) + P(ig)), ("q2", neg(P(ib) + P(ig))), ("q3", neg(P(it) + P(ig))),
+                ("q4", P(itb) + P(ig)), ("k1", P(ib) + P(ik)), ("k2", P(it) + P(itb))]
+        kix = {nm: self.npar + n for n, (nm, _) in enumerate(vecs)}
+        coef, gram = colmod.quark_jet_colour()
+        # gcd of the Gram matrix folded into the colour denominator (flows scaled by 6)
+        g = 0
+        for v in gram.flatten():
+            g = math.gcd(g, int(v))
+        cf = gram // g
+        cden = 36 // math.gcd(36, g)
+        cf = cf * (cden * g // 36) if (cden * g) % 36 == 0 else None
+        assert cf is not None
+        phases = [1j, 1j, 1j, 1j, -1]
+        fa = 4 * FLOPS["ext_u"] + FLOPS["ext_eps"] + 6 * FLOPS["pj"] + 2 * FLOPS["ket"] + 2 * FLOPS["bra"]
+        fa += 4 * FLOPS["dot"] + 5 * 2 + FLOPS["v3"]
+        pairs = 0
+        acc = []
+        for d in range(5):
+            ops = []
+            for c in range(4):
+                k = coef[d][c] * phases[d]
+                k = complex(round(k.real), round(k.imag))
+                if k == 0:
+                    continue
+                mag = int(abs(k.real) + abs(k.imag))
+                unit = k / mag
+                src = "a" if mag == 1 else f"a{mag}"
+                if unit == 1:
+                    ops.append(f"J[{c}] += {src};")
+                elif unit == -1:
+                    ops.append(f"J[{c}] -= {src};")
+                elif unit == 1j:
+                    ops.append(f"acc_pi(J[{c}], {src});")
+                elif unit == -1j:
+                    ops.append(f"acc_mi(J[{c}], {src});")
+                else:
+                    raise ValueError(k)
+                pairs += 1
+                fa += 2
+            mags = sorted({int(abs(complex(coef[d][c] * phases[d]).real) + abs(complex(coef[d][c] * phases[d]).imag))
+                           for c in range(4) if coef[d][c] != 0} - {1})
+            pre = "".join(f" const cx<R> a{m} = R({m}) * a;" for m in mags)
+            fa += 2 * len(mags)
+            acc.append(pre + " " + " ".join(ops))
+
+        def ext(i):
+            r = roles[i]
+            kt = f"(kt + {i} * S)"
+            if r == "q_in":
+                return f"ext_u<R>({kt}, R(0), lam[{i}], x{i});"
+            if r == "qb_in":
+                return f"ext_vbar<R>({kt}, R(0), lam[{i}], x{i});"
+            if r == "q_out":
+                return f"ext_ubar<R>({kt}, R(0), lam[{i}], x{i});"
+            if r == "qb_out":
+                return f"ext_v<R>({kt}, R(0), lam[{i}], x{i});"
+            if r in ("g_in", "g_out"):
+                return f"ext_eps<R>({kt}, lam[{i}], {'true' if r == 'g_out' else 'false'}, x{i});"
+            if r == "t":
+                return f"ext_ubar<R>({kt}, mt, lam[{i}], x{i});"
+            return f"ext_v<R>({kt}, mt, lam[{i}], x{i});"
+
+        K = lambda nm: f"(kt + {kix[nm]} * S)"
+        body = [f"  int lam[{self.npar}];",
+                f"  for (int i = 0; i < {self.npar}; ++i) lam[i] = ((h >> ({self.npar - 1} - i)) & 1) ? 1 : -1;",
+                "  " + " ".join(f"cx<R> x{i}[4];" for i in range(self.npar))]
+        body += ["  " + ext(i) for i in range(self.npar)]
+        body += ["  cx<R> L[4], H[4], w[4], c[4];",
+                 f"  pair_current<R>(x{ib}, x{ik}, L);",
+                 f"  pair_current<R>(x{it}, x{itb}, H);",
+                 f"  ket_step<R>(x{ig}, x{ik}, {K('q1')}, R(0), dt[0], w);  // D1",
+                 f"  pair_current<R>(x{ib}, w, c);",
+                 f"  {{ const cx<R> a = dg[1] * mdot(c, H);{acc[0]} }}",
+                 f"  bra_step<R>(x{ib}, x{ig}, {K('q2')}, R(0), dt[1], w);  // D2",
+                 f"  pair_current<R>(w, x{ik}, c);",
+                 f"  {{ const cx<R> a = dg[1] * mdot(c, H);{acc[1]} }}",
+                 f"  bra_step<R>(x{it}, x{ig}, {K('q3')}, mt, dt[2], w);  // D3",
+                 f"  pair_current<R>(w, x{itb}, c);",
+                 f"  {{ const cx<R> a = dg[0] * mdot(L, c);{acc[2]} }}",
+                 f"  ket_step<R>(x{ig}, x{itb}, {K('q4')}, mt, dt[3], w);  // D4",
+                 f"  pair_current<R>(x{it}, w, c);",
+                 f"  {{ const cx<R> a = dg[0] * mdot(L, c);{acc[3]} }}",
+                 f"  {{ const cx<R> a = dg[1] * close_v3<R>(x{ig}, L, {K('k1')}, H, {K('k2')}, dg[0]);{acc[4]} }}  // D5"]
+
+        # denominators, in FP64 from the FP64 momenta (error-free sums and squares in the
+        # FP64 mode), once per event
+        den = ["  using DD = dd_for<R>;", "  DD q[4];",
+               "  double kappa = 0.0;  // conditioning: max over light-line and gluon invariants of (sum E)^2 / |K^2|"]
+
+        def dd_sum(parts):
+            out = []
+            for mu in range(4):
+                s0, i0 = parts[0]
+                e = f"DD{{{'-' if s0 == '-' else ''}p[{i0}][{mu}], 0.0}}"
+                for sgn, i in parts[1:]:
+                    e = f"dd_add({e}, {'-' if sgn == '-' else ''}p[{i}][{mu}])"
+                out.append(f"  q[{mu}] = {e};")
+            return out
+
+        def esum(parts):
+            return " + ".join(f"p[{i}][0]" for _, i in parts)
+
+        vd = dict(vecs)
+        for slot, nm in ((0, "q1"), (1, "q2")):
+            den += dd_sum(vd[nm])
+            den.append(f"  {{ const double k2 = dd_invariant(q, 0.0), es = {esum(vd[nm])};")
+            den.append(f"    dt[{slot}] = mk<R>(R(1.0 / k2), R(0)); kappa = fmax(kappa, es * es / fabs(k2)); }}")
+        for slot, nm, other in ((2, "q3", it), (3, "q4", itb)):
+            mask = (1 << other) | (1 << ig)
+            tchan = (mask & 1) != ((mask >> 1) & 1)
+            den += dd_sum(vd[nm])
+            den.append(f"  {{ const double w = {'(zwt ? 0.0 : wt)' if tchan else 'wt'};")
+            den.append("    const double re = dd_invariant(q, mt);")
+            den.append("    const double im = mt * w, inv = 1.0 / (re * re + im * im);")
+            den.append(f"    dt[{slot}] = mk<R>(R(re * inv), R(-im * inv)); }}")
+        for slot, nm in ((0, "k1"), (1, "k2")):
+            den += dd_sum(vd[nm])
+            den.append(f"  {{ const double k2 = dd_invariant(q, 0.0), es = {esum(vd[nm])};")
+            den.append(f"    dg[{slot}] = R(1.0 / k2); kappa = fmax(kappa, es * es / fabs(k2)); }}")
+        den.append("  // momentum table: external momenta, then the vectors the vertices use")
+        den.append(f"  for (int i = 0; i < {self.npar}; ++i)")
+        den.append("    for (int m = 0; m < 4; ++m) kt[i * S + m] = R(p[i][m]);")
+        for nm, parts in vecs:
+            for mu in range(4):
+                den.append(f"  kt[{kix[nm]} * S + {mu}] = R({self._sum_expr(parts, mu)});")
+
+        cs, csflops = [], 0
+        for i in range(4):
+            tr = [f"{_lit(int(cf[i][j]) * (1 if j == i else 2))} * J[{j}].r" for j in range(i, 4) if cf[i][j]]
+            ti = [f"{_lit(int(cf[i][j]) * (1 if j == i else 2))} * J[{j}].i" for j in range(i, 4) if cf[i][j]]
+            csflops += 4 * len(tr) + 4
+            cs.append(f"  {{ const R tr = {' + '.join(tr)}; const R ti = {' + '.join(ti)};")
+            cs.append(f"    s = fmadd(J[{i}].r, tr, fmadd(J[{i}].i, ti, s)); }}")
+        iden = 4 * (9 if ig >= 2 else 24)
+        tag = self.tag
+        out = [f"// Generated by paper_2312_02898_b300/gen/emit.py for '{self.process}'. Do not edit.",
+               "#pragma once", '#include "../helas.cuh"', "namespace meb300 {", f"struct proc_{tag} {{",
+               f'static constexpr const char* NAME = "{self.process}";',
+               "// NGLUON counts the powers of g_s^2 in |M|^2 (three QCD vertices)",
+               f"static constexpr int NPAR = 5, NCOMB = 32, NCOL = 4, NDIAG = 5, NAMP = 5, NNODE = 6, IDEN = {iden}, NGLUON = 3;",
+               f"static constexpr int NDEN_G = 2, NDEN_T = 4, COL_DEN = {cden}, NCOLPAIR = {pairs}, MAX_LIVE = 4, NKVEC = {self.npar + len(vecs)};",
+               f"static constexpr long FLOPS_AMP = {fa}, FLOPS_COL = {csflops};",
+               "static constexpr bool QCD = true;",
+               "static constexpr bool CF_BF16_EXACT = true, CF_FP16_EXACT = true;",
+               "// dg[0] = 1/s_L, dg[1] = 1/s_H (the gluons off the light and the top line);",
+               "// dt[0], dt[1]: 1/q^2 of the light-quark propagators; dt[2], dt[3]: the top propagators",
+               "template <int S, class R, class DG, class DT, class KT>",
+               "static HD double precompute(const double (*p)[4], double mt, double wt, int zwt, DG& dg, DT& dt, KT kt) {"]
+        out += den
+        out += ["  return kappa;", "}",
+                "static constexpr int NVARIANT = 1;",
+                "static constexpr int NSLOT[1] = {0};",
+                "template <int V> static HD constexpr int nslot() { return 0; }",
+                "template <int V> static HD constexpr bool grouped() { return false; }",
+                "static constexpr int BUDGET[1] = {-1};",
+                "template <int V, int S, class R, int SYNC = 0, class DG, class DT, class JA>",
+                "static HD void jamps(int h, R mt, const DG& dg, const DT& dt, JA& J, cx<R>*, const R* kt) {"]
+        out += body
+        out += ["}", "template <class R, class JA>", "static HD R colour_sum(JA& J) {", "  R s = R(0);"] + cs
+        out += ["  return s;", "}", "};",
+                f"constexpr int proc_{tag}_CF[16] = {{{', '.join(str(int(x)) for x in cf.flatten())}}};",
+                "}  // namespace meb300"]
+        stats = dict(ndiag=5, namp=5, nnode=6, ncol=4, pairs=pairs, flops_amp=fa, flops_col=csflops, nden_g=2,
+                     nden_t=4, col_den=cden, max_live=4)
+        return "\n".join(out) + "\n", stats
+
     def emit(self):
+        if self.tag in QUARK_JET_TAGS:
+            return self.emit_quark_jet()
         if self.tag == "eemumu":
             return self.emit_eemumu()
         if self.tag in ("qqtt", "qxqtt"):
