@@ -464,7 +464,8 @@ def run_gpu(args):
             # the rest of the metric: every process at its own workload size, and the
             # serving stream in mixed precision beside the same stream in FP64
             line["processes"] = processes_table(args, peaks, reuse={PROCESS: (results, acc)})
-            line["dispatch"] = dispatch_table(args)
+            line["dispatch"] = dispatch_table(args, DISPATCH_CHANNELS)
+            line["dispatch_jet"] = dispatch_table(args, DISPATCH_JET_CHANNELS)
             line["serving"] = serving_table(args, quick=True)
         print(json.dumps(line), flush=True)
     if dist:
@@ -474,30 +475,36 @@ def run_gpu(args):
 
 # the per-process workloads: (process, events, alpha_s)
 PROCESS_TABLE = (("e+ e- > mu+ mu-", 16384, None), ("g g > t t~", 524288, 0.118), ("g g > t t~ g", 524288, 0.118),
-                 ("g g > t t~ g g", 1048576, "uniform"), ("g g > t t~ g g g", 262144, 0.118))
+                 ("g g > t t~ g g", 1048576, "uniform"), ("g g > t t~ g g g", 262144, 0.118),
+                 ("u u~ > t t~", 524288, 0.118), ("u u~ > t t~ g", 524288, 0.118), ("u g > t t~ u", 524288, 0.118))
 
 
 DISPATCH_CHANNELS = (("g g > t t~", 0.90), ("u u~ > t t~", 0.05), ("u~ u > t t~", 0.05))
+# p p -> t t~ + jet: g g -> t t~ g and the six quark channels (synthetic shares)
+DISPATCH_JET_CHANNELS = (("g g > t t~ g", 0.55), ("u u~ > t t~ g", 0.10), ("u~ u > t t~ g", 0.10),
+                         ("u g > t t~ u", 0.07), ("g u > t t~ u", 0.07), ("u~ g > t t~ u~", 0.055),
+                         ("g u~ > t t~ u~", 0.055))
 
 
-def dispatch_table(args, nevt=524288):
-    """p p -> t t~ with per-event channel dispatch (me_compute_channels): one batch of
-    2 -> 2 RAMBO events (massless beams, massive tops: valid for every channel), each
-    event assigned a channel with the fractions of DISPATCH_CHANNELS (synthetic, close to
-    the g g / q q~ shares of top-pair production at the LHC); ME/s of the mixed batch
-    beside the g g channel alone, and the error of each channel against its oracle."""
+def dispatch_table(args, channels, nevt=524288):
+    """p p -> t t~ (+ jet) with per-event channel dispatch (me_compute_channels): one
+    batch of RAMBO events (massless beams and jet, massive tops: valid for every channel
+    of the list), each event assigned a channel with the list's fractions (synthetic,
+    close to the g g / q q~ / q g shares of top-pair production at the LHC); ME/s of the
+    mixed batch beside the first (g g) channel alone, and the error of each channel
+    against its oracle."""
     import torch
     import oracle
     from paper_2312_02898_b300 import phasespace as ps
     from paper_2312_02898_b300.binding import MatrixElement, compute_channels
     mom, a, rh, rc = (torch.from_numpy(x).cuda() for x in
-                      ps.make_batch(DISPATCH_CHANNELS[0][0], nevt, seed=0, alphas="uniform"))
+                      ps.make_batch(channels[0][0], nevt, seed=0, alphas="uniform"))
     rng = np.random.default_rng(0)
-    ch_np = rng.choice(len(DISPATCH_CHANNELS), size=nevt, p=[f for _, f in DISPATCH_CHANNELS]).astype(np.int32)
+    ch_np = rng.choice(len(channels), size=nevt, p=[f for _, f in channels]).astype(np.int32)
     ch = torch.from_numpy(ch_np).cuda()
-    out = {"events": nevt, "channels": {p: float(f) for p, f in DISPATCH_CHANNELS}}
+    out = {"events": nevt, "channels": {p: float(f) for p, f in channels}}
     for prec in ("fp64", "fp32"):
-        hs = [MatrixElement(p, precision=prec) for p, _ in DISPATCH_CHANNELS]
+        hs = [MatrixElement(p, precision=prec) for p, _ in channels]
         res = (torch.empty(nevt, dtype=torch.float64, device="cuda"), torch.empty(nevt, dtype=torch.int32, device="cuda"),
                torch.empty(nevt, dtype=torch.int32, device="cuda"))
 
@@ -519,7 +526,7 @@ def dispatch_table(args, nevt=524288):
         torch.cuda.synchronize()
         got = res[0].cpu().numpy()
         errs = {}
-        for c, (p, _) in enumerate(DISPATCH_CHANNELS):
+        for c, (p, _) in enumerate(channels):
             idx = np.nonzero(ch_np == c)[0][:512]
             ref = oracle.me(p, mom[idx].cpu().numpy(), alphas=a[idx].cpu().numpy())["me"]
             errs[p] = float(np.max(np.abs(got[idx] / ref - 1)))

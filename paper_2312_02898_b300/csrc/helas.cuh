@@ -64,9 +64,27 @@ template <class R> HD void copy4(cx<R>* dst, const cx<R>* src) {
   for (int m = 0; m < 4; ++m) dst[m] = src[m];
 }
 
+// Sums of complex products as chains of real multiply-adds.  Written with the cx
+// operators, every complex product is rounded on its own and then added (two
+// multiplies, two multiply-adds and two adds for c + a b); as one chain each real part
+// of c + a b takes two multiply-adds, so a sum of n complex products costs 4n - 2
+// instructions instead of 6n - 2.  Negated operands are free in an FMA.
+template <class R> HD cx<R> cmul(cx<R> a, cx<R> b) { return mk<R>(fmadd(a.r, b.r, -(a.i * b.i)), fmadd(a.r, b.i, a.i * b.r)); }
+// c + a b
+template <class R> HD cx<R> cfma(cx<R> a, cx<R> b, cx<R> c) {
+  return mk<R>(fmadd(a.r, b.r, fmadd(-a.i, b.i, c.r)), fmadd(a.r, b.i, fmadd(a.i, b.r, c.i)));
+}
+// c - a b
+template <class R> HD cx<R> cfms(cx<R> a, cx<R> b, cx<R> c) {
+  return mk<R>(fmadd(-a.r, b.r, fmadd(a.i, b.i, c.r)), fmadd(-a.r, b.i, fmadd(-a.i, b.r, c.i)));
+}
+// c + s a and c - s a for real s
+template <class R> HD cx<R> rfma(R s, cx<R> a, cx<R> c) { return mk<R>(fmadd(s, a.r, c.r), fmadd(s, a.i, c.i)); }
+template <class R> HD cx<R> rfms(R s, cx<R> a, cx<R> c) { return mk<R>(fmadd(-s, a.r, c.r), fmadd(-s, a.i, c.i)); }
+
 // Minkowski product of two complex 4-vectors (bilinear, no conjugation)
 template <class R> HD cx<R> mdot(const cx<R>* a, const cx<R>* b) {
-  return a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
+  return cfms(a[3], b[3], cfms(a[2], b[2], cfms(a[1], b[1], cmul(a[0], b[0]))));
 }
 // Minkowski product of a real and a complex 4-vector
 template <class R> HD cx<R> mdot(const R* k, const cx<R>* a) {
@@ -227,55 +245,55 @@ HD void ext_eps(const R* k, int lam, bool outgoing, cx<R>* w) {
 // three-gluon vertex contracted with two currents X (momentum kx) and Y (ky):
 //   V3^rho = (X.Y)(kx - ky)^rho + Y^rho (kx + 2 ky).X - X^rho (2 kx + ky).Y
 // (all momenta incoming; the third leg carries q = -(kx + ky)).
+// (s scales the three scalar products, so that V3 / K^2 costs no extra pass)
 template <class R>
-HD void v3_raw(const cx<R>* X, const R* kx, const cx<R>* Y, const R* ky, cx<R>* out) {
+HD void v3_scaled(const cx<R>* X, const R* kx, const cx<R>* Y, const R* ky, R s, cx<R>* out) {
   R a[4], b[4], d[4];
 #pragma unroll
   for (int m = 0; m < 4; ++m) {
     d[m] = kx[m] - ky[m];
-    a[m] = kx[m] + R(2) * ky[m];
-    b[m] = R(2) * kx[m] + ky[m];
+    a[m] = fmadd(R(2), ky[m], kx[m]);
+    b[m] = fmadd(R(2), kx[m], ky[m]);
   }
-  const cx<R> xy = mdot(X, Y), ax = mdot(a, X), by = mdot(b, Y);
+  const cx<R> xy = s * mdot(X, Y), ax = s * mdot(a, X), by = s * mdot(b, Y);
 #pragma unroll
-  for (int m = 0; m < 4; ++m) out[m] = d[m] * xy + Y[m] * ax - X[m] * by;
+  for (int m = 0; m < 4; ++m) out[m] = cfms(X[m], by, cfma(Y[m], ax, d[m] * xy));
+}
+template <class R>
+HD void v3_raw(const cx<R>* X, const R* kx, const cx<R>* Y, const R* ky, cx<R>* out) {
+  v3_scaled(X, kx, Y, ky, R(1), out);
 }
 
 // off-shell gluon from a three-gluon vertex: V3 / K^2   (phase i)
 template <class R>
 HD void g3_current(const cx<R>* X, const R* kx, const cx<R>* Y, const R* ky, R invK2, cx<R>* out) {
-  v3_raw(X, kx, Y, ky, out);
-#pragma unroll
-  for (int m = 0; m < 4; ++m) out[m] = invK2 * out[m];
+  v3_scaled(X, kx, Y, ky, invK2, out);
 }
 
 // Lorentz structure s of the four-gluon vertex contracted with X, Y, Z (legs a, b, c):
 //   s=1 (f^abe f^cde): (X.Z) Y - (Y.Z) X
 //   s=2 (f^ace f^bde): (X.Y) Z - (Y.Z) X
 //   s=3 (f^ade f^bce): (X.Y) Z - (X.Z) Y
+// (s scales the two scalar products, as in v3_scaled)
+template <int S, class R>
+HD void v4_scaled(const cx<R>* X, const cx<R>* Y, const cx<R>* Z, R s, cx<R>* out) {
+  // out = u U - w W with (u, U, w, W) by structure
+  const cx<R>* U = S == 1 ? Y : Z;
+  const cx<R>* W = S == 3 ? Y : X;
+  const cx<R> u = s * (S == 1 ? mdot(X, Z) : mdot(X, Y));
+  const cx<R> w = s * (S == 3 ? mdot(X, Z) : mdot(Y, Z));
+#pragma unroll
+  for (int m = 0; m < 4; ++m) out[m] = cfms(w, W[m], cmul(u, U[m]));
+}
 template <int S, class R>
 HD void v4_raw(const cx<R>* X, const cx<R>* Y, const cx<R>* Z, cx<R>* out) {
-  if (S == 1) {
-    const cx<R> xz = mdot(X, Z), yz = mdot(Y, Z);
-#pragma unroll
-    for (int m = 0; m < 4; ++m) out[m] = xz * Y[m] - yz * X[m];
-  } else if (S == 2) {
-    const cx<R> xy = mdot(X, Y), yz = mdot(Y, Z);
-#pragma unroll
-    for (int m = 0; m < 4; ++m) out[m] = xy * Z[m] - yz * X[m];
-  } else {
-    const cx<R> xy = mdot(X, Y), xz = mdot(X, Z);
-#pragma unroll
-    for (int m = 0; m < 4; ++m) out[m] = xy * Z[m] - xz * Y[m];
-  }
+  v4_scaled<S>(X, Y, Z, R(1), out);
 }
 
 // off-shell gluon from a four-gluon structure: V4_s / K^2   (phase -1)
 template <int S, class R>
 HD void g4_current(const cx<R>* X, const cx<R>* Y, const cx<R>* Z, R invK2, cx<R>* out) {
-  v4_raw<S>(X, Y, Z, out);
-#pragma unroll
-  for (int m = 0; m < 4; ++m) out[m] = invK2 * out[m];
+  v4_scaled<S>(X, Y, Z, invK2, out);
 }
 
 // row spinor (a | b) times gamma.G, G contravariant:
@@ -285,10 +303,10 @@ HD void bra_gslash(const cx<R>* f, const cx<R>* G, cx<R>* o) {
   const cx<R> p03 = G[0] + G[3], m03 = G[0] - G[3];
   const cx<R> p12 = G[1] + times_i(G[2]), m12 = G[1] - times_i(G[2]);  // G1 +- i G2
   // G.sigmabar = [[G0+G3, G1-iG2], [G1+iG2, G0-G3]], G.sigma = [[G0-G3, -(G1-iG2)], [-(G1+iG2), G0+G3]]
-  o[0] = f[2] * p03 + f[3] * p12;
-  o[1] = f[2] * m12 + f[3] * m03;
-  o[2] = f[0] * m03 - f[1] * p12;
-  o[3] = f[1] * p03 - f[0] * m12;
+  o[0] = cfma(f[2], p03, cmul(f[3], p12));
+  o[1] = cfma(f[2], m12, cmul(f[3], m03));
+  o[2] = cfms(f[1], p12, cmul(f[0], m03));
+  o[3] = cfms(f[0], m12, cmul(f[1], p03));
 }
 
 // gamma.G times column spinor (l ; r) = (G.sigma r ; G.sigmabar l)
@@ -296,34 +314,45 @@ template <class R>
 HD void gslash_ket(const cx<R>* G, const cx<R>* f, cx<R>* o) {
   const cx<R> p03 = G[0] + G[3], m03 = G[0] - G[3];
   const cx<R> p12 = G[1] + times_i(G[2]), m12 = G[1] - times_i(G[2]);
-  o[0] = m03 * f[2] - m12 * f[3];
-  o[1] = p03 * f[3] - p12 * f[2];
-  o[2] = p03 * f[0] + m12 * f[1];
-  o[3] = p12 * f[0] + m03 * f[1];
+  o[0] = cfms(m12, f[3], cmul(m03, f[2]));
+  o[1] = cfms(p12, f[2], cmul(p03, f[3]));
+  o[2] = cfma(m12, f[1], cmul(p03, f[0]));
+  o[3] = cfma(m03, f[1], cmul(p12, f[0]));
 }
 
 // row spinor times (qslash + m), q real
 template <class R>
 HD void bra_prop(const cx<R>* c, const R* q, R m, cx<R>* o) {
   // (c|d) [[m, q.sigma], [q.sigmabar, m]] = (m c + d q.sigmabar | c q.sigma + m d)
-  const R p03 = q[0] + q[3], m03 = q[0] - q[3];
-  const cx<R> p12 = mk<R>(q[1], q[2]), m12 = mk<R>(q[1], -q[2]);
-  o[0] = m * c[0] + p03 * c[2] + c[3] * p12;
-  o[1] = m * c[1] + c[2] * m12 + m03 * c[3];
-  o[2] = m03 * c[0] - c[1] * p12 + m * c[2];
-  o[3] = p03 * c[1] - c[0] * m12 + m * c[3];
+  // with q1 +- i q2 written out: c (q1 + i q2) = (c.r q1 - c.i q2, c.i q1 + c.r q2)
+  const R p03 = q[0] + q[3], m03 = q[0] - q[3], q1 = q[1], q2 = q[2];
+  o[0] = mk<R>(fmadd(m, c[0].r, fmadd(p03, c[2].r, fmadd(c[3].r, q1, -(c[3].i * q2)))),
+               fmadd(m, c[0].i, fmadd(p03, c[2].i, fmadd(c[3].i, q1, c[3].r * q2))));
+  o[1] = mk<R>(fmadd(m, c[1].r, fmadd(m03, c[3].r, fmadd(c[2].r, q1, c[2].i * q2))),
+               fmadd(m, c[1].i, fmadd(m03, c[3].i, fmadd(c[2].i, q1, -(c[2].r * q2)))));
+  o[2] = mk<R>(fmadd(m, c[2].r, fmadd(m03, c[0].r, fmadd(-c[1].r, q1, c[1].i * q2))),
+               fmadd(m, c[2].i, fmadd(m03, c[0].i, fmadd(-c[1].i, q1, -(c[1].r * q2)))));
+  o[3] = mk<R>(fmadd(m, c[3].r, fmadd(p03, c[1].r, fmadd(-c[0].r, q1, -(c[0].i * q2)))),
+               fmadd(m, c[3].i, fmadd(p03, c[1].i, fmadd(-c[0].i, q1, c[0].r * q2))));
 }
 
 // (qslash + m) times column spinor, q real
 template <class R>
 HD void prop_ket(const R* q, R m, const cx<R>* c, cx<R>* o) {
   // [[m, q.sigma], [q.sigmabar, m]] (l ; r) = (m l + q.sigma r ; q.sigmabar l + m r)
-  const R p03 = q[0] + q[3], m03 = q[0] - q[3];
-  const cx<R> p12 = mk<R>(q[1], q[2]), m12 = mk<R>(q[1], -q[2]);
-  o[0] = m * c[0] + m03 * c[2] - m12 * c[3];
-  o[1] = m * c[1] + p03 * c[3] - p12 * c[2];
-  o[2] = p03 * c[0] + m12 * c[1] + m * c[2];
-  o[3] = p12 * c[0] + m03 * c[1] + m * c[3];
+  const R p03 = q[0] + q[3], m03 = q[0] - q[3], q1 = q[1], q2 = q[2];
+  // -(q1 - i q2) c3 = (-q1 c3.r - q2 c3.i, -q1 c3.i + q2 c3.r)
+  o[0] = mk<R>(fmadd(m, c[0].r, fmadd(m03, c[2].r, fmadd(-q1, c[3].r, -(q2 * c[3].i)))),
+               fmadd(m, c[0].i, fmadd(m03, c[2].i, fmadd(-q1, c[3].i, q2 * c[3].r))));
+  // -(q1 + i q2) c2 = (-q1 c2.r + q2 c2.i, -q1 c2.i - q2 c2.r)
+  o[1] = mk<R>(fmadd(m, c[1].r, fmadd(p03, c[3].r, fmadd(-q1, c[2].r, q2 * c[2].i))),
+               fmadd(m, c[1].i, fmadd(p03, c[3].i, fmadd(-q1, c[2].i, -(q2 * c[2].r)))));
+  // (q1 - i q2) c1 = (q1 c1.r + q2 c1.i, q1 c1.i - q2 c1.r)
+  o[2] = mk<R>(fmadd(m, c[2].r, fmadd(p03, c[0].r, fmadd(q1, c[1].r, q2 * c[1].i))),
+               fmadd(m, c[2].i, fmadd(p03, c[0].i, fmadd(q1, c[1].i, -(q2 * c[1].r)))));
+  // (q1 + i q2) c0 = (q1 c0.r - q2 c0.i, q1 c0.i + q2 c0.r)
+  o[3] = mk<R>(fmadd(m, c[3].r, fmadd(m03, c[1].r, fmadd(q1, c[0].r, -(q2 * c[0].i)))),
+               fmadd(m, c[3].i, fmadd(m03, c[1].i, fmadd(q1, c[0].i, q2 * c[0].r))));
 }
 
 // bra chain step: F (gamma.G) (qslash + m) / D       (phase +1)
@@ -350,12 +379,13 @@ HD void ket_step(const cx<R>* G, const cx<R>* F, const R* q, R m, cx<R> invD, cx
 // B = (a|b), K = (l;r)
 template <class R>
 HD void pair_current(const cx<R>* B, const cx<R>* K, cx<R>* j) {
-  const cx<R> a1r1 = B[0] * K[2], a2r2 = B[1] * K[3], a1r2 = B[0] * K[3], a2r1 = B[1] * K[2];
-  const cx<R> b1l1 = B[2] * K[0], b2l2 = B[3] * K[1], b1l2 = B[2] * K[1], b2l1 = B[3] * K[0];
-  j[0] = (a1r1 + a2r2) + (b1l1 + b2l2);
+  // j0 = s + t, j3 = s - t with s = a1r1 + b2l2, t = a2r2 + b1l1 (each one chain)
+  const cx<R> s = cfma(B[3], K[1], cmul(B[0], K[2])), t = cfma(B[2], K[0], cmul(B[1], K[3]));
+  j[0] = s + t;
+  j[3] = s - t;
+  const cx<R> a1r2 = cmul(B[0], K[3]), a2r1 = cmul(B[1], K[2]), b1l2 = cmul(B[2], K[1]), b2l1 = cmul(B[3], K[0]);
   j[1] = (a1r2 + a2r1) - (b1l2 + b2l1);
   j[2] = times_i((a2r1 - a1r2) - (b2l1 - b1l2));
-  j[3] = (a1r1 - a2r2) - (b1l1 - b2l2);
 }
 
 // chiral couplings: j^mu = B gamma^mu (cL P_L + cR P_R) K = cR a sigma^mu r + cL b sigmabar^mu l
@@ -384,9 +414,9 @@ HD cx<R> close_v3(const cx<R>* PJ, const cx<R>* X, const R* kx, const cx<R>* Y, 
 
 template <int S, class R>
 HD cx<R> close_v4(const cx<R>* PJ, const cx<R>* X, const cx<R>* Y, const cx<R>* Z, R invK2) {
-  if (S == 1) return invK2 * (mdot(X, Z) * mdot(Y, PJ) - mdot(Y, Z) * mdot(X, PJ));
-  if (S == 2) return invK2 * (mdot(X, Y) * mdot(Z, PJ) - mdot(Y, Z) * mdot(X, PJ));
-  return invK2 * (mdot(X, Y) * mdot(Z, PJ) - mdot(X, Z) * mdot(Y, PJ));
+  if (S == 1) return invK2 * cfms(mdot(Y, Z), mdot(X, PJ), cmul(mdot(X, Z), mdot(Y, PJ)));
+  if (S == 2) return invK2 * cfms(mdot(Y, Z), mdot(X, PJ), cmul(mdot(X, Y), mdot(Z, PJ)));
+  return invK2 * cfms(mdot(X, Z), mdot(Y, PJ), cmul(mdot(X, Y), mdot(Z, PJ)));
 }
 
 }  // namespace meb300

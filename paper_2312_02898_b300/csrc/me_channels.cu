@@ -4,8 +4,8 @@
 // quark-initiated q q~ -> t t~ in either beam order, routed per event).
 //
 // On the stream: the counts per channel are cleared, one kernel partitions the event
-// indices by channel into per-channel lists (one atomic per event; the order inside a
-// list does not matter, every event is evaluated on its own), and each channel's main
+// indices by channel into per-channel lists (one atomic per warp and channel; the order
+// inside a list does not matter, every event is evaluated on its own), and each channel's main
 // kernel then walks its list in indexed mode -- the mode the FP64 rescue pass uses --
 // reading that channel's count on the device, so the host never waits for the
 // partition.  Results land at the events' own positions.  An FP32 channel runs its FP64
@@ -28,15 +28,26 @@ namespace {
 
 constexpr int kMaxChannels = 16;
 
+// One atomic per warp and channel: the lanes of a warp that hold the same channel
+// (__match_any_sync) take consecutive list positions from one atomicAdd by their lowest
+// lane, instead of every event contending for the same few counters.
 __global__ void __launch_bounds__(256) partition_channels(int64_t nevt, const int32_t* __restrict__ channel, int nchan,
                                                           int* __restrict__ counts, int* __restrict__ lists,
                                                           double* __restrict__ me, int32_t* __restrict__ sel_hel,
                                                           int32_t* __restrict__ sel_col) {
   const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  const unsigned lane = threadIdx.x & 31u;
   for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < nevt; e += stride) {
     const int c = channel[e];
-    if (c >= 0 && c < nchan) {
-      const int pos = atomicAdd(counts + c, 1);
+    const bool valid = c >= 0 && c < nchan;
+    const unsigned active = __activemask();
+    const unsigned peers = __match_any_sync(active, valid ? c : -1);
+    if (valid) {
+      const int leader = __ffs(peers) - 1;
+      int base = 0;
+      if (int(lane) == leader) base = atomicAdd(counts + c, __popc(peers));
+      base = __shfl_sync(peers, base, leader);
+      const int pos = base + __popc(peers & ((1u << lane) - 1u));
       lists[int64_t(c) * nevt + pos] = int(e);
     } else {  // no such channel: the event gets NaN and selections 0
       me[e] = __longlong_as_double(0x7ff8000000000000ll);
