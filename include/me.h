@@ -22,13 +22,22 @@
  *   "g g > t t~ g g g"     1240 diagrams,          128 helicities, 120
  *   "u u~ > t t~"          1 diagram,               16 helicities,   2 (a light quark
  *   "u~ u > t t~"          from either beam: the quark-initiated channel of p p -> t t~)
+ *   "u u~ > t t~ g"        5 diagrams,              32 helicities,   4 (the one-jet quark
+ *   "u~ u > t t~ g"        channels of p p -> t t~ + jet, either beam order; with
+ *   "u g > t t~ u"         "g g > t t~ g" every channel of p p -> t t~ + 1 jet for one
+ *   "g u > t t~ u"         massless light flavour.  Colour flows over the colours of
+ *   "u~ g > t t~ u~"       the light line's row end B (incoming antiquark or outgoing
+ *   "g u~ > t t~ u~"       quark), column end K, top t, antitop tb and gluon a:
+ *                          T^a_{B tb} d_{t K}, T^a_{t K} d_{B tb}, T^a_{B K} d_{t tb},
+ *                          T^a_{t tb} d_{B K})
  *
  * Conventions:
  *   momenta   (E, px, py, pz) in GeV, FP64, array-of-structures [nevt][npar][4];
  *   helicity  index h in [0, 2^npar): particle i has helicity +1 if bit (npar-1-i) of h
  *             is set, else -1 (the physical helicity of that particle);
  *   colour    flow index = lexicographic rank of the gluon permutation s of the string
- *             (T^{a_s1} ... T^{a_sn})_{i_t j_tbar} (gluons named by particle index);
+ *             (T^{a_s1} ... T^{a_sn})_{i_t j_tbar} (gluons named by particle index) for
+ *             the gluon processes; the flows listed above for the quark channels;
  *   selection sel_hel = first kept helicity whose running sum of |M_h|^2 exceeds
  *             rnd_hel * total; sel_col = first flow whose running sum of
  *             w_i = sum_h |J_{h,i}|^2 exceeds rnd_col * sum_i w_i; both 0-based; an event
