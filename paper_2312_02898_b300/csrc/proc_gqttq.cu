@@ -1,7 +1,8 @@
 // Kernel instantiations and launch table for the process in generated/proc_gqttq.cuh
 // (g u > t t~ u, a one-jet quark channel of p p -> t t~ + jet): everything in registers, one
-// event per thread, in FP64 and FP32.
+// event per thread, in FP64, FP32 and double-float.
 #include "generated/proc_gqttq.cuh"
+#include "dfloat.cuh"
 #include "me_kernels.cuh"
 
 namespace meb300 {
@@ -16,6 +17,8 @@ template <> struct Cfg<0, 1> { using R = double; using L = Layout<0, 128, 1, 1, 
 template <> struct Cfg<1, 0> { using R = float; using L = Layout<0, 128, 0, 0, 0, 0, 1, 0, 4>; };
 template <> struct Cfg<1, 1> { using R = float; using L = Layout<0, 128, 0, 0, 0, 0, 1, 0, 3>; };
 template <> struct Cfg<1, 2> { using R = float; using L = Layout<0, 128, 0, 0, 0, 0, 1>; };
+// FP64-emulating double-float amplitudes: the FP64 default layout
+template <> struct Cfg<3, 0> { using R = dfloat; using L = Layout<0, 128, 0, 0, 0, 0, 1>; };
 
 LaunchNeeds needs(int prec, int config) {
   switch (prec * 8 + config) {
@@ -24,6 +27,7 @@ LaunchNeeds needs(int prec, int config) {
     case 8: return needs_of<P, Cfg<1, 0>::R, Cfg<1, 0>::L>();
     case 9: return needs_of<P, Cfg<1, 1>::R, Cfg<1, 1>::L>();
     case 10: return needs_of<P, Cfg<1, 2>::R, Cfg<1, 2>::L>();
+    case 24: return needs_of<P, Cfg<3, 0>::R, Cfg<3, 0>::L>();
     default: return LaunchNeeds{0, 0, 0, 0, false, 128, 1};
   }
 }
@@ -35,12 +39,13 @@ cudaError_t launch(int prec, int config, const MeLaunch& a, cudaStream_t s) {
     case 8: return launch_me<P, Cfg<1, 0>::R, Cfg<1, 0>::L>(a, s);
     case 9: return launch_me<P, Cfg<1, 1>::R, Cfg<1, 1>::L>(a, s);
     case 10: return launch_me<P, Cfg<1, 2>::R, Cfg<1, 2>::L>(a, s);
+    case 24: return launch_me<P, Cfg<3, 0>::R, Cfg<3, 0>::L>(a, s);
     default: return cudaErrorNotSupported;
   }
 }
 }  // namespace
 
 extern const ProcessOps ops_gqttq = {P::NAME, P::NPAR, P::NCOMB, P::NCOL, P::NDIAG, P::NAMP, P::IDEN,
-                                   P::FLOPS_AMP, P::FLOPS_COL, /*has_mixed=*/false, {2, 3, 0, 0},
+                                   P::FLOPS_AMP, P::FLOPS_COL, /*has_mixed=*/false, {2, 3, 0, 1},
                                    needs, launch};
 }  // namespace meb300
