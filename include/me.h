@@ -82,8 +82,8 @@ extern "C" {
 #define ME_PREC_DFLOAT 3 /* FP64-emulating amplitudes and colour sum in double-float arithmetic
                             (hi + lo FP32 pairs, about 48 significant bits, FP32 exponent range)
                             on the FP32 pipe; FP64 inputs, error-free invariants and helicity sum
-                            as in FP64 mode.  Built for "g g > t t~" and "g g > t t~ g";
-                            ME_ERR_MODE elsewhere */
+                            as in FP64 mode.  Built for "g g > t t~", "g g > t t~ g" and the
+                            six one-jet quark channels; ME_ERR_MODE elsewhere */
 
 typedef struct me_handle me_handle;
 
