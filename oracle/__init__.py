@@ -23,7 +23,12 @@ qbar g -> t tbar qbar, in either beam order) are pinned by gauge invariance, the
 soft-gluon limit with colour correlators from an explicit Gell-Mann sum, the
 initial-state collinear limits with the Altarelli-Parisi splitting functions (onto the
 closed-form-pinned q qbar -> t tbar and g g -> t tbar), charge conjugation, beam order,
-Lorentz invariance and their flow colour matrix.
+Lorentz invariance and their flow colour matrix.  The two-jet channels with one light
+line (q qbar -> t tbar g g, q g -> t tbar q g and its antiquark and beam-order crossings,
+g g -> t tbar q qbar) are pinned the same way: gauge invariance in each gluon, the soft
+limit onto q qbar -> t tbar g with colour correlators built from its flow amplitudes,
+initial-state collinear limits (P_qq, P_qg, P_gq, P_gg) onto the one-jet channels and
+g g -> t tbar g, Bose symmetry, charge conjugation, beam order and the 13-flow basis.
 """
 from __future__ import annotations
 
@@ -52,6 +57,13 @@ PROCESSES = (
     "g u > t t~ u",
     "u~ g > t t~ u~",
     "g u~ > t t~ u~",
+    "u u~ > t t~ g g",
+    "u~ u > t t~ g g",
+    "u g > t t~ u g",
+    "g u > t t~ u g",
+    "u~ g > t t~ u~ g",
+    "g u~ > t t~ u~ g",
+    "g g > t t~ u u~",
 )
 
 

@@ -32,7 +32,10 @@
  * coefficients of the amplitude on the two flow tensors (a 2 x 2 Gram system).  Its
  * one-jet crossings (q qbar -> t tbar g, q g -> t tbar q, qbar g -> t tbar qbar) are the
  * five Feynman diagrams of one light-quark line, the top line and one gluon, summed the
- * same way over all 648 colour assignments and projected onto four flow tensors.
+ * same way over all 648 colour assignments and projected onto four flow tensors.  The
+ * two-jet channels with one light line (q qbar -> t tbar g g and crossings) are their 36
+ * Feynman diagrams (38 terms), summed over all 5184 colour assignments and projected
+ * onto 13 flow tensors.
  *
  * Conventions shared with the product only through their published definitions:
  *   * momenta [nevt][npar][4] = (E, px, py, pz); particle order of the process string;
@@ -54,7 +57,7 @@
 
 typedef double complex cx;
 
-#define NPROC 13
+#define NPROC 20
 #define MAXPAR 7
 #define MAXG 5
 #define MAXCOL 120
@@ -70,7 +73,8 @@ enum { R_EBAR_IN, R_E_IN, R_MUBAR_OUT, R_MU_OUT, R_G_IN, R_G_OUT, R_T_OUT, R_TBA
 
 /* kind: 0 e+ e- -> mu+ mu-; 1 g g -> t tbar + gluons (Berends-Giele); 2 q qbar -> t tbar
  * (explicit colour); 3 q qbar -> t tbar g and its crossings with one light quark line, a
- * top line and one gluon (explicit colour, five Feynman diagrams) */
+ * top line and one gluon (explicit colour, five Feynman diagrams); 4 the same with two
+ * gluons (explicit colour, 36 Feynman diagrams) */
 typedef struct {
   const char* name;
   int npar;
@@ -98,6 +102,14 @@ static const proc_def PROCS[NPROC] = {
     {"g u > t t~ u", 5, 0, 96, {R_G_IN, R_Q_IN, R_T_OUT, R_TBAR_OUT, R_Q_OUT}, 3, 4},
     {"u~ g > t t~ u~", 5, 0, 96, {R_QB_IN, R_G_IN, R_T_OUT, R_TBAR_OUT, R_QB_OUT}, 3, 4},
     {"g u~ > t t~ u~", 5, 0, 96, {R_G_IN, R_QB_IN, R_T_OUT, R_TBAR_OUT, R_QB_OUT}, 3, 4},
+    /* two extra partons: IDEN = 4 x 9 x 2! (two final gluons), 4 x 3 x 8 (q g), 4 x 64 (g g) */
+    {"u u~ > t t~ g g", 6, 0, 72, {R_Q_IN, R_QB_IN, R_T_OUT, R_TBAR_OUT, R_G_OUT, R_G_OUT}, 4, 13},
+    {"u~ u > t t~ g g", 6, 0, 72, {R_QB_IN, R_Q_IN, R_T_OUT, R_TBAR_OUT, R_G_OUT, R_G_OUT}, 4, 13},
+    {"u g > t t~ u g", 6, 0, 96, {R_Q_IN, R_G_IN, R_T_OUT, R_TBAR_OUT, R_Q_OUT, R_G_OUT}, 4, 13},
+    {"g u > t t~ u g", 6, 0, 96, {R_G_IN, R_Q_IN, R_T_OUT, R_TBAR_OUT, R_Q_OUT, R_G_OUT}, 4, 13},
+    {"u~ g > t t~ u~ g", 6, 0, 96, {R_QB_IN, R_G_IN, R_T_OUT, R_TBAR_OUT, R_QB_OUT, R_G_OUT}, 4, 13},
+    {"g u~ > t t~ u~ g", 6, 0, 96, {R_G_IN, R_QB_IN, R_T_OUT, R_TBAR_OUT, R_QB_OUT, R_G_OUT}, 4, 13},
+    {"g g > t t~ u u~", 6, 0, 256, {R_G_IN, R_G_IN, R_T_OUT, R_TBAR_OUT, R_Q_OUT, R_QB_OUT}, 4, 13},
 };
 
 static int factorial(int n) { return n <= 1 ? 1 : n * factorial(n - 1); }
@@ -234,9 +246,27 @@ static double qq_flow_tensor(int n, int i, int j, int k, int l);
 
 static void qg_colour_init(void);
 static void qg_gram(cx G[4][4]);
+static void q4_colour_init(void);
+static void q4_gram(cx* G);
 
 int oracle_colour_matrix_exact(int proc, int64_t* num, int64_t* den) {
   if (proc < 0 || proc >= NPROC) return -1;
+  if (PROCS[proc].kind == 4) {
+    /* C_nm = sum over all colour assignments of conj(c_n) c_m, explicit Gell-Mann sums;
+     * the entries are multiples of 1/3 */
+    cx G[13 * 13];
+    q4_colour_init();
+    q4_gram(G);
+    for (int i = 0; i < 13 * 13; ++i) {
+      double r = round(creal(G[i]) * 3.0);
+      if (fabs(creal(G[i]) * 3.0 - r) > 1e-8 || fabs(cimag(G[i])) > 1e-8) return -1;
+      int64_t nn = (int64_t)r, dd = 3;
+      if (nn % 3 == 0) { nn /= 3; dd = 1; }
+      num[i] = nn;
+      den[i] = dd;
+    }
+    return 0;
+  }
   if (PROCS[proc].kind == 3) {
     /* C_nm = sum over all colour assignments of conj(c_n) c_m, with explicit Gell-Mann
      * matrices; the sums are integers (traces of pairs of generators) */
@@ -993,6 +1023,451 @@ static void inv4(const cx G[4][4], cx Ginv[4][4]) {
 }
 
 /* ------------------------------------------------------------------------- */
+/* One light-quark line, the top line and two gluons (kind 4): q qbar -> t tbar g g and its
+ * crossings, explicit colour                                                   */
+/* ------------------------------------------------------------------------- */
+/* The Feynman diagrams are built from three kinds of objects: gluon a and gluon b (a is
+ * the one with the lower particle index) and the pair a b joined by a three-gluon vertex
+ * into one off-shell gluon.  Each object hangs on the light line, on the top line or on
+ * the gluon that joins the two lines (the connector); every order of the objects and of
+ * the connector's end ("stub") along each line gives one diagram.  The connector is one
+ * propagator (no object on it), a three-gluon vertex with one object, two three-gluon
+ * vertices with a and b in either order, or the four-gluon vertex, whose three
+ * colour-Lorentz structures are kept as three terms.  For two separate gluons this
+ * gives 6 + 6 + 8 + 4 + 4 + 3 diagrams (both on the light line, both on the top line,
+ * one on each, one on the connector and the other on either line, both on the
+ * connector) and for the joined pair 2 + 2 + 1 (on either line or on the connector):
+ * 36 diagrams, 38 terms.
+ * Feynman rules as for the other QCD processes: quark-gluon vertex -i g gamma^mu T^x,
+ * fermion propagator i(qslash + m)/(q^2 - m^2 + i m w) with q along the fermion arrow,
+ * gluon propagator -i g_{mu nu}/K^2, three-gluon vertex -g f^{xyz} V^{mu nu rho}(k1, k2,
+ * k3) (all momenta incoming), four-gluon vertex -i g^2 [f^{x y e} f^{z w e} (g^{mu rho}
+ * g^{nu sigma} - g^{mu sigma} g^{nu rho}) + f^{x z e} f^{y w e} (g^{mu nu} g^{rho sigma} -
+ * g^{mu sigma} g^{nu rho}) + f^{x w e} f^{y z e} (g^{mu nu} g^{rho sigma} - g^{mu rho}
+ * g^{nu sigma})] for legs (x mu) (y nu) (z rho) (w sigma).
+ * Colour flows (indices: light row end B, light column end K, top t, antitop y, gluons
+ * a b; 13 independent tensors, the fourteenth string product being a combination of
+ * these):
+ *   0 (T^a T^b)_{B y} d_{t K}   1 (T^b T^a)_{B y} d_{t K}   2 T^a_{B y} T^b_{t K}
+ *   3 T^b_{B y} T^a_{t K}       4 d_{B y} (T^a T^b)_{t K}   5 d_{B y} (T^b T^a)_{t K}
+ *   6 (T^a T^b)_{B K} d_{t y}   7 (T^b T^a)_{B K} d_{t y}   8 T^a_{B K} T^b_{t y}
+ *   9 T^b_{B K} T^a_{t y}       10 d_{B K} (T^a T^b)_{t y}  11 d_{B K} (T^b T^a)_{t y}
+ *   12 d^{ab} d_{B y} d_{t K} */
+#define Q4_NCI (NC * NC * NC * NC * 64)
+#define Q4_NFLOW 13
+#define Q4_MAXTERM 40
+enum { Q4_A = 0, Q4_B = 1, Q4_AB = 2, Q4_STUB = 3 };
+
+typedef struct {
+  int nl, nh;  /* insertions on the light line (from its row end) and on the top line (from the top), stub included */
+  int l[3], h[3];
+  int conn;    /* 0 one propagator; 1, 2, 3 a three-gluon vertex with object a, b, ab;
+                  4 a then b from the light side; 5 b then a; 6, 7, 8 four-gluon structure 1, 2, 3 */
+} q4_term;
+
+static q4_term Q4_TERMS[Q4_MAXTERM];
+static int q4_nterm = 0;
+static cx* Q4_DCOL = 0;            /* [term][Q4_NCI] */
+static cx Q4_FLOW[Q4_NFLOW][Q4_NCI];
+static double Q4_F[8][8][8];
+static int q4_ready = 0;
+
+/* colour assignment index of (B, K, t, y, a, b) */
+static int q4_cidx(int B, int K, int t, int y, int a, int b) { return ((((B * NC + K) * NC + t) * NC + y) * 8 + a) * 8 + b; }
+
+/* every order of the n items (n <= 3) */
+static int q4_perms(const int* items, int n, int out[6][3]) {
+  int np = 0;
+  if (n == 1) { out[0][0] = items[0]; return 1; }
+  for (int i = 0; i < n; ++i) {
+    int rest[2], nr = 0;
+    for (int j = 0; j < n; ++j) if (j != i) rest[nr++] = items[j];
+    int sub[6][3];
+    int ns = q4_perms(rest, n - 1, sub);
+    for (int s = 0; s < ns; ++s) {
+      out[np][0] = items[i];
+      for (int j = 0; j < n - 1; ++j) out[np][j + 1] = sub[s][j];
+      ++np;
+    }
+  }
+  return np;
+}
+
+static void q4_enumerate(void) {
+  q4_nterm = 0;
+  for (int joined = 0; joined < 2; ++joined) {
+    int nobj = joined ? 1 : 2;
+    int obj[2] = {joined ? Q4_AB : Q4_A, Q4_B};
+    for (int pa = 0; pa < 3; ++pa)
+      for (int pb = 0; pb < (joined ? 1 : 3); ++pb) {
+        int place[2] = {pa, pb};
+        int li[3], hi[3], ci[2], nl = 0, nh = 0, nc = 0;
+        for (int o = 0; o < nobj; ++o) {
+          if (place[o] == 0) li[nl++] = obj[o];
+          else if (place[o] == 1) hi[nh++] = obj[o];
+          else ci[nc++] = obj[o];
+        }
+        li[nl++] = Q4_STUB;
+        hi[nh++] = Q4_STUB;
+        int conns[5], ncon = 0;
+        if (nc == 0) conns[ncon++] = 0;
+        else if (nc == 1) conns[ncon++] = 1 + ci[0];
+        else { conns[0] = 4; conns[1] = 5; conns[2] = 6; conns[3] = 7; conns[4] = 8; ncon = 5; }
+        int lp[6][3], hp[6][3];
+        int nlp = q4_perms(li, nl, lp), nhp = q4_perms(hi, nh, hp);
+        for (int x = 0; x < nlp; ++x)
+          for (int y = 0; y < nhp; ++y)
+            for (int c = 0; c < ncon; ++c) {
+              q4_term* t = &Q4_TERMS[q4_nterm++];
+              t->nl = nl;
+              t->nh = nh;
+              for (int j = 0; j < nl; ++j) t->l[j] = lp[x][j];
+              for (int j = 0; j < nh; ++j) t->h[j] = hp[y][j];
+              t->conn = conns[c];
+            }
+      }
+  }
+}
+
+/* 3 x 3 colour matrix of one insertion: object a, b, the joined pair (colour e), the stub (colour c) */
+static void q4_mat(int o, int a, int b, int c, int e, cx m[NC][NC]) {
+  int x = o == Q4_A ? a : o == Q4_B ? b : o == Q4_AB ? e : c;
+  for (int i = 0; i < NC; ++i)
+    for (int j = 0; j < NC; ++j) m[i][j] = TGM[x][i][j];
+}
+
+static void q4_string(const int* items, int n, int a, int b, int c, int e, cx out[NC][NC]) {
+  cx acc[NC][NC], m[NC][NC], t[NC][NC];
+  q4_mat(items[0], a, b, c, e, acc);
+  for (int k = 1; k < n; ++k) {
+    q4_mat(items[k], a, b, c, e, m);
+    for (int i = 0; i < NC; ++i)
+      for (int j = 0; j < NC; ++j) {
+        cx s = 0;
+        for (int l = 0; l < NC; ++l) s += acc[i][l] * m[l][j];
+        t[i][j] = s;
+      }
+    memcpy(acc, t, sizeof acc);
+  }
+  memcpy(out, acc, sizeof acc);
+}
+
+/* connector colour (with f^{abe} of a joined pair on either line); c1 the light stub,
+ * c2 the top stub, e the internal gluon */
+static double q4_conn_colour(const q4_term* t, int a, int b, int c1, int c2, int e) {
+  int joined = 0;
+  for (int j = 0; j < t->nl; ++j) joined |= t->l[j] == Q4_AB;
+  for (int j = 0; j < t->nh; ++j) joined |= t->h[j] == Q4_AB;
+  double f = joined ? Q4_F[a][b][e] : 1.0;
+  switch (t->conn) {
+    case 0: return joined ? f * (c1 == c2) : (double)(c1 == c2) * (e == 0);
+    case 1: return Q4_F[c1][a][c2] * (e == 0);
+    case 2: return Q4_F[c1][b][c2] * (e == 0);
+    case 3: return Q4_F[c1][e][c2] * Q4_F[a][b][e];
+    case 4: return Q4_F[c1][a][e] * Q4_F[e][b][c2];
+    case 5: return Q4_F[c1][b][e] * Q4_F[e][a][c2];
+    case 6: return Q4_F[c1][a][e] * Q4_F[b][c2][e];
+    case 7: return Q4_F[c1][b][e] * Q4_F[a][c2][e];
+    default: return Q4_F[c1][c2][e] * Q4_F[a][b][e];
+  }
+}
+
+static void q4_colour_init(void) {
+  if (q4_ready) return;
+  tgm_init();
+  for (int a = 0; a < 8; ++a)
+    for (int b = 0; b < 8; ++b)
+      for (int c = 0; c < 8; ++c) {
+        cx tr = 0;
+        for (int i = 0; i < NC; ++i)
+          for (int j = 0; j < NC; ++j)
+            for (int k = 0; k < NC; ++k)
+              tr += (TGM[a][i][j] * TGM[b][j][k] - TGM[b][i][j] * TGM[a][j][k]) * TGM[c][k][i];
+        Q4_F[a][b][c] = creal(-2.0 * I * tr);
+      }
+  q4_enumerate();
+  Q4_DCOL = (cx*)calloc((size_t)q4_nterm * Q4_NCI, sizeof(cx));
+  for (int d = 0; d < q4_nterm; ++d) {
+    const q4_term* t = &Q4_TERMS[d];
+    for (int a = 0; a < 8; ++a)
+      for (int b = 0; b < 8; ++b)
+        for (int c1 = 0; c1 < 8; ++c1)
+          for (int c2 = 0; c2 < 8; ++c2)
+            for (int e = 0; e < 8; ++e) {
+              double w = q4_conn_colour(t, a, b, c1, c2, e);
+              if (w == 0.0) continue;
+              cx L[NC][NC], H[NC][NC];
+              q4_string(t->l, t->nl, a, b, c1, e, L);
+              q4_string(t->h, t->nh, a, b, c2, e, H);
+              for (int B = 0; B < NC; ++B)
+                for (int K = 0; K < NC; ++K)
+                  for (int tt = 0; tt < NC; ++tt)
+                    for (int y = 0; y < NC; ++y) Q4_DCOL[(size_t)d * Q4_NCI + q4_cidx(B, K, tt, y, a, b)] += w * L[B][K] * H[tt][y];
+            }
+  }
+  for (int B = 0; B < NC; ++B)
+    for (int K = 0; K < NC; ++K)
+      for (int t = 0; t < NC; ++t)
+        for (int y = 0; y < NC; ++y)
+          for (int a = 0; a < 8; ++a)
+            for (int b = 0; b < 8; ++b) {
+              int x = q4_cidx(B, K, t, y, a, b);
+              cx ab_By = 0, ba_By = 0, ab_tK = 0, ba_tK = 0, ab_BK = 0, ba_BK = 0, ab_ty = 0, ba_ty = 0;
+              for (int m = 0; m < NC; ++m) {
+                ab_By += TGM[a][B][m] * TGM[b][m][y];
+                ba_By += TGM[b][B][m] * TGM[a][m][y];
+                ab_tK += TGM[a][t][m] * TGM[b][m][K];
+                ba_tK += TGM[b][t][m] * TGM[a][m][K];
+                ab_BK += TGM[a][B][m] * TGM[b][m][K];
+                ba_BK += TGM[b][B][m] * TGM[a][m][K];
+                ab_ty += TGM[a][t][m] * TGM[b][m][y];
+                ba_ty += TGM[b][t][m] * TGM[a][m][y];
+              }
+              double dtK = t == K, dBy = B == y, dBK = B == K, dty = t == y;
+              Q4_FLOW[0][x] = ab_By * dtK;
+              Q4_FLOW[1][x] = ba_By * dtK;
+              Q4_FLOW[2][x] = TGM[a][B][y] * TGM[b][t][K];
+              Q4_FLOW[3][x] = TGM[b][B][y] * TGM[a][t][K];
+              Q4_FLOW[4][x] = dBy * ab_tK;
+              Q4_FLOW[5][x] = dBy * ba_tK;
+              Q4_FLOW[6][x] = ab_BK * dty;
+              Q4_FLOW[7][x] = ba_BK * dty;
+              Q4_FLOW[8][x] = TGM[a][B][K] * TGM[b][t][y];
+              Q4_FLOW[9][x] = TGM[b][B][K] * TGM[a][t][y];
+              Q4_FLOW[10][x] = dBK * ab_ty;
+              Q4_FLOW[11][x] = dBK * ba_ty;
+              Q4_FLOW[12][x] = (double)(a == b) * dBy * dtK;
+            }
+  q4_ready = 1;
+}
+
+/* inverse of an n x n complex matrix (n <= MAXFLOWINV) by Gauss-Jordan elimination with
+ * partial pivoting */
+#define MAXFLOWINV 16
+static void invn(int n, const cx* G, cx* Ginv) {
+  cx a[MAXFLOWINV][2 * MAXFLOWINV];
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < 2 * n; ++j) a[i][j] = j < n ? G[i * n + j] : (cx)(j - n == i);
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r) if (cabs(a[r][c]) > cabs(a[piv][c])) piv = r;
+    for (int j = 0; j < 2 * n; ++j) { cx t = a[c][j]; a[c][j] = a[piv][j]; a[piv][j] = t; }
+    cx dv = a[c][c];
+    for (int j = 0; j < 2 * n; ++j) a[c][j] /= dv;
+    for (int r = 0; r < n; ++r)
+      if (r != c) {
+        cx f = a[r][c];
+        for (int j = 0; j < 2 * n; ++j) a[r][j] -= f * a[c][j];
+      }
+  }
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) Ginv[i * n + j] = a[i][n + j];
+}
+
+static void q4_gram(cx* G) {
+  for (int n = 0; n < Q4_NFLOW; ++n)
+    for (int m = 0; m < Q4_NFLOW; ++m) {
+      cx s = 0;
+      for (int x = 0; x < Q4_NCI; ++x) s += conj(Q4_FLOW[n][x]) * Q4_FLOW[m][x];
+      G[n * Q4_NFLOW + m] = s;
+    }
+}
+
+typedef struct {
+  int bl, kl, t, tb, ga, gb;       /* particle indices */
+  double inv[1 << MAXPAR];         /* (sum over the mask of the incoming momenta)^2, formed in quad */
+} q4_kin;
+
+static int q4_in(int r) { return r == R_Q_IN || r == R_QB_IN || r == R_G_IN; }
+
+static void q4_kinematics(const proc_def* pd, const double* mom, q4_kin* k) {
+  int ng = 0;
+  k->bl = k->kl = k->t = k->tb = k->ga = k->gb = 0;
+  for (int i = 0; i < pd->npar; ++i) {
+    int r = pd->role[i];
+    if (r == R_QB_IN || r == R_Q_OUT) k->bl = i;
+    if (r == R_Q_IN || r == R_QB_OUT) k->kl = i;
+    if (r == R_T_OUT) k->t = i;
+    if (r == R_TBAR_OUT) k->tb = i;
+    if (r == R_G_IN || r == R_G_OUT) { if (ng++ == 0) k->ga = i; else k->gb = i; }
+  }
+  for (unsigned mask = 0; mask < (1u << pd->npar); ++mask) {
+    quad K[4] = {0, 0, 0, 0};
+    for (int i = 0; i < pd->npar; ++i)
+      if (mask >> i & 1)
+        for (int m = 0; m < 4; ++m) K[m] += q4_in(pd->role[i]) ? (quad)mom[4 * i + m] : -(quad)mom[4 * i + m];
+    k->inv[mask] = (double)msq_q(K);
+  }
+}
+
+/* the wavefunction, incoming momentum and particle mask of each object */
+typedef struct {
+  cx W[3][4];
+  double P[3][4];
+  unsigned mask[3];
+} q4_objs;
+
+/* fermion line B ... K with insertions ins[0..n-1] (from B), one of them the stub; the
+ * line's vector current at the stub (including the stub's -i g) into L, and the mask of
+ * the momentum it sends into the connector */
+static unsigned q4_line(const cx* Bsp, const cx* Ksp, int ib, int ik, const int* ins, int n, const q4_objs* o,
+                        const double (*Pin)[4], const q4_kin* k, double m, double wt, int zwt, double g, cx* L) {
+  int s = 0;
+  while (ins[s] != Q4_STUB) ++s;
+  cx x[4], y[4], t[4], S[4][4], G[4][4];
+  memcpy(x, Bsp, sizeof x);
+  unsigned mB = 1u << ib;
+  double qB[4] = {Pin[ib][0], Pin[ib][1], Pin[ib][2], Pin[ib][3]};
+  for (int j = 0; j < s; ++j) {
+    slash(o->W[ins[j]], G);
+    bra_mat(x, G, t);
+    for (int r = 0; r < 4; ++r) x[r] = -I * g * t[r];
+    mB |= o->mask[ins[j]];
+    for (int mu = 0; mu < 4; ++mu) qB[mu] += o->P[ins[j]][mu];
+    /* propagator K-ward of vertex j: momentum along the arrow -(P_B + sum k) */
+    cx qc[4] = {-qB[0], -qB[1], -qB[2], -qB[3]};
+    slash(qc, S);
+    for (int r = 0; r < 4; ++r) S[r][r] += m;
+    double w = (m > 0.0 && !(zwt && is_tchannel(mB))) ? wt : 0.0;
+    cx D = k->inv[mB] - m * m + I * m * w;
+    bra_mat(x, S, t);
+    for (int r = 0; r < 4; ++r) x[r] = I * t[r] / D;
+  }
+  memcpy(y, Ksp, sizeof y);
+  unsigned mK = 1u << ik;
+  double qK[4] = {Pin[ik][0], Pin[ik][1], Pin[ik][2], Pin[ik][3]};
+  for (int j = n - 1; j > s; --j) {
+    slash(o->W[ins[j]], G);
+    for (int r = 0; r < 4; ++r) { t[r] = 0; for (int c = 0; c < 4; ++c) t[r] += G[r][c] * y[c]; }
+    for (int r = 0; r < 4; ++r) y[r] = -I * g * t[r];
+    mK |= o->mask[ins[j]];
+    for (int mu = 0; mu < 4; ++mu) qK[mu] += o->P[ins[j]][mu];
+    /* propagator B-ward of vertex j: momentum along the arrow P_K + sum k */
+    cx qc[4] = {qK[0], qK[1], qK[2], qK[3]};
+    slash(qc, S);
+    for (int r = 0; r < 4; ++r) S[r][r] += m;
+    double w = (m > 0.0 && !(zwt && is_tchannel(mK))) ? wt : 0.0;
+    cx D = k->inv[mK] - m * m + I * m * w;
+    for (int r = 0; r < 4; ++r) { t[r] = 0; for (int c = 0; c < 4; ++c) t[r] += S[r][c] * y[c]; }
+    for (int r = 0; r < 4; ++r) y[r] = I * t[r] / D;
+  }
+  cx J[4];
+  vector_current(x, y, 1.0, 1.0, J);
+  for (int mu = 0; mu < 4; ++mu) L[mu] = -I * g * J[mu];
+  return mB | mK;
+}
+
+/* the colour-stripped value of every term at one helicity */
+static void q4_diagrams(const double* mom, const int* lam, const proc_def* pd, const q4_kin* k, double gs, double mt,
+                        double wt, int zwt, int gauge_leg, cx* A) {
+  double Pin[MAXPAR][4];
+  for (int i = 0; i < pd->npar; ++i)
+    for (int m = 0; m < 4; ++m) Pin[i][m] = q4_in(pd->role[i]) ? mom[4 * i + m] : -mom[4 * i + m];
+  cx BL[4], KL[4], BH[4], KH[4], tmp[4];
+  const double *pbl = mom + 4 * k->bl, *pkl = mom + 4 * k->kl;
+  if (pd->role[k->bl] == R_QB_IN) spinor_v(pbl, 0.0, lam[k->bl], tmp);
+  else spinor_u(pbl, 0.0, lam[k->bl], tmp);
+  dirac_bar(tmp, BL);
+  if (pd->role[k->kl] == R_Q_IN) spinor_u(pkl, 0.0, lam[k->kl], KL);
+  else spinor_v(pkl, 0.0, lam[k->kl], KL);
+  spinor_u(mom + 4 * k->t, mt, lam[k->t], tmp);
+  dirac_bar(tmp, BH);
+  spinor_v(mom + 4 * k->tb, mt, lam[k->tb], KH);
+  q4_objs o;
+  int gl[2] = {k->ga, k->gb};
+  for (int x = 0; x < 2; ++x) {
+    const double* pg = mom + 4 * gl[x];
+    polvec(pg, lam[gl[x]], o.W[x]);
+    if (pd->role[gl[x]] == R_G_OUT)
+      for (int m = 0; m < 4; ++m) o.W[x][m] = conj(o.W[x][m]);
+    if (gl[x] == gauge_leg)
+      for (int m = 0; m < 4; ++m) o.W[x][m] = pg[m] / pg[0];
+    for (int m = 0; m < 4; ++m) o.P[x][m] = Pin[gl[x]][m];
+    o.mask[x] = 1u << gl[x];
+  }
+  /* the joined pair: vertex -g f^{abe} V(P_a, P_b, -(P_a + P_b)), propagator -i/s_ab */
+  {
+    cx v[4];
+    v3(o.P[0], o.W[0], o.P[1], o.W[1], v);
+    o.mask[2] = o.mask[0] | o.mask[1];
+    double sab = k->inv[o.mask[2]];
+    for (int m = 0; m < 4; ++m) {
+      o.W[2][m] = (-gs) * (-I / sab) * v[m];
+      o.P[2][m] = o.P[0][m] + o.P[1][m];
+    }
+  }
+  for (int d = 0; d < q4_nterm; ++d) {
+    const q4_term* t = &Q4_TERMS[d];
+    cx L[4], H[4];
+    unsigned mL = q4_line(BL, KL, k->bl, k->kl, t->l, t->nl, &o, (const double (*)[4])Pin, k, 0.0, 0.0, 0, gs, L);
+    unsigned mH = q4_line(BH, KH, k->t, k->tb, t->h, t->nh, &o, (const double (*)[4])Pin, k, mt, wt, zwt, gs, H);
+    /* momenta the lines send into the connector */
+    double QL[4], QH[4];
+    for (int m = 0; m < 4; ++m) {
+      QL[m] = 0;
+      QH[m] = 0;
+      for (int i = 0; i < pd->npar; ++i) {
+        if (mL >> i & 1) QL[m] += Pin[i][m];
+        if (mH >> i & 1) QH[m] += Pin[i][m];
+      }
+    }
+    cx pL = -I / k->inv[mL], pH = -I / k->inv[mH];
+    cx v[4], val;
+    switch (t->conn) {
+      case 0:
+        val = pL * mdot_c(L, H);
+        break;
+      case 1: case 2: case 3: {
+        int x = t->conn - 1;
+        v3(QL, L, o.P[x], o.W[x], v);
+        val = (-gs) * pL * pH * mdot_c(v, H);
+        break;
+      }
+      case 4: case 5: {
+        int x1 = t->conn == 4 ? 0 : 1, x2 = 1 - x1;
+        double Qe[4];
+        for (int m = 0; m < 4; ++m) Qe[m] = QL[m] + o.P[x1][m];
+        cx Je[4], w[4];
+        v3(QL, L, o.P[x1], o.W[x1], w);
+        cx pe = -I / k->inv[mL | o.mask[x1]];
+        for (int m = 0; m < 4; ++m) Je[m] = (-gs) * pe * w[m];
+        v3(Qe, Je, o.P[x2], o.W[x2], v);
+        val = (-gs) * pL * pH * mdot_c(v, H);
+        break;
+      }
+      default: {
+        const cx *ea = o.W[0], *eb = o.W[1];
+        cx lor;
+        if (t->conn == 6) lor = mdot_c(L, eb) * mdot_c(ea, H) - mdot_c(L, H) * mdot_c(ea, eb);
+        else if (t->conn == 7) lor = mdot_c(L, ea) * mdot_c(eb, H) - mdot_c(L, H) * mdot_c(ea, eb);
+        else lor = mdot_c(L, ea) * mdot_c(eb, H) - mdot_c(L, eb) * mdot_c(ea, H);
+        val = (-I * gs * gs) * pL * pH * lor;
+      }
+    }
+    A[d] = val;
+  }
+}
+
+/* explicit colour sum of |M|^2 at one helicity and the flow amplitudes */
+static double q4_colour_sum(const cx* A, const cx* Ginv, cx* J) {
+  double m2 = 0;
+  cx Pr[Q4_NFLOW];
+  for (int n = 0; n < Q4_NFLOW; ++n) Pr[n] = 0;
+  for (int x = 0; x < Q4_NCI; ++x) {
+    cx M = 0;
+    for (int d = 0; d < q4_nterm; ++d) M += A[d] * Q4_DCOL[(size_t)d * Q4_NCI + x];
+    if (M == 0) continue;
+    m2 += creal(M) * creal(M) + cimag(M) * cimag(M);
+    for (int n = 0; n < Q4_NFLOW; ++n) Pr[n] += conj(Q4_FLOW[n][x]) * M;
+  }
+  for (int n = 0; n < Q4_NFLOW; ++n) {
+    J[n] = 0;
+    for (int m = 0; m < Q4_NFLOW; ++m) J[n] += Ginv[n * Q4_NFLOW + m] * Pr[m];
+  }
+  return m2;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Driver                                                                     */
 /* ------------------------------------------------------------------------- */
 static int select_first_exceeding(const double* w, int n, double r) {
@@ -1049,6 +1524,14 @@ int oracle_me(int proc, const oracle_params* par, int64_t nevt, const double* mo
     qg_gram(G);
     inv4(G, Ginv);
   }
+  cx G4inv[Q4_NFLOW * Q4_NFLOW];
+  if (pd->kind == 4) {
+    cx G[Q4_NFLOW * Q4_NFLOW];
+#pragma omp critical(q4_init)
+    q4_colour_init();
+    q4_gram(G);
+    invn(Q4_NFLOW, G, G4inv);
+  }
 
 #pragma omp parallel for schedule(dynamic, 4)
   for (int64_t e = 0; e < nevt; ++e) {
@@ -1061,9 +1544,11 @@ int oracle_me(int proc, const oracle_params* par, int64_t nevt, const double* mo
     double gs = sqrt(4.0 * M_PI * as);
     invariants inv;
     qg_kin qk;
+    q4_kin k4;
     if (pd->kind == 1) event_invariants(pd, p, par->mt, &inv);
     memset(&qk, 0, sizeof qk);
     if (pd->kind == 3) qg_kinematics(pd, p, par->mt, &qk);
+    if (pd->kind == 4) q4_kinematics(pd, p, &k4);
     for (int h = 0; h < ncomb; ++h) {
       int lam[MAXPAR];
       for (int i = 0; i < npar; ++i) lam[i] = ((h >> (npar - 1 - i)) & 1) ? 1 : -1;
@@ -1074,6 +1559,11 @@ int oracle_me(int proc, const oracle_params* par, int64_t nevt, const double* mo
         A[0] = amp_eemumu(p, lam, par, &sm);
       } else if (pd->kind == 2) {
         m2 = qq_colour_sum(amp_qqbar_tt(p, lam, pd, gs, par->mt), A);
+        explicit_colour = 1;
+      } else if (pd->kind == 4) {
+        cx D[Q4_MAXTERM];
+        q4_diagrams(p, lam, pd, &k4, gs, par->mt, par->wt, par->zero_width_tchan, gauge_leg, D);
+        m2 = q4_colour_sum(D, G4inv, A);
         explicit_colour = 1;
       } else if (pd->kind == 3) {
         cx D[5];

@@ -166,6 +166,13 @@ PROCESS_FINAL_MASSES = {
     "g u > t t~ u": lambda mt: (mt, mt, 0.0),
     "u~ g > t t~ u~": lambda mt: (mt, mt, 0.0),
     "g u~ > t t~ u~": lambda mt: (mt, mt, 0.0),
+    "u u~ > t t~ g g": lambda mt: (mt, mt, 0.0, 0.0),
+    "u~ u > t t~ g g": lambda mt: (mt, mt, 0.0, 0.0),
+    "u g > t t~ u g": lambda mt: (mt, mt, 0.0, 0.0),
+    "g u > t t~ u g": lambda mt: (mt, mt, 0.0, 0.0),
+    "u~ g > t t~ u~ g": lambda mt: (mt, mt, 0.0, 0.0),
+    "g u~ > t t~ u~ g": lambda mt: (mt, mt, 0.0, 0.0),
+    "g g > t t~ u u~": lambda mt: (mt, mt, 0.0, 0.0),
 }
 
 
