@@ -467,6 +467,7 @@ def run_gpu(args):
             line["processes"] = processes_table(args, peaks, reuse={PROCESS: (results, acc)})
             line["dispatch"] = dispatch_table(args, DISPATCH_CHANNELS)
             line["dispatch_jet"] = dispatch_table(args, DISPATCH_JET_CHANNELS)
+            line["dispatch_2jet"] = dispatch_table(args, DISPATCH_2JET_CHANNELS, nevt=262144)
             line["serving"] = serving_table(args, quick=True)
         print(json.dumps(line), flush=True)
     if dist:
@@ -477,7 +478,8 @@ def run_gpu(args):
 # the per-process workloads: (process, events, alpha_s)
 PROCESS_TABLE = (("e+ e- > mu+ mu-", 16384, None), ("g g > t t~", 524288, 0.118), ("g g > t t~ g", 524288, 0.118),
                  ("g g > t t~ g g", 1048576, "uniform"), ("g g > t t~ g g g", 262144, 0.118),
-                 ("u u~ > t t~", 524288, 0.118), ("u u~ > t t~ g", 524288, 0.118), ("u g > t t~ u", 524288, 0.118))
+                 ("u u~ > t t~", 524288, 0.118), ("u u~ > t t~ g", 524288, 0.118), ("u g > t t~ u", 524288, 0.118),
+                 ("u u~ > t t~ g g", 262144, 0.118), ("u g > t t~ u g", 262144, 0.118), ("g g > t t~ u u~", 262144, 0.118))
 
 
 DISPATCH_CHANNELS = (("g g > t t~", 0.90), ("u u~ > t t~", 0.05), ("u~ u > t t~", 0.05))
@@ -485,6 +487,11 @@ DISPATCH_CHANNELS = (("g g > t t~", 0.90), ("u u~ > t t~", 0.05), ("u~ u > t t~"
 DISPATCH_JET_CHANNELS = (("g g > t t~ g", 0.55), ("u u~ > t t~ g", 0.10), ("u~ u > t t~ g", 0.10),
                          ("u g > t t~ u", 0.07), ("g u > t t~ u", 0.07), ("u~ g > t t~ u~", 0.055),
                          ("g u~ > t t~ u~", 0.055))
+# p p -> t t~ + 2 jets: g g -> t t~ g g and the seven channels with one light-quark line
+# (synthetic shares; the four-quark channels are not built)
+DISPATCH_2JET_CHANNELS = (("g g > t t~ g g", 0.50), ("u u~ > t t~ g g", 0.08), ("u~ u > t t~ g g", 0.08),
+                          ("u g > t t~ u g", 0.08), ("g u > t t~ u g", 0.08), ("u~ g > t t~ u~ g", 0.06),
+                          ("g u~ > t t~ u~ g", 0.06), ("g g > t t~ u u~", 0.06))
 
 
 def dispatch_table(args, channels, nevt=524288):

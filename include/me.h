@@ -30,6 +30,15 @@
  *   "g u~ > t t~ u~"       quark), column end K, top t, antitop tb and gluon a:
  *                          T^a_{B tb} d_{t K}, T^a_{t K} d_{B tb}, T^a_{B K} d_{t tb},
  *                          T^a_{t tb} d_{B K})
+ *   "u u~ > t t~ g g"      36 diagrams,             64 helicities,  13 (the two-jet
+ *   "u~ u > t t~ g g"      channels of p p -> t t~ + 2 jets with one light-quark line,
+ *   "u g > t t~ u g"       either beam order; with "g g > t t~ g g" all of them but
+ *   "g u > t t~ u g"       the four-quark channels.  Flows over B, K, t, tb and the
+ *   "u~ g > t t~ u~ g"     gluons a, b (a the lower particle index):
+ *   "g u~ > t t~ u~ g"     (T^a T^b)_{B tb} d_{t K}, (T^b T^a)_{B tb} d_{t K},
+ *   "g g > t t~ u u~"      T^a_{B tb} T^b_{t K}, T^b_{B tb} T^a_{t K}, d_{B tb} (T^a T^b)_{t K},
+ *                          d_{B tb} (T^b T^a)_{t K}, the same six with (B K, t tb) in
+ *                          place of (B tb, t K), and d^{ab} d_{B tb} d_{t K})
  *
  * Conventions:
  *   momenta   (E, px, py, pz) in GeV, FP64, array-of-structures [nevt][npar][4];

@@ -315,7 +315,7 @@ cudaError_t launch_x2(const MeLaunch& a, cudaStream_t s) {
   constexpr size_t smem = me_x2_smem_bytes<P, L>();
   static_assert(smem <= 227 * 1024, "shared-memory footprint of this layout exceeds 227 KB");
   auto k = me_kernel_x2<P, L>;
-  if (smem > 48 * 1024) {
+  if (smem > kSmemOptIn) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
   }

@@ -148,6 +148,11 @@ struct Layout {
   static constexpr int w_mode = W_MODE, s_mode = S_MODE, k_mode = K_MODE;
 };
 
+// Dynamic shared memory above which a kernel opts in to more than the default 48 KB per
+// block.  The limit counts the kernel's static shared memory too (a few hundred bytes
+// here), so the opt-in starts well below 48 KB.
+constexpr size_t kSmemOptIn = 40 * 1024;
+
 template <class P, class R, class L>
 constexpr size_t me_smem_bytes() {
   size_t b = 0;
@@ -545,7 +550,7 @@ int resident_blocks(K k, int threads, size_t smem) {
   if (per_block > 0) b = std::min<int>(b, int(size_t(smem_sm) / per_block));
   b = std::min(b, thr_sm / threads);
   b = std::max(b, 1);
-  if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (smem > kSmemOptIn) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   const int pct = int((size_t(b) * per_block * 100 + size_t(smem_sm) - 1) / size_t(smem_sm));
   cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, std::min(100, pct));
   cudaGetLastError();
@@ -579,7 +584,7 @@ cudaError_t launch_me(const MeLaunch& a, cudaStream_t s) {
   constexpr size_t smem = me_smem_bytes<P, R, L>();
   static_assert(smem <= 227 * 1024, "shared-memory footprint of this layout exceeds 227 KB");
   auto k = me_kernel<P, R, L>;
-  if (smem > 48 * 1024) {
+  if (smem > kSmemOptIn) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
   }

@@ -37,6 +37,13 @@ extern const ProcessOps ops_qgttq __attribute__((weak));
 extern const ProcessOps ops_gqttq __attribute__((weak));
 extern const ProcessOps ops_qxgttqx __attribute__((weak));
 extern const ProcessOps ops_gqxttqx __attribute__((weak));
+extern const ProcessOps ops_qqttgg __attribute__((weak));
+extern const ProcessOps ops_qxqttgg __attribute__((weak));
+extern const ProcessOps ops_qgttqg __attribute__((weak));
+extern const ProcessOps ops_gqttqg __attribute__((weak));
+extern const ProcessOps ops_qxgttqxg __attribute__((weak));
+extern const ProcessOps ops_gqxttqxg __attribute__((weak));
+extern const ProcessOps ops_ggttqqx __attribute__((weak));
 }
 using namespace meb300;
 
@@ -44,7 +51,8 @@ namespace {
 
 const ProcessOps* const kProcs[] = {&ops_eemumu, &ops_ggtt,   &ops_ggttg,  &ops_ggttgg,  &ops_ggttggg,
                                     &ops_qqtt,   &ops_qxqtt,  &ops_qqttg,  &ops_qxqttg,  &ops_qgttq,
-                                    &ops_gqttq,  &ops_qxgttqx, &ops_gqxttqx};
+                                    &ops_gqttq,  &ops_qxgttqx, &ops_gqxttqx, &ops_qqttgg, &ops_qxqttgg,
+                                    &ops_qgttqg, &ops_gqttqg, &ops_qxgttqxg, &ops_gqxttqxg, &ops_ggttqqx};
 
 thread_local std::string g_init_error;
 

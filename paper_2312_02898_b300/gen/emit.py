@@ -45,6 +45,17 @@ PROCESSES = {
     "g u~ > t t~ u~": dict(tag="gqxttqx", roles=("g_in", "qb_in", "t", "tb", "qb_out")),
 }
 QUARK_JET_TAGS = ("qqttg", "qxqttg", "qgttq", "gqttq", "qxgttqx", "gqxttqx")
+# the two-jet channels with one light-quark line (gen/quark_lines.py)
+PROCESSES.update({
+    "u u~ > t t~ g g": dict(tag="qqttgg", roles=("q_in", "qb_in", "t", "tb", "g_out", "g_out")),
+    "u~ u > t t~ g g": dict(tag="qxqttgg", roles=("qb_in", "q_in", "t", "tb", "g_out", "g_out")),
+    "u g > t t~ u g": dict(tag="qgttqg", roles=("q_in", "g_in", "t", "tb", "q_out", "g_out")),
+    "g u > t t~ u g": dict(tag="gqttqg", roles=("g_in", "q_in", "t", "tb", "q_out", "g_out")),
+    "u~ g > t t~ u~ g": dict(tag="qxgttqxg", roles=("qb_in", "g_in", "t", "tb", "qb_out", "g_out")),
+    "g u~ > t t~ u~ g": dict(tag="gqxttqxg", roles=("g_in", "qb_in", "t", "tb", "qb_out", "g_out")),
+    "g g > t t~ u u~": dict(tag="ggttqqx", roles=("g_in", "g_in", "t", "tb", "q_out", "qb_out")),
+})
+QUARK_JET2_TAGS = ("qqttgg", "qxqttgg", "qgttqg", "gqttqg", "qxgttqxg", "gqxttqxg", "ggttqqx")
 
 # jamps variants per process: (register budget, diagram-group size).  The budget is the
 # number of currents kept in registers (None: all); a group size splits the emission
@@ -839,6 +850,9 @@ class Emitter:
         return "\n".join(out) + "\n", stats
 
     def emit(self):
+        if self.tag in QUARK_JET2_TAGS:
+            from . import quark_lines
+            return quark_lines.header(self)
         if self.tag in QUARK_JET_TAGS:
             return self.emit_quark_jet()
         if self.tag == "eemumu":
