@@ -244,11 +244,12 @@ def emit(em):
         key = (tuple(sorted(o for o in light if o != STUB)), tuple(sorted(o for o in top if o != STUB)))
         by_place.setdefault(key, []).append(d)
     npairs = 0
-    mags_used = set()
+    # every distinct fermion-chain prefix and line current is computed once (the same
+    # values recur across placements), so the code and its flop count describe the work
+    # that runs
+    memo = {}
+    cnt = {"v": 0}
     for key, ds in by_place.items():
-        body.append("  {")
-        memo = {}
-        cnt = {"v": 0}
 
         def newvar(prefix):
             cnt["v"] += 1
@@ -343,7 +344,6 @@ def emit(em):
             pre = "".join(f" const cx<R> a{m} = R({m}) * a;" for m in sorted(mags))
             flop("scale", len(mags))
             body.append(f"    {{ const cx<R> a = {expr};{pre} {' '.join(ops)} }}")
-        body.append("  }")
     return body, dict(kvec=kvec, dgs=dgs, dts=dts, flops=fl["n"], pairs=npairs, scale=scale, gram=gram,
                       ib=ib, ik=ik, ga=ga, gb=gb, it=it, itb=itb, parts=parts)
 
