@@ -29,6 +29,10 @@ g g -> t tbar q qbar) are pinned the same way: gauge invariance in each gluon, t
 limit onto q qbar -> t tbar g with colour correlators built from its flow amplitudes,
 initial-state collinear limits (P_qq, P_qg, P_gq, P_gg) onto the one-jet channels and
 g g -> t tbar g, Bose symmetry, charge conjugation, beam order and the 13-flow basis.
+The four-quark channels with two light flavours (u u~ -> t t~ d d~, u d -> t t~ u d,
+u d~ -> t t~ u d~, u~ d~ -> t t~ u~ d~) are pinned by the final-state g -> d d~ and the
+initial-state collinear limits onto the one-jet channels, Lorentz invariance, beam order,
+charge conjugation and their six-flow colour basis.
 """
 from __future__ import annotations
 
@@ -64,6 +68,11 @@ PROCESSES = (
     "u~ g > t t~ u~ g",
     "g u~ > t t~ u~ g",
     "g g > t t~ u u~",
+    "u u~ > t t~ d d~",
+    "u~ u > t t~ d d~",
+    "u d > t t~ u d",
+    "u d~ > t t~ u d~",
+    "u~ d~ > t t~ u~ d~",
 )
 
 

@@ -35,7 +35,9 @@
  * same way over all 648 colour assignments and projected onto four flow tensors.  The
  * two-jet channels with one light line (q qbar -> t tbar g g and crossings) are their 36
  * Feynman diagrams (38 terms), summed over all 5184 colour assignments and projected
- * onto 13 flow tensors.
+ * onto 13 flow tensors.  The four-quark channels with two light flavours are the 7
+ * diagrams of three fermion lines joined by gluons, summed over all 729 colour
+ * assignments and projected onto the six colour-routing tensors.
  *
  * Conventions shared with the product only through their published definitions:
  *   * momenta [nevt][npar][4] = (E, px, py, pz); particle order of the process string;
@@ -57,7 +59,7 @@
 
 typedef double complex cx;
 
-#define NPROC 20
+#define NPROC 25
 #define MAXPAR 7
 #define MAXG 5
 #define MAXCOL 120
@@ -69,12 +71,13 @@ typedef struct {
 
 /* roles of external particles */
 enum { R_EBAR_IN, R_E_IN, R_MUBAR_OUT, R_MU_OUT, R_G_IN, R_G_OUT, R_T_OUT, R_TBAR_OUT, R_Q_IN, R_QB_IN,
-       R_Q_OUT, R_QB_OUT };
+       R_Q_OUT, R_QB_OUT, R_D_IN, R_DB_IN, R_D_OUT, R_DB_OUT };
 
 /* kind: 0 e+ e- -> mu+ mu-; 1 g g -> t tbar + gluons (Berends-Giele); 2 q qbar -> t tbar
  * (explicit colour); 3 q qbar -> t tbar g and its crossings with one light quark line, a
  * top line and one gluon (explicit colour, five Feynman diagrams); 4 the same with two
- * gluons (explicit colour, 36 Feynman diagrams) */
+ * gluons (explicit colour, 36 Feynman diagrams); 5 two light quark lines of different
+ * flavours and the top line (explicit colour, 7 Feynman diagrams) */
 typedef struct {
   const char* name;
   int npar;
@@ -110,6 +113,12 @@ static const proc_def PROCS[NPROC] = {
     {"u~ g > t t~ u~ g", 6, 0, 96, {R_QB_IN, R_G_IN, R_T_OUT, R_TBAR_OUT, R_QB_OUT, R_G_OUT}, 4, 13},
     {"g u~ > t t~ u~ g", 6, 0, 96, {R_G_IN, R_QB_IN, R_T_OUT, R_TBAR_OUT, R_QB_OUT, R_G_OUT}, 4, 13},
     {"g g > t t~ u u~", 6, 0, 256, {R_G_IN, R_G_IN, R_T_OUT, R_TBAR_OUT, R_Q_OUT, R_QB_OUT}, 4, 13},
+    /* four quarks of two different light flavours: IDEN = 4 x 9 */
+    {"u u~ > t t~ d d~", 6, 0, 36, {R_Q_IN, R_QB_IN, R_T_OUT, R_TBAR_OUT, R_D_OUT, R_DB_OUT}, 5, 6},
+    {"u~ u > t t~ d d~", 6, 0, 36, {R_QB_IN, R_Q_IN, R_T_OUT, R_TBAR_OUT, R_D_OUT, R_DB_OUT}, 5, 6},
+    {"u d > t t~ u d", 6, 0, 36, {R_Q_IN, R_D_IN, R_T_OUT, R_TBAR_OUT, R_Q_OUT, R_D_OUT}, 5, 6},
+    {"u d~ > t t~ u d~", 6, 0, 36, {R_Q_IN, R_DB_IN, R_T_OUT, R_TBAR_OUT, R_Q_OUT, R_DB_OUT}, 5, 6},
+    {"u~ d~ > t t~ u~ d~", 6, 0, 36, {R_QB_IN, R_DB_IN, R_T_OUT, R_TBAR_OUT, R_QB_OUT, R_DB_OUT}, 5, 6},
 };
 
 static int factorial(int n) { return n <= 1 ? 1 : n * factorial(n - 1); }
@@ -248,9 +257,22 @@ static void qg_colour_init(void);
 static void qg_gram(cx G[4][4]);
 static void q4_colour_init(void);
 static void q4_gram(cx* G);
+static void q5_colour_init(void);
+static void q5_gram(cx* G);
 
 int oracle_colour_matrix_exact(int proc, int64_t* num, int64_t* den) {
   if (proc < 0 || proc >= NPROC) return -1;
+  if (PROCS[proc].kind == 5) {
+    /* C_nm = number of colour assignments on which flows n and m are both 1 */
+    cx G[36];
+    q5_colour_init();
+    q5_gram(G);
+    for (int i = 0; i < 36; ++i) {
+      num[i] = (int64_t)llround(creal(G[i]));
+      den[i] = 1;
+    }
+    return 0;
+  }
   if (PROCS[proc].kind == 4) {
     /* C_nm = sum over all colour assignments of conj(c_n) c_m, explicit Gell-Mann sums;
      * the entries are multiples of 1/3 */
@@ -1468,6 +1490,182 @@ static double q4_colour_sum(const cx* A, const cx* Ginv, cx* J) {
 }
 
 /* ------------------------------------------------------------------------- */
+/* Three fermion lines (kind 5): the four-quark channels of p p -> t tbar + 2 jets with two
+ * light quarks of different flavours (u and d), explicit colour                */
+/* ------------------------------------------------------------------------- */
+/* Lines: 0 the u line, 1 the d line, 2 the top line; each runs from its row end (an
+ * incoming antiquark or outgoing quark: vbar or ubar) to its column end (an incoming
+ * quark or outgoing antiquark: u or v).  The gluons form a tree joining the three lines:
+ *   term 0: one three-gluon vertex joining a stub of every line;
+ *   terms 1-6: line X carries the currents of the other two lines Y, Z (Y nearer X's row
+ *   end), X = 0, 1, 2 and both orders.
+ * Feynman rules as for the other QCD processes.  Colour flows over the row-end colours
+ * (B0, B1, t) and column-end colours (K0, K1, y): the six products d_{B0 K_s0} d_{B1 K_s1}
+ * d_{t K_s2} for the permutations s of (K0, K1, y) in lexicographic order. */
+#define Q5_NCI (NC * NC * NC * NC * NC * NC)
+#define Q5_NFLOW 6
+#define Q5_NTERM 7
+static cx Q5_DCOL[Q5_NTERM][Q5_NCI];
+static double Q5_FLOW[Q5_NFLOW][Q5_NCI];
+static int q5_ready = 0;
+static const int Q5_MID[Q5_NTERM][3] = {{-1, -1, -1}, {0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+static const int Q5_PERM[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+
+static void q5_colour_init(void) {
+  if (q5_ready) return;
+  q4_colour_init(); /* the structure constants */
+  memset(Q5_DCOL, 0, sizeof Q5_DCOL);
+  int B[3], K[3];
+  for (int x = 0; x < Q5_NCI; ++x) {
+    int r = x;
+    K[2] = r % NC; r /= NC; B[2] = r % NC; r /= NC; K[1] = r % NC; r /= NC; B[1] = r % NC; r /= NC;
+    K[0] = r % NC; r /= NC; B[0] = r;
+    for (int f = 0; f < Q5_NFLOW; ++f)
+      Q5_FLOW[f][x] = (B[0] == K[Q5_PERM[f][0]]) && (B[1] == K[Q5_PERM[f][1]]) && (B[2] == K[Q5_PERM[f][2]]);
+    /* term 0: f^{c0 c1 c2} T^{c0}_{B0 K0} T^{c1}_{B1 K1} T^{c2}_{t y} */
+    cx s = 0;
+    for (int c0 = 0; c0 < 8; ++c0)
+      for (int c1 = 0; c1 < 8; ++c1)
+        for (int c2 = 0; c2 < 8; ++c2) {
+          double f = Q4_F[c0][c1][c2];
+          if (f != 0.0) s += f * TGM[c0][B[0]][K[0]] * TGM[c1][B[1]][K[1]] * TGM[c2][B[2]][K[2]];
+        }
+    Q5_DCOL[0][x] = s;
+    /* terms 1-6: (T^{cY} T^{cZ})_{B_X K_X} T^{cY}_{B_Y K_Y} T^{cZ}_{B_Z K_Z} */
+    for (int d = 1; d < Q5_NTERM; ++d) {
+      int X = Q5_MID[d][0], Y = Q5_MID[d][1], Z = Q5_MID[d][2];
+      cx v = 0;
+      for (int cy = 0; cy < 8; ++cy)
+        for (int cz = 0; cz < 8; ++cz) {
+          cx m = 0;
+          for (int l = 0; l < NC; ++l) m += TGM[cy][B[X]][l] * TGM[cz][l][K[X]];
+          v += m * TGM[cy][B[Y]][K[Y]] * TGM[cz][B[Z]][K[Z]];
+        }
+      Q5_DCOL[d][x] = v;
+    }
+  }
+  q5_ready = 1;
+}
+
+typedef struct {
+  int B[3], K[3];                /* particle index of each line's row end and column end */
+  double inv[1 << MAXPAR];
+} q5_kin;
+
+static int q5_row(int r) { return r == R_QB_IN || r == R_Q_OUT || r == R_DB_IN || r == R_D_OUT || r == R_T_OUT; }
+static int q5_line_of(int r) {
+  if (r == R_Q_IN || r == R_QB_IN || r == R_Q_OUT || r == R_QB_OUT) return 0;
+  if (r == R_D_IN || r == R_DB_IN || r == R_D_OUT || r == R_DB_OUT) return 1;
+  return 2;
+}
+static int q5_in(int r) { return r == R_Q_IN || r == R_QB_IN || r == R_D_IN || r == R_DB_IN; }
+
+static void q5_kinematics(const proc_def* pd, const double* mom, q5_kin* k) {
+  for (int i = 0; i < pd->npar; ++i) {
+    int r = pd->role[i], ln = q5_line_of(r);
+    if (q5_row(r)) k->B[ln] = i;
+    else k->K[ln] = i;
+  }
+  for (unsigned mask = 0; mask < (1u << pd->npar); ++mask) {
+    quad Q[4] = {0, 0, 0, 0};
+    for (int i = 0; i < pd->npar; ++i)
+      if (mask >> i & 1)
+        for (int m = 0; m < 4; ++m) Q[m] += q5_in(pd->role[i]) ? (quad)mom[4 * i + m] : -(quad)mom[4 * i + m];
+    k->inv[mask] = (double)msq_q(Q);
+  }
+}
+
+/* external spinor of particle i: row (bar) spinor for a row end, column spinor else */
+static void q5_spinor(const proc_def* pd, const double* mom, const int* lam, int i, double m, cx* w) {
+  int r = pd->role[i];
+  cx t[4];
+  const double* p = mom + 4 * i;
+  if (r == R_QB_IN || r == R_DB_IN) { spinor_v(p, m, lam[i], t); dirac_bar(t, w); }
+  else if (r == R_Q_OUT || r == R_D_OUT || r == R_T_OUT) { spinor_u(p, m, lam[i], t); dirac_bar(t, w); }
+  else if (r == R_Q_IN || r == R_D_IN) spinor_u(p, m, lam[i], w);
+  else spinor_v(p, m, lam[i], w);
+}
+
+static void q5_diagrams(const double* mom, const int* lam, const proc_def* pd, const q5_kin* k, double gs, double mt,
+                        double wt, int zwt, cx* A) {
+  double Pin[MAXPAR][4];
+  for (int i = 0; i < pd->npar; ++i)
+    for (int m = 0; m < 4; ++m) Pin[i][m] = q5_in(pd->role[i]) ? mom[4 * i + m] : -mom[4 * i + m];
+  cx Bs[3][4], Ks[3][4], J[3][4];
+  double Q[3][4], ms[3] = {0.0, 0.0, mt};
+  unsigned mk[3];
+  for (int ln = 0; ln < 3; ++ln) {
+    q5_spinor(pd, mom, lam, k->B[ln], ms[ln], Bs[ln]);
+    q5_spinor(pd, mom, lam, k->K[ln], ms[ln], Ks[ln]);
+    /* the line's current at a stub, -i g B gamma^mu K, and the momentum it sends out */
+    vector_current(Bs[ln], Ks[ln], 1.0, 1.0, J[ln]);
+    for (int m = 0; m < 4; ++m) {
+      J[ln][m] *= -I * gs;
+      Q[ln][m] = Pin[k->B[ln]][m] + Pin[k->K[ln]][m];
+    }
+    mk[ln] = (1u << k->B[ln]) | (1u << k->K[ln]);
+  }
+  /* term 0: three gluon propagators -i/Q^2 and the vertex -g f V(Q0, Q1, Q2) */
+  {
+    cx v[4];
+    v3(Q[0], J[0], Q[1], J[1], v);
+    cx p = (-I / k->inv[mk[0]]) * (-I / k->inv[mk[1]]) * (-I / k->inv[mk[2]]);
+    A[0] = (-gs) * p * mdot_c(v, J[2]);
+  }
+  /* terms 1-6: line X with the currents of Y (row side) and Z, one fermion propagator */
+  for (int d = 1; d < Q5_NTERM; ++d) {
+    int X = Q5_MID[d][0], Y = Q5_MID[d][1], Z = Q5_MID[d][2];
+    cx WY[4], WZ[4], G[4][4], S[4][4], x[4], t[4];
+    for (int m = 0; m < 4; ++m) {
+      WY[m] = (-I / k->inv[mk[Y]]) * J[Y][m];
+      WZ[m] = (-I / k->inv[mk[Z]]) * J[Z][m];
+    }
+    /* B_X (-i g WYslash) i(qslash + m)/D (-i g WZslash) K_X, q = -(P_BX + Q_Y) */
+    slash(WY, G);
+    bra_mat(Bs[X], G, t);
+    for (int r = 0; r < 4; ++r) x[r] = -I * gs * t[r];
+    unsigned mB = (1u << k->B[X]) | mk[Y];
+    cx qc[4];
+    for (int m = 0; m < 4; ++m) qc[m] = -(Pin[k->B[X]][m] + Q[Y][m]);
+    slash(qc, S);
+    for (int r = 0; r < 4; ++r) S[r][r] += ms[X];
+    double w = (X == 2 && !(zwt && is_tchannel(mB))) ? wt : 0.0;
+    cx D = k->inv[mB] - ms[X] * ms[X] + I * ms[X] * w;
+    bra_mat(x, S, t);
+    for (int r = 0; r < 4; ++r) x[r] = I * t[r] / D;
+    slash(WZ, G);
+    bra_mat(x, G, t);
+    A[d] = -I * gs * bra_ket(t, Ks[X]);
+  }
+}
+
+static double q5_colour_sum(const cx* A, const cx* Ginv, cx* Jf) {
+  double m2 = 0;
+  cx Pr[Q5_NFLOW];
+  for (int n = 0; n < Q5_NFLOW; ++n) Pr[n] = 0;
+  for (int x = 0; x < Q5_NCI; ++x) {
+    cx M = 0;
+    for (int d = 0; d < Q5_NTERM; ++d) M += A[d] * Q5_DCOL[d][x];
+    m2 += creal(M) * creal(M) + cimag(M) * cimag(M);
+    for (int n = 0; n < Q5_NFLOW; ++n) Pr[n] += Q5_FLOW[n][x] * M;
+  }
+  for (int n = 0; n < Q5_NFLOW; ++n) {
+    Jf[n] = 0;
+    for (int m = 0; m < Q5_NFLOW; ++m) Jf[n] += Ginv[n * Q5_NFLOW + m] * Pr[m];
+  }
+  return m2;
+}
+
+static void q5_gram(cx* G) {
+  for (int n = 0; n < Q5_NFLOW; ++n)
+    for (int m = 0; m < Q5_NFLOW; ++m) {
+      double s = 0;
+      for (int x = 0; x < Q5_NCI; ++x) s += Q5_FLOW[n][x] * Q5_FLOW[m][x];
+      G[n * Q5_NFLOW + m] = s;
+    }
+}
+
+/* ------------------------------------------------------------------------- */
 /* Driver                                                                     */
 /* ------------------------------------------------------------------------- */
 static int select_first_exceeding(const double* w, int n, double r) {
@@ -1524,6 +1722,13 @@ int oracle_me(int proc, const oracle_params* par, int64_t nevt, const double* mo
     qg_gram(G);
     inv4(G, Ginv);
   }
+  cx G5inv[Q5_NFLOW * Q5_NFLOW];
+  if (pd->kind == 5) {
+    cx G[Q5_NFLOW * Q5_NFLOW];
+    q5_colour_init();
+    q5_gram(G);
+    invn(Q5_NFLOW, G, G5inv);
+  }
   cx G4inv[Q4_NFLOW * Q4_NFLOW];
   if (pd->kind == 4) {
     cx G[Q4_NFLOW * Q4_NFLOW];
@@ -1545,10 +1750,12 @@ int oracle_me(int proc, const oracle_params* par, int64_t nevt, const double* mo
     invariants inv;
     qg_kin qk;
     q4_kin k4;
+    q5_kin k5;
     if (pd->kind == 1) event_invariants(pd, p, par->mt, &inv);
     memset(&qk, 0, sizeof qk);
     if (pd->kind == 3) qg_kinematics(pd, p, par->mt, &qk);
     if (pd->kind == 4) q4_kinematics(pd, p, &k4);
+    if (pd->kind == 5) q5_kinematics(pd, p, &k5);
     for (int h = 0; h < ncomb; ++h) {
       int lam[MAXPAR];
       for (int i = 0; i < npar; ++i) lam[i] = ((h >> (npar - 1 - i)) & 1) ? 1 : -1;
@@ -1559,6 +1766,11 @@ int oracle_me(int proc, const oracle_params* par, int64_t nevt, const double* mo
         A[0] = amp_eemumu(p, lam, par, &sm);
       } else if (pd->kind == 2) {
         m2 = qq_colour_sum(amp_qqbar_tt(p, lam, pd, gs, par->mt), A);
+        explicit_colour = 1;
+      } else if (pd->kind == 5) {
+        cx D[Q5_NTERM];
+        q5_diagrams(p, lam, pd, &k5, gs, par->mt, par->wt, par->zero_width_tchan, D);
+        m2 = q5_colour_sum(D, G5inv, A);
         explicit_colour = 1;
       } else if (pd->kind == 4) {
         cx D[Q4_MAXTERM];

@@ -173,6 +173,11 @@ PROCESS_FINAL_MASSES = {
     "u~ g > t t~ u~ g": lambda mt: (mt, mt, 0.0, 0.0),
     "g u~ > t t~ u~ g": lambda mt: (mt, mt, 0.0, 0.0),
     "g g > t t~ u u~": lambda mt: (mt, mt, 0.0, 0.0),
+    "u u~ > t t~ d d~": lambda mt: (mt, mt, 0.0, 0.0),
+    "u~ u > t t~ d d~": lambda mt: (mt, mt, 0.0, 0.0),
+    "u d > t t~ u d": lambda mt: (mt, mt, 0.0, 0.0),
+    "u d~ > t t~ u d~": lambda mt: (mt, mt, 0.0, 0.0),
+    "u~ d~ > t t~ u~ d~": lambda mt: (mt, mt, 0.0, 0.0),
 }
 
 
