@@ -44,6 +44,11 @@ extern const ProcessOps ops_gqttqg __attribute__((weak));
 extern const ProcessOps ops_qxgttqxg __attribute__((weak));
 extern const ProcessOps ops_gqxttqxg __attribute__((weak));
 extern const ProcessOps ops_ggttqqx __attribute__((weak));
+extern const ProcessOps ops_uuxttddx __attribute__((weak));
+extern const ProcessOps ops_uxuttddx __attribute__((weak));
+extern const ProcessOps ops_udttud __attribute__((weak));
+extern const ProcessOps ops_udxttudx __attribute__((weak));
+extern const ProcessOps ops_uxdxttuxdx __attribute__((weak));
 }
 using namespace meb300;
 
@@ -52,7 +57,8 @@ namespace {
 const ProcessOps* const kProcs[] = {&ops_eemumu, &ops_ggtt,   &ops_ggttg,  &ops_ggttgg,  &ops_ggttggg,
                                     &ops_qqtt,   &ops_qxqtt,  &ops_qqttg,  &ops_qxqttg,  &ops_qgttq,
                                     &ops_gqttq,  &ops_qxgttqx, &ops_gqxttqx, &ops_qqttgg, &ops_qxqttgg,
-                                    &ops_qgttqg, &ops_gqttqg, &ops_qxgttqxg, &ops_gqxttqxg, &ops_ggttqqx};
+                                    &ops_qgttqg, &ops_gqttqg, &ops_qxgttqxg, &ops_gqxttqxg, &ops_ggttqqx,
+                                    &ops_uuxttddx, &ops_uxuttddx, &ops_udttud, &ops_udxttudx, &ops_uxdxttuxdx};
 
 thread_local std::string g_init_error;
 

@@ -55,7 +55,16 @@ PROCESSES.update({
     "g u~ > t t~ u~ g": dict(tag="gqxttqxg", roles=("g_in", "qb_in", "t", "tb", "qb_out", "g_out")),
     "g g > t t~ u u~": dict(tag="ggttqqx", roles=("g_in", "g_in", "t", "tb", "q_out", "qb_out")),
 })
-QUARK_JET2_TAGS = ("qqttgg", "qxqttgg", "qgttqg", "gqttqg", "qxgttqxg", "gqxttqxg", "ggttqqx")
+# the four-quark channels with two light flavours (gen/quark_lines.py, three lines)
+PROCESSES.update({
+    "u u~ > t t~ d d~": dict(tag="uuxttddx", roles=("q_in", "qb_in", "t", "tb", "d_out", "db_out")),
+    "u~ u > t t~ d d~": dict(tag="uxuttddx", roles=("qb_in", "q_in", "t", "tb", "d_out", "db_out")),
+    "u d > t t~ u d": dict(tag="udttud", roles=("q_in", "d_in", "t", "tb", "q_out", "d_out")),
+    "u d~ > t t~ u d~": dict(tag="udxttudx", roles=("q_in", "db_in", "t", "tb", "q_out", "db_out")),
+    "u~ d~ > t t~ u~ d~": dict(tag="uxdxttuxdx", roles=("qb_in", "db_in", "t", "tb", "qb_out", "db_out")),
+})
+QUARK_JET2_TAGS = ("qqttgg", "qxqttgg", "qgttqg", "gqttqg", "qxgttqxg", "gqxttqxg", "ggttqqx",
+                   "uuxttddx", "uxuttddx", "udttud", "udxttudx", "uxdxttuxdx")
 
 # jamps variants per process: (register budget, diagram-group size).  The budget is the
 # number of currents kept in registers (None: all); a group size splits the emission

@@ -345,13 +345,16 @@ def emit(em):
             flop("scale", len(mags))
             body.append(f"    {{ const cx<R> a = {expr};{pre} {' '.join(ops)} }}")
     return body, dict(kvec=kvec, dgs=dgs, dts=dts, flops=fl["n"], pairs=npairs, scale=scale, gram=gram,
-                      ib=ib, ik=ik, ga=ga, gb=gb, it=it, itb=itb, parts=parts)
+                      parts=parts, ncol=13, ndiag=36, namp=38)
 
 
 def header(em):
-    """the generated proc_<tag>.cuh text and its stats"""
+    """the generated proc_<tag>.cuh text and its stats (one light-quark line and two
+    gluons, or two light-quark lines of different flavours)"""
     from .emit import _lit
-    body, st = emit(em)
+    three = any(r.startswith("d") for r in em.roles)
+    body, st = emit3(em) if three else emit(em)
+    ncol, ndiag, namp = st["ncol"], st["ndiag"], st["namp"]
     roles, npar, tag = em.roles, em.npar, em.tag
     parts = st["parts"]
     # IDEN: initial spins x initial colours x (identical final gluons)!
@@ -428,9 +431,9 @@ def header(em):
             e = f"fmadd({a_}, {b_}, {e})"
         return e
 
-    for i in range(13):
+    for i in range(ncol):
         tr, ti = [], []
-        for j in range(i, 13):
+        for j in range(i, ncol):
             c = cf[i][j] * (1 if j == i else 2)
             if c == 0:
                 continue
@@ -444,13 +447,13 @@ def header(em):
            "#pragma once", '#include "../helas.cuh"', "namespace meb300 {", f"struct proc_{tag} {{",
            f'static constexpr const char* NAME = "{em.process}";',
            "// NGLUON counts the powers of g_s^2 in |M|^2 (four QCD vertices)",
-           f"static constexpr int NPAR = {npar}, NCOMB = {1 << npar}, NCOL = 13, NDIAG = 36, NAMP = 38, NNODE = 0, "
+           f"static constexpr int NPAR = {npar}, NCOMB = {1 << npar}, NCOL = {ncol}, NDIAG = {ndiag}, NAMP = {namp}, NNODE = 0, "
            f"IDEN = {iden}, NGLUON = 4;",
            f"static constexpr int NDEN_G = {len(st['dgs'])}, NDEN_T = {len(st['dts'])}, COL_DEN = {cden}, "
            f"NCOLPAIR = {st['pairs']}, MAX_LIVE = 8, NKVEC = {nk};",
            f"static constexpr long FLOPS_AMP = {st['flops']}, FLOPS_COL = {csflops};",
            "static constexpr bool QCD = true;",
-           "static constexpr bool CF_BF16_EXACT = false, CF_FP16_EXACT = false;",
+           "static constexpr bool CF_BF16_EXACT = false, CF_FP16_EXACT = false;  // (no tensor-core path)",
            "// dg: 1/K^2 of the gluon propagators; dt: 1/q^2 of the light-quark propagators and",
            "// 1/(q^2 - mt^2 + i mt wt) of the top propagators (by particle set)",
            "template <int S, class R, class DG, class DT, class KT>",
@@ -467,8 +470,160 @@ def header(em):
     out += body
     out += ["}", "template <class R, class JA>", "static HD R colour_sum(JA& J) {", "  R s = R(0);"] + cs
     out += ["  return s;", "}", "};",
-            f"constexpr int proc_{tag}_CF[169] = {{{', '.join(str(v) for row in cf for v in row)}}};",
+            f"constexpr int proc_{tag}_CF[{ncol * ncol}] = {{{', '.join(str(v) for row in cf for v in row)}}};",
             "}  // namespace meb300"]
-    stats = dict(ndiag=36, namp=38, nnode=0, ncol=13, pairs=st["pairs"], flops_amp=st["flops"], flops_col=csflops,
+    stats = dict(ndiag=ndiag, namp=namp, nnode=0, ncol=ncol, pairs=st["pairs"], flops_amp=st["flops"], flops_col=csflops,
                  nden_g=len(st["dgs"]), nden_t=len(st["dts"]), col_den=cden, max_live=8, iden=iden)
     return "\n".join(out) + "\n", stats
+
+
+# ----------------------------------------------------------------------------
+# two light-quark lines of different flavours and the top line
+# ----------------------------------------------------------------------------
+# terms: 0 the three-gluon vertex joining the three lines; then line X carrying the
+# currents of Y (nearer X's row end) and Z, for (X, Y, Z) in this order
+MIDDLE = ((0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0))
+
+
+def three_line_colour():
+    """(flow coefficients of the 7 terms scaled to Gaussian integers, the scale, the Gram
+    matrix of the 6 flows).  Indices (B0, K0, B1, K1, t, y): row and column ends of the u
+    line, the d line and the top line; flows d_{B0 K_s0} d_{B1 K_s1} d_{t K_s2} for the
+    permutations s of (K0, K1, y) in lexicographic order."""
+    T = gell_mann_T()
+    f = _structure_constants(T)
+    d = np.eye(3)
+    perms = list(itertools.permutations(range(3)))
+    flows3 = []
+    for s in perms:
+        x = np.zeros((3,) * 6)
+        for B0, K0, B1, K1, t, y in itertools.product(range(3), repeat=6):
+            K = (K0, K1, y)
+            x[B0, K0, B1, K1, t, y] = d[B0, K[s[0]]] * d[B1, K[s[1]]] * d[t, K[s[2]]]
+        flows3.append(x.ravel())
+    Fm = np.array(flows3).T
+    letters = ("BK", "CL", "ty")  # index letters of the rows/columns of lines 0, 1, 2
+    tens = [np.einsum("abc,aBK,bCL,cty->BKCLty", f, T, T, T)]
+    for X, Y, Z in MIDDLE:
+        # gluon colours: g joins X and Y, h joins X and Z
+        spec = {X: f"g{letters[X][0]}m,hm{letters[X][1]}", Y: f"g{letters[Y]}", Z: f"h{letters[Z]}"}
+        tens.append(np.einsum(f"{spec[X]},{spec[Y]},{spec[Z]}->BKCLty", T, T, T, T))
+    coef = []
+    for x in tens:
+        c = np.linalg.lstsq(Fm, x.ravel(), rcond=None)[0]
+        if np.abs(Fm @ c - x.ravel()).max() > 1e-10:
+            raise RuntimeError("colour of a three-line term is not in the span of the flows")
+        coef.append(c)
+    coef = np.array(coef)
+    for scale in (1, 2, 3, 4, 6, 12, 24, 36):
+        cs = coef * scale
+        if np.abs(cs - np.round(cs.real) - 1j * np.round(cs.imag)).max() < 1e-9:
+            break
+    else:
+        raise RuntimeError("three-line flow coefficients are not multiples of 1/36")
+    ci = np.round(coef.real * scale) + 1j * np.round(coef.imag * scale)
+    G = Fm.T @ Fm
+    return ci, scale, [[Fraction(int(round(v))) for v in row] for row in G]
+
+
+def emit3(em):
+    """(jamps body, stats) for two light-quark lines of different flavours and the top line"""
+    roles, npar = em.roles, em.npar
+    line_of = {"q": 0, "qb": 0, "d": 1, "db": 1, "t": 2, "tb": 2}
+    row_roles = ("qb_in", "q_out", "db_in", "d_out", "t")
+    B, K = [None] * 3, [None] * 3
+    for i, r in enumerate(roles):
+        ln = line_of[r.split("_")[0]]
+        if r in row_roles:
+            B[ln] = i
+        else:
+            K[ln] = i
+
+    def parts(S, sign=1):
+        out = []
+        for i in sorted(S):
+            s = 1 if roles[i].endswith("_in") else -1
+            out.append(("+" if s * sign > 0 else "-", i))
+        return tuple(out)
+
+    kvec, dgs, dts = {}, {}, {}
+
+    def kv(S, sign=1):
+        key = parts(S, sign)
+        if key not in kvec:
+            kvec[key] = npar + len(kvec)
+        return f"(kt + {kvec[key]} * S)"
+
+    def dg(S):
+        S = frozenset(S)
+        if S not in dgs:
+            dgs[S] = len(dgs)
+        return f"dg[{dgs[S]}]"
+
+    def dt(S, massive):
+        key = (frozenset(S), massive)
+        if key not in dts:
+            dts[key] = len(dts)
+        return f"dt[{dts[key]}]"
+
+    fl = {"n": 0}
+
+    def flop(k, n=1):
+        fl["n"] += _FL[k] * n
+
+    body = [f"  int lam[{npar}];",
+            f"  for (int i = 0; i < {npar}; ++i) lam[i] = ((h >> ({npar - 1} - i)) & 1) ? 1 : -1;",
+            "  " + " ".join(f"cx<R> x{i}[4];" for i in range(npar))]
+    for i, r in enumerate(roles):
+        ktp, m = f"(kt + {i} * S)", "mt" if r in ("t", "tb") else "R(0)"
+        fn = {"q_in": "ext_u", "d_in": "ext_u", "qb_in": "ext_vbar", "db_in": "ext_vbar", "q_out": "ext_ubar",
+              "d_out": "ext_ubar", "t": "ext_ubar", "qb_out": "ext_v", "db_out": "ext_v", "tb": "ext_v"}[r]
+        body.append(f"  {fn}<R>({ktp}, {m}, lam[{i}], x{i});")
+        flop("ext")
+    lines = [frozenset([B[l], K[l]]) for l in range(3)]
+    for l in range(3):
+        body.append(f"  cx<R> J{l}[4]; pair_current<R>(x{B[l]}, x{K[l]}, J{l});")
+        flop("pj")
+    coef, scale, gram = three_line_colour()
+    amps = []
+    # term 0: the three-gluon vertex; phases -i per line current (3), -i per gluon
+    # propagator (3), -1 for the vertex -g f V: +1 overall
+    amps.append((f"{dg(lines[1])} * {dg(lines[2])} * close_v3<R>(J2, J0, {kv(lines[0])}, J1, {kv(lines[1])}, "
+                 f"{dg(lines[0])})", 1))
+    flop("v3")
+    flop("scale", 2)
+    for n, (X, Y, Z) in enumerate(MIDDLE):
+        # line X: the current of Y enters nearer its row end, one fermion propagator, the
+        # current of Z; phases -i (Y), -i (Z), +1 (step), -i (last vertex), -i -i (gluon
+        # propagators): -i overall
+        SX = frozenset([B[X]]) | lines[Y]
+        m = "mt" if X == 2 else "R(0)"
+        body.append(f"  cx<R> c{n}[4]; bra_step<R>(x{B[X]}, J{Y}, {kv(SX, -1)}, {m}, {dt(SX, X == 2)}, c{n});")
+        body.append(f"  cx<R> v{n}[4]; pair_current<R>(c{n}, x{K[X]}, v{n});")
+        flop("step")
+        flop("pj")
+        amps.append((f"{dg(lines[Y])} * {dg(lines[Z])} * mdot(v{n}, J{Z})", -1j))
+        flop("dot")
+        flop("scale", 2)
+    npairs = 0
+    for d, (expr, ph) in enumerate(amps):
+        ops, mags = [], set()
+        for n in range(6):
+            k = complex(coef[d][n]) * ph
+            k = complex(round(k.real), round(k.imag))
+            if k == 0:
+                continue
+            mag = int(abs(k.real) + abs(k.imag))
+            unit = k / mag
+            src = "a" if mag == 1 else f"a{mag}"
+            if mag != 1:
+                mags.add(mag)
+            ops.append({1: f"J[{n}] += {src};", -1: f"J[{n}] -= {src};", 1j: f"acc_pi(J[{n}], {src});",
+                        -1j: f"acc_mi(J[{n}], {src});"}[unit])
+            flop("add")
+            npairs += 1
+        pre = "".join(f" const cx<R> a{m} = R({m}) * a;" for m in sorted(mags))
+        flop("scale", len(mags))
+        body.append(f"  {{ const cx<R> a = {expr};{pre} {' '.join(ops)} }}")
+    return body, dict(kvec=kvec, dgs=dgs, dts=dts, flops=fl["n"], pairs=npairs, scale=scale, gram=gram,
+                      parts=parts, ncol=6, ndiag=7, namp=7)

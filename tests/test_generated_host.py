@@ -1,4 +1,5 @@
-"""The generated code of the two-jet channels with one light-quark line, run on the host:
+"""The generated code of the two-jet channels with one light-quark line and of the
+four-quark channels, run on the host:
 nvcc compiles tests/generated_host_check.cu for the host around one generated process
 header (its precompute, jamps and colour_sum in FP64, the computation the kernels perform
 per event) and the result must equal the FP64 oracle within 1e-12, with and without the
@@ -16,12 +17,13 @@ from paper_2312_02898_b300 import phasespace as ps
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(os.path.dirname(HERE), "paper_2312_02898_b300", "csrc")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
-CASES = [("u u~ > t t~ g g", "qqttgg"), ("g u > t t~ u g", "gqttqg"), ("g g > t t~ u u~", "ggttqqx")]
+CASES = [("u u~ > t t~ g g", "qqttgg"), ("g u > t t~ u g", "gqttqg"), ("g g > t t~ u u~", "ggttqqx"),
+         ("u d~ > t t~ u d~", "udxttudx")]
 
 
 @pytest.mark.skipif(not (os.path.exists(NVCC) or shutil.which("nvcc")), reason="nvcc not available")
 @pytest.mark.parametrize("process,tag", CASES)
-def test_generated_two_jet_code_on_the_host(oracle_mod, tmp_path, process, tag):
+def test_generated_code_on_the_host(oracle_mod, tmp_path, process, tag):
     from paper_2312_02898_b300.gen import emit
     gen = tmp_path / "generated"
     emit.generate_all(str(gen), processes=[process])
