@@ -32,7 +32,9 @@ g g -> t tbar g, Bose symmetry, charge conjugation, beam order and the 13-flow b
 The four-quark channels with two light flavours (u u~ -> t t~ d d~, u d -> t t~ u d,
 u d~ -> t t~ u d~, u~ d~ -> t t~ u~ d~) are pinned by the final-state g -> d d~ and the
 initial-state collinear limits onto the one-jet channels, Lorentz invariance, beam order,
-charge conjugation and their six-flow colour basis.
+charge conjugation and their six-flow colour basis; the same-flavour channels
+(u u -> t t~ u u, u~ u~ -> t t~ u~ u~, u u~ -> t t~ u u~) add Pauli antisymmetry at equal
+final momenta, which fixes the sign of the exchange pairing, and Bose/Fermi relabelling.
 """
 from __future__ import annotations
 
@@ -73,6 +75,10 @@ PROCESSES = (
     "u d > t t~ u d",
     "u d~ > t t~ u d~",
     "u~ d~ > t t~ u~ d~",
+    "u u > t t~ u u",
+    "u~ u~ > t t~ u~ u~",
+    "u u~ > t t~ u u~",
+    "u~ u > t t~ u u~",
 )
 
 

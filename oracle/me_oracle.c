@@ -37,7 +37,9 @@
  * Feynman diagrams (38 terms), summed over all 5184 colour assignments and projected
  * onto 13 flow tensors.  The four-quark channels with two light flavours are the 7
  * diagrams of three fermion lines joined by gluons, summed over all 729 colour
- * assignments and projected onto the six colour-routing tensors.
+ * assignments and projected onto the six colour-routing tensors; with one light flavour
+ * the second pairing of the light quarks (their column ends exchanged) is added with the
+ * sign -1 of exchanging identical fermions.
  *
  * Conventions shared with the product only through their published definitions:
  *   * momenta [nevt][npar][4] = (E, px, py, pz); particle order of the process string;
@@ -59,7 +61,7 @@
 
 typedef double complex cx;
 
-#define NPROC 25
+#define NPROC 29
 #define MAXPAR 7
 #define MAXG 5
 #define MAXCOL 120
@@ -77,7 +79,8 @@ enum { R_EBAR_IN, R_E_IN, R_MUBAR_OUT, R_MU_OUT, R_G_IN, R_G_OUT, R_T_OUT, R_TBA
  * (explicit colour); 3 q qbar -> t tbar g and its crossings with one light quark line, a
  * top line and one gluon (explicit colour, five Feynman diagrams); 4 the same with two
  * gluons (explicit colour, 36 Feynman diagrams); 5 two light quark lines of different
- * flavours and the top line (explicit colour, 7 Feynman diagrams) */
+ * flavours and the top line (explicit colour, 7 Feynman diagrams); 6 the same with one
+ * light flavour (both pairings of the light quarks, 14 diagrams) */
 typedef struct {
   const char* name;
   int npar;
@@ -119,6 +122,11 @@ static const proc_def PROCS[NPROC] = {
     {"u d > t t~ u d", 6, 0, 36, {R_Q_IN, R_D_IN, R_T_OUT, R_TBAR_OUT, R_Q_OUT, R_D_OUT}, 5, 6},
     {"u d~ > t t~ u d~", 6, 0, 36, {R_Q_IN, R_DB_IN, R_T_OUT, R_TBAR_OUT, R_Q_OUT, R_DB_OUT}, 5, 6},
     {"u~ d~ > t t~ u~ d~", 6, 0, 36, {R_QB_IN, R_DB_IN, R_T_OUT, R_TBAR_OUT, R_QB_OUT, R_DB_OUT}, 5, 6},
+    /* four quarks of one light flavour: IDEN = 4 x 9 (x 2! for two identical final quarks) */
+    {"u u > t t~ u u", 6, 0, 72, {R_Q_IN, R_Q_IN, R_T_OUT, R_TBAR_OUT, R_Q_OUT, R_Q_OUT}, 6, 6},
+    {"u~ u~ > t t~ u~ u~", 6, 0, 72, {R_QB_IN, R_QB_IN, R_T_OUT, R_TBAR_OUT, R_QB_OUT, R_QB_OUT}, 6, 6},
+    {"u u~ > t t~ u u~", 6, 0, 36, {R_Q_IN, R_QB_IN, R_T_OUT, R_TBAR_OUT, R_Q_OUT, R_QB_OUT}, 6, 6},
+    {"u~ u > t t~ u u~", 6, 0, 36, {R_QB_IN, R_Q_IN, R_T_OUT, R_TBAR_OUT, R_Q_OUT, R_QB_OUT}, 6, 6},
 };
 
 static int factorial(int n) { return n <= 1 ? 1 : n * factorial(n - 1); }
@@ -262,7 +270,7 @@ static void q5_gram(cx* G);
 
 int oracle_colour_matrix_exact(int proc, int64_t* num, int64_t* den) {
   if (proc < 0 || proc >= NPROC) return -1;
-  if (PROCS[proc].kind == 5) {
+  if (PROCS[proc].kind == 5 || PROCS[proc].kind == 6) {
     /* C_nm = number of colour assignments on which flows n and m are both 1 */
     cx G[36];
     q5_colour_init();
@@ -1505,7 +1513,8 @@ static double q4_colour_sum(const cx* A, const cx* Ginv, cx* J) {
 #define Q5_NCI (NC * NC * NC * NC * NC * NC)
 #define Q5_NFLOW 6
 #define Q5_NTERM 7
-static cx Q5_DCOL[Q5_NTERM][Q5_NCI];
+/* terms 7-13: the second pairing of one light flavour (column ends K0 and K1 exchanged) */
+static cx Q5_DCOL[2 * Q5_NTERM][Q5_NCI];
 static double Q5_FLOW[Q5_NFLOW][Q5_NCI];
 static int q5_ready = 0;
 static const int Q5_MID[Q5_NTERM][3] = {{-1, -1, -1}, {0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
@@ -1544,6 +1553,17 @@ static void q5_colour_init(void) {
       Q5_DCOL[d][x] = v;
     }
   }
+  for (int x = 0; x < Q5_NCI; ++x) {
+    int r = x, y = r % NC;
+    r /= NC;
+    int t = r % NC; r /= NC;
+    int K1 = r % NC; r /= NC;
+    int B1 = r % NC; r /= NC;
+    int K0 = r % NC; r /= NC;
+    int B0 = r;
+    int xs = ((((B0 * NC + K1) * NC + B1) * NC + K0) * NC + t) * NC + y;
+    for (int d = 0; d < Q5_NTERM; ++d) Q5_DCOL[Q5_NTERM + d][x] = Q5_DCOL[d][xs];
+  }
   q5_ready = 1;
 }
 
@@ -1561,8 +1581,15 @@ static int q5_line_of(int r) {
 static int q5_in(int r) { return r == R_Q_IN || r == R_QB_IN || r == R_D_IN || r == R_DB_IN; }
 
 static void q5_kinematics(const proc_def* pd, const double* mom, q5_kin* k) {
+  int nb = 0, nk = 0;
   for (int i = 0; i < pd->npar; ++i) {
     int r = pd->role[i], ln = q5_line_of(r);
+    if (pd->kind == 6 && ln < 2) {
+      /* one light flavour: row ends and column ends take slots 0, 1 in particle order */
+      if (q5_row(r)) k->B[nb++] = i;
+      else k->K[nk++] = i;
+      continue;
+    }
     if (q5_row(r)) k->B[ln] = i;
     else k->K[ln] = i;
   }
@@ -1639,13 +1666,13 @@ static void q5_diagrams(const double* mom, const int* lam, const proc_def* pd, c
   }
 }
 
-static double q5_colour_sum(const cx* A, const cx* Ginv, cx* Jf) {
+static double q5_colour_sum(const cx* A, int nterm, const cx* Ginv, cx* Jf) {
   double m2 = 0;
   cx Pr[Q5_NFLOW];
   for (int n = 0; n < Q5_NFLOW; ++n) Pr[n] = 0;
   for (int x = 0; x < Q5_NCI; ++x) {
     cx M = 0;
-    for (int d = 0; d < Q5_NTERM; ++d) M += A[d] * Q5_DCOL[d][x];
+    for (int d = 0; d < nterm; ++d) M += A[d] * Q5_DCOL[d][x];
     m2 += creal(M) * creal(M) + cimag(M) * cimag(M);
     for (int n = 0; n < Q5_NFLOW; ++n) Pr[n] += Q5_FLOW[n][x] * M;
   }
@@ -1723,7 +1750,7 @@ int oracle_me(int proc, const oracle_params* par, int64_t nevt, const double* mo
     inv4(G, Ginv);
   }
   cx G5inv[Q5_NFLOW * Q5_NFLOW];
-  if (pd->kind == 5) {
+  if (pd->kind == 5 || pd->kind == 6) {
     cx G[Q5_NFLOW * Q5_NFLOW];
     q5_colour_init();
     q5_gram(G);
@@ -1755,7 +1782,7 @@ int oracle_me(int proc, const oracle_params* par, int64_t nevt, const double* mo
     memset(&qk, 0, sizeof qk);
     if (pd->kind == 3) qg_kinematics(pd, p, par->mt, &qk);
     if (pd->kind == 4) q4_kinematics(pd, p, &k4);
-    if (pd->kind == 5) q5_kinematics(pd, p, &k5);
+    if (pd->kind == 5 || pd->kind == 6) q5_kinematics(pd, p, &k5);
     for (int h = 0; h < ncomb; ++h) {
       int lam[MAXPAR];
       for (int i = 0; i < npar; ++i) lam[i] = ((h >> (npar - 1 - i)) & 1) ? 1 : -1;
@@ -1767,10 +1794,21 @@ int oracle_me(int proc, const oracle_params* par, int64_t nevt, const double* mo
       } else if (pd->kind == 2) {
         m2 = qq_colour_sum(amp_qqbar_tt(p, lam, pd, gs, par->mt), A);
         explicit_colour = 1;
-      } else if (pd->kind == 5) {
-        cx D[Q5_NTERM];
+      } else if (pd->kind == 5 || pd->kind == 6) {
+        cx D[2 * Q5_NTERM];
         q5_diagrams(p, lam, pd, &k5, gs, par->mt, par->wt, par->zero_width_tchan, D);
-        m2 = q5_colour_sum(D, G5inv, A);
+        int nterm = Q5_NTERM;
+        if (pd->kind == 6) {
+          /* the second pairing (column ends exchanged) enters with the relative sign -1 of
+           * exchanging two identical fermions */
+          q5_kin k2 = k5;
+          k2.K[0] = k5.K[1];
+          k2.K[1] = k5.K[0];
+          q5_diagrams(p, lam, pd, &k2, gs, par->mt, par->wt, par->zero_width_tchan, D + Q5_NTERM);
+          for (int d = 0; d < Q5_NTERM; ++d) D[Q5_NTERM + d] = -D[Q5_NTERM + d];
+          nterm = 2 * Q5_NTERM;
+        }
+        m2 = q5_colour_sum(D, nterm, G5inv, A);
         explicit_colour = 1;
       } else if (pd->kind == 4) {
         cx D[Q4_MAXTERM];

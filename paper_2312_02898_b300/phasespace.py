@@ -178,6 +178,10 @@ PROCESS_FINAL_MASSES = {
     "u d > t t~ u d": lambda mt: (mt, mt, 0.0, 0.0),
     "u d~ > t t~ u d~": lambda mt: (mt, mt, 0.0, 0.0),
     "u~ d~ > t t~ u~ d~": lambda mt: (mt, mt, 0.0, 0.0),
+    "u u > t t~ u u": lambda mt: (mt, mt, 0.0, 0.0),
+    "u~ u~ > t t~ u~ u~": lambda mt: (mt, mt, 0.0, 0.0),
+    "u u~ > t t~ u u~": lambda mt: (mt, mt, 0.0, 0.0),
+    "u~ u > t t~ u u~": lambda mt: (mt, mt, 0.0, 0.0),
 }
 
 
