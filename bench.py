@@ -480,7 +480,7 @@ PROCESS_TABLE = (("e+ e- > mu+ mu-", 16384, None), ("g g > t t~", 524288, 0.118)
                  ("g g > t t~ g g", 1048576, "uniform"), ("g g > t t~ g g g", 262144, 0.118),
                  ("u u~ > t t~", 524288, 0.118), ("u u~ > t t~ g", 524288, 0.118), ("u g > t t~ u", 524288, 0.118),
                  ("u u~ > t t~ g g", 262144, 0.118), ("u g > t t~ u g", 262144, 0.118), ("g g > t t~ u u~", 262144, 0.118),
-                 ("u u~ > t t~ d d~", 262144, 0.118), ("u d > t t~ u d", 262144, 0.118))
+                 ("u u~ > t t~ d d~", 262144, 0.118), ("u d > t t~ u d", 262144, 0.118), ("u u > t t~ u u", 262144, 0.118))
 
 
 DISPATCH_CHANNELS = (("g g > t t~", 0.90), ("u u~ > t t~", 0.05), ("u~ u > t t~", 0.05))
@@ -489,13 +489,14 @@ DISPATCH_JET_CHANNELS = (("g g > t t~ g", 0.55), ("u u~ > t t~ g", 0.10), ("u~ u
                          ("u g > t t~ u", 0.07), ("g u > t t~ u", 0.07), ("u~ g > t t~ u~", 0.055),
                          ("g u~ > t t~ u~", 0.055))
 # p p -> t t~ + 2 jets: g g -> t t~ g g, the seven channels with one light-quark line and
-# the five four-quark channels with two light flavours (synthetic shares; the four-quark
-# channels with identical quarks are not built)
-DISPATCH_2JET_CHANNELS = (("g g > t t~ g g", 0.40), ("u u~ > t t~ g g", 0.07), ("u~ u > t t~ g g", 0.07),
-                          ("u g > t t~ u g", 0.07), ("g u > t t~ u g", 0.07), ("u~ g > t t~ u~ g", 0.05),
+# the nine four-quark channels (two light flavours, or one with both pairings); synthetic
+# shares
+DISPATCH_2JET_CHANNELS = (("g g > t t~ g g", 0.36), ("u u~ > t t~ g g", 0.06), ("u~ u > t t~ g g", 0.06),
+                          ("u g > t t~ u g", 0.06), ("g u > t t~ u g", 0.06), ("u~ g > t t~ u~ g", 0.05),
                           ("g u~ > t t~ u~ g", 0.05), ("g g > t t~ u u~", 0.05), ("u u~ > t t~ d d~", 0.04),
                           ("u~ u > t t~ d d~", 0.03), ("u d > t t~ u d", 0.04), ("u d~ > t t~ u d~", 0.03),
-                          ("u~ d~ > t t~ u~ d~", 0.03))
+                          ("u~ d~ > t t~ u~ d~", 0.03), ("u u > t t~ u u", 0.02), ("u~ u~ > t t~ u~ u~", 0.02),
+                          ("u u~ > t t~ u u~", 0.02), ("u~ u > t t~ u u~", 0.02))
 
 
 def dispatch_table(args, channels, nevt=524288):

@@ -12,7 +12,8 @@
  * built from HELAS-style external wavefunctions, FFV / VVV / VVVV vertex currents for
  * every Feynman diagram, the helicity sum and the colour sum J^dagger C J over
  * colour-flow amplitudes J.  IDEN averages over initial spins and colours and divides
- * by (number of identical final gluons)!.
+ * by n! for every set of n identical final particles (gluons, or the light quarks of
+ * "u u > t t~ u u" and "u~ u~ > t t~ u~ u~").
  *
  * Processes (particle order of the string):
  *   "e+ e- > mu+ mu-"      2 diagrams (photon, Z),   16 helicities,   1 colour flow
@@ -39,6 +40,17 @@
  *   "g g > t t~ u u~"      T^a_{B tb} T^b_{t K}, T^b_{B tb} T^a_{t K}, d_{B tb} (T^a T^b)_{t K},
  *                          d_{B tb} (T^b T^a)_{t K}, the same six with (B K, t tb) in
  *                          place of (B tb, t K), and d^{ab} d_{B tb} d_{t K})
+ *   "u u~ > t t~ d d~"     7 diagrams,              64 helicities,   6 (the four-quark
+ *   "u~ u > t t~ d d~"     channels of p p -> t t~ + 2 jets with two light flavours:
+ *   "u d > t t~ u d"       three fermion lines, u, d and top.  Flows over each line's
+ *   "u d~ > t t~ u d~"     row end B (incoming antiquark or outgoing quark) and column
+ *   "u~ d~ > t t~ u~ d~"   end K: d_{Bu K_s0} d_{Bd K_s1} d_{t K_s2} for the permutations
+ *                          s of (Ku, Kd, tb) in lexicographic order)
+ *   "u u > t t~ u u"       14 diagrams,             64 helicities,   6 (the four-quark
+ *   "u~ u~ > t t~ u~ u~"   channels with one light flavour: both pairings of the light
+ *   "u u~ > t t~ u u~"     quarks into lines, the second with the sign -1 of exchanging
+ *   "u~ u > t t~ u u~"     identical fermions; the same six flows, the first pairing's
+ *                          lines taken as the u and d lines above)
  *
  * Conventions:
  *   momenta   (E, px, py, pz) in GeV, FP64, array-of-structures [nevt][npar][4];
@@ -180,7 +192,7 @@ int me_compute_noalloc(me_handle* h, int64_t nevt, const double* momenta, const 
  * same matrix element), and an event generator produces the events of all channels in one
  * batch; the paper's outlook (Section 5) names this multi-subprocess case.  Event e of
  * the batch belongs to channel channel[e] and is evaluated by handle hs[channel[e]]:
- *   hs       host array of nchan (1 to 16) handles, all with the same number of
+ *   hs       host array of nchan (1 to 32) handles, all with the same number of
  *            particles, each in FP64 or FP32 (ME_ERR_MODE otherwise)
  *   channel  device, int32 [nevt]; an index outside [0, nchan) gives that event NaN in
  *            me and selections 0

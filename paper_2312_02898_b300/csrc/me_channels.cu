@@ -26,7 +26,7 @@ using namespace meb300::detail;
 
 namespace {
 
-constexpr int kMaxChannels = 16;
+constexpr int kMaxChannels = 32;  // the counts take the first 256 bytes of the partition buffer (64 ints)
 
 // One atomic per warp and channel: the lanes of a warp that hold the same channel
 // (__match_any_sync) take consecutive list positions from one atomicAdd by their lowest
@@ -64,7 +64,7 @@ extern "C" int me_compute_channels(me_handle* const* hs, int nchan, int64_t nevt
                                    const double* rnd_col, double* me, int32_t* sel_hel, int32_t* sel_col,
                                    void* cuda_stream) {
   if (!hs || nchan < 1 || nchan > kMaxChannels)
-    return fail(nullptr, ME_ERR_ARG, "me_compute_channels: 1 to 16 handles are required");
+    return fail(nullptr, ME_ERR_ARG, "me_compute_channels: 1 to 32 handles are required");
   for (int c = 0; c < nchan; ++c)
     if (!hs[c]) return fail(nullptr, ME_ERR_ARG, "me_compute_channels: null handle");
   me_handle* h0 = hs[0];

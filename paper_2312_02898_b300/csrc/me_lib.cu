@@ -49,6 +49,10 @@ extern const ProcessOps ops_uxuttddx __attribute__((weak));
 extern const ProcessOps ops_udttud __attribute__((weak));
 extern const ProcessOps ops_udxttudx __attribute__((weak));
 extern const ProcessOps ops_uxdxttuxdx __attribute__((weak));
+extern const ProcessOps ops_uuttuu __attribute__((weak));
+extern const ProcessOps ops_uxuxttuxux __attribute__((weak));
+extern const ProcessOps ops_uuxttuux __attribute__((weak));
+extern const ProcessOps ops_uxuttuux __attribute__((weak));
 }
 using namespace meb300;
 
@@ -58,7 +62,8 @@ const ProcessOps* const kProcs[] = {&ops_eemumu, &ops_ggtt,   &ops_ggttg,  &ops_
                                     &ops_qqtt,   &ops_qxqtt,  &ops_qqttg,  &ops_qxqttg,  &ops_qgttq,
                                     &ops_gqttq,  &ops_qxgttqx, &ops_gqxttqx, &ops_qqttgg, &ops_qxqttgg,
                                     &ops_qgttqg, &ops_gqttqg, &ops_qxgttqxg, &ops_gqxttqxg, &ops_ggttqqx,
-                                    &ops_uuxttddx, &ops_uxuttddx, &ops_udttud, &ops_udxttudx, &ops_uxdxttuxdx};
+                                    &ops_uuxttddx, &ops_uxuttddx, &ops_udttud, &ops_udxttudx, &ops_uxdxttuxdx,
+                                    &ops_uuttuu, &ops_uxuxttuxux, &ops_uuxttuux, &ops_uxuttuux};
 
 thread_local std::string g_init_error;
 

@@ -62,9 +62,15 @@ PROCESSES.update({
     "u d > t t~ u d": dict(tag="udttud", roles=("q_in", "d_in", "t", "tb", "q_out", "d_out")),
     "u d~ > t t~ u d~": dict(tag="udxttudx", roles=("q_in", "db_in", "t", "tb", "q_out", "db_out")),
     "u~ d~ > t t~ u~ d~": dict(tag="uxdxttuxdx", roles=("qb_in", "db_in", "t", "tb", "qb_out", "db_out")),
+    # one light flavour: both pairings of the light quarks
+    "u u > t t~ u u": dict(tag="uuttuu", roles=("q_in", "q_in", "t", "tb", "q_out", "q_out")),
+    "u~ u~ > t t~ u~ u~": dict(tag="uxuxttuxux", roles=("qb_in", "qb_in", "t", "tb", "qb_out", "qb_out")),
+    "u u~ > t t~ u u~": dict(tag="uuxttuux", roles=("q_in", "qb_in", "t", "tb", "q_out", "qb_out")),
+    "u~ u > t t~ u u~": dict(tag="uxuttuux", roles=("qb_in", "q_in", "t", "tb", "q_out", "qb_out")),
 })
 QUARK_JET2_TAGS = ("qqttgg", "qxqttgg", "qgttqg", "gqttqg", "qxgttqxg", "gqxttqxg", "ggttqqx",
-                   "uuxttddx", "uxuttddx", "udttud", "udxttudx", "uxdxttuxdx")
+                   "uuxttddx", "uxuttddx", "udttud", "udxttudx", "uxdxttuxdx", "uuttuu", "uxuxttuxux", "uuxttuux",
+                   "uxuttuux")
 
 # jamps variants per process: (register budget, diagram-group size).  The budget is the
 # number of currents kept in registers (None: all); a group size splits the emission

@@ -352,7 +352,7 @@ def header(em):
     """the generated proc_<tag>.cuh text and its stats (one light-quark line and two
     gluons, or two light-quark lines of different flavours)"""
     from .emit import _lit
-    three = any(r.startswith("d") for r in em.roles)
+    three = sum(1 for r in em.roles if r.split("_")[0] in ("q", "qb", "d", "db")) == 4
     body, st = emit3(em) if three else emit(em)
     ncol, ndiag, namp = st["ncol"], st["ndiag"], st["namp"]
     roles, npar, tag = em.roles, em.npar, em.tag
@@ -362,8 +362,10 @@ def header(em):
     for r in roles:
         if r.endswith("_in"):
             ncolour *= 8 if r == "g_in" else 3
-    nfg = sum(1 for r in roles if r == "g_out")
-    iden = 4 * ncolour * math.factorial(nfg)
+    iden = 4 * ncolour
+    for r in set(roles):
+        if r.endswith("_out"):
+            iden *= math.factorial(sum(1 for x in roles if x == r))
     # colour matrix: flows carried times scale, so |M|^2 = J'^+ G J' / scale^2
     scale = st["scale"]
     G = st["gram"]
@@ -485,11 +487,12 @@ def header(em):
 MIDDLE = ((0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0))
 
 
-def three_line_colour():
+def three_line_colour(swap=False):
     """(flow coefficients of the 7 terms scaled to Gaussian integers, the scale, the Gram
-    matrix of the 6 flows).  Indices (B0, K0, B1, K1, t, y): row and column ends of the u
-    line, the d line and the top line; flows d_{B0 K_s0} d_{B1 K_s1} d_{t K_s2} for the
-    permutations s of (K0, K1, y) in lexicographic order."""
+    matrix of the 6 flows).  Indices (B0, K0, B1, K1, t, y): row and column ends of the
+    two light lines and the top line; flows d_{B0 K_s0} d_{B1 K_s1} d_{t K_s2} for the
+    permutations s of (K0, K1, y) in lexicographic order.  With swap the light lines are
+    (B0, K1) and (B1, K0): the second pairing of one light flavour."""
     T = gell_mann_T()
     f = _structure_constants(T)
     d = np.eye(3)
@@ -510,6 +513,8 @@ def three_line_colour():
         tens.append(np.einsum(f"{spec[X]},{spec[Y]},{spec[Z]}->BKCLty", T, T, T, T))
     coef = []
     for x in tens:
+        if swap:
+            x = np.swapaxes(x, 1, 3)  # K0 <-> K1
         c = np.linalg.lstsq(Fm, x.ravel(), rcond=None)[0]
         if np.abs(Fm @ c - x.ravel()).max() > 1e-10:
             raise RuntimeError("colour of a three-line term is not in the span of the flows")
@@ -527,17 +532,29 @@ def three_line_colour():
 
 
 def emit3(em):
-    """(jamps body, stats) for two light-quark lines of different flavours and the top line"""
+    """(jamps body, stats) for two light-quark lines and the top line.  With two flavours
+    the lines are the u line and the d line; with one flavour the row ends (B0 < B1) and
+    column ends (K0 < K1) of the light quarks pair up both ways, (B0 K0)(B1 K1) and
+    (B0 K1)(B1 K0), the second pairing with the sign -1 of exchanging identical
+    fermions."""
     roles, npar = em.roles, em.npar
     line_of = {"q": 0, "qb": 0, "d": 1, "db": 1, "t": 2, "tb": 2}
     row_roles = ("qb_in", "q_out", "db_in", "d_out", "t")
+    same = not any(r.startswith("d") for r in roles)
     B, K = [None] * 3, [None] * 3
+    rows, cols = [], []
     for i, r in enumerate(roles):
         ln = line_of[r.split("_")[0]]
+        if same and ln < 2:
+            (rows if r in row_roles else cols).append(i)
+            continue
         if r in row_roles:
             B[ln] = i
         else:
             K[ln] = i
+    if same:
+        B[0], B[1] = rows
+        K[0], K[1] = cols
 
     def parts(S, sign=1):
         out = []
@@ -580,31 +597,42 @@ def emit3(em):
               "d_out": "ext_ubar", "t": "ext_ubar", "qb_out": "ext_v", "db_out": "ext_v", "tb": "ext_v"}[r]
         body.append(f"  {fn}<R>({ktp}, {m}, lam[{i}], x{i});")
         flop("ext")
-    lines = [frozenset([B[l], K[l]]) for l in range(3)]
-    for l in range(3):
-        body.append(f"  cx<R> J{l}[4]; pair_current<R>(x{B[l]}, x{K[l]}, J{l});")
-        flop("pj")
-    coef, scale, gram = three_line_colour()
+    body.append(f"  cx<R> J2[4]; pair_current<R>(x{B[2]}, x{K[2]}, J2);")
+    flop("pj")
     amps = []
-    # term 0: the three-gluon vertex; phases -i per line current (3), -i per gluon
-    # propagator (3), -1 for the vertex -g f V: +1 overall
-    amps.append((f"{dg(lines[1])} * {dg(lines[2])} * close_v3<R>(J2, J0, {kv(lines[0])}, J1, {kv(lines[1])}, "
-                 f"{dg(lines[0])})", 1))
-    flop("v3")
-    flop("scale", 2)
-    for n, (X, Y, Z) in enumerate(MIDDLE):
-        # line X: the current of Y enters nearer its row end, one fermion propagator, the
-        # current of Z; phases -i (Y), -i (Z), +1 (step), -i (last vertex), -i -i (gluon
-        # propagators): -i overall
-        SX = frozenset([B[X]]) | lines[Y]
-        m = "mt" if X == 2 else "R(0)"
-        body.append(f"  cx<R> c{n}[4]; bra_step<R>(x{B[X]}, J{Y}, {kv(SX, -1)}, {m}, {dt(SX, X == 2)}, c{n});")
-        body.append(f"  cx<R> v{n}[4]; pair_current<R>(c{n}, x{K[X]}, v{n});")
-        flop("step")
-        flop("pj")
-        amps.append((f"{dg(lines[Y])} * {dg(lines[Z])} * mdot(v{n}, J{Z})", -1j))
-        flop("dot")
+    coefs = []
+    for pr in ((0, 1) if same else (0,)):
+        Kp = [K[1], K[0], K[2]] if pr else list(K)
+        sfx = "x" if pr else ""
+        sign = -1 if pr else 1
+        lines = [frozenset([B[l], Kp[l]]) for l in range(3)]
+        J = [f"J0{sfx}", f"J1{sfx}", "J2"]
+        for l in range(2):
+            body.append(f"  cx<R> {J[l]}[4]; pair_current<R>(x{B[l]}, x{Kp[l]}, {J[l]});")
+            flop("pj")
+        coef, scale, gram = three_line_colour(swap=bool(pr))
+        coefs += list(coef)
+        # term 0: the three-gluon vertex; phases -i per line current (3), -i per gluon
+        # propagator (3), -1 for the vertex -g f V: +1 overall
+        amps.append((f"{dg(lines[1])} * {dg(lines[2])} * close_v3<R>({J[2]}, {J[0]}, {kv(lines[0])}, {J[1]}, "
+                     f"{kv(lines[1])}, {dg(lines[0])})", sign))
+        flop("v3")
         flop("scale", 2)
+        for n, (X, Y, Z) in enumerate(MIDDLE):
+            # line X: the current of Y enters nearer its row end, one fermion propagator, the
+            # current of Z; phases -i (Y), -i (Z), +1 (step), -i (last vertex), -i -i (gluon
+            # propagators): -i overall
+            SX = frozenset([B[X]]) | lines[Y]
+            m = "mt" if X == 2 else "R(0)"
+            body.append(f"  cx<R> c{n}{sfx}[4]; bra_step<R>(x{B[X]}, {J[Y]}, {kv(SX, -1)}, {m}, {dt(SX, X == 2)}, "
+                        f"c{n}{sfx});")
+            body.append(f"  cx<R> v{n}{sfx}[4]; pair_current<R>(c{n}{sfx}, x{Kp[X]}, v{n}{sfx});")
+            flop("step")
+            flop("pj")
+            amps.append((f"{dg(lines[Y])} * {dg(lines[Z])} * mdot(v{n}{sfx}, {J[Z]})", -1j * sign))
+            flop("dot")
+            flop("scale", 2)
+    coef = coefs
     npairs = 0
     for d, (expr, ph) in enumerate(amps):
         ops, mags = [], set()
@@ -625,5 +653,6 @@ def emit3(em):
         pre = "".join(f" const cx<R> a{m} = R({m}) * a;" for m in sorted(mags))
         flop("scale", len(mags))
         body.append(f"  {{ const cx<R> a = {expr};{pre} {' '.join(ops)} }}")
+    nd = 14 if same else 7
     return body, dict(kvec=kvec, dgs=dgs, dts=dts, flops=fl["n"], pairs=npairs, scale=scale, gram=gram,
-                      parts=parts, ncol=6, ndiag=7, namp=7)
+                      parts=parts, ncol=6, ndiag=nd, namp=nd)

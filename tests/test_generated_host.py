@@ -18,7 +18,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(os.path.dirname(HERE), "paper_2312_02898_b300", "csrc")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 CASES = [("u u~ > t t~ g g", "qqttgg"), ("g u > t t~ u g", "gqttqg"), ("g g > t t~ u u~", "ggttqqx"),
-         ("u d~ > t t~ u d~", "udxttudx")]
+         ("u d~ > t t~ u d~", "udxttudx"), ("u~ u > t t~ u u~", "uxuttuux")]
 
 
 @pytest.mark.skipif(not (os.path.exists(NVCC) or shutil.which("nvcc")), reason="nvcc not available")

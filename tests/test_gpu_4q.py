@@ -1,7 +1,9 @@
-"""GPU parity of the four-quark channels of p p -> t tbar + 2 jets with two light flavours
-(u u~ > t t~ d d~ in both beam orders, u d > t t~ u d, u d~ > t t~ u d~,
-u~ d~ > t t~ u~ d~) against the FP64 oracle: FP64 within 1e-12 on every event, FP32 within
-1e-5; selections equal except at running-sum boundaries."""
+"""GPU parity of the four-quark channels of p p -> t tbar + 2 jets against the FP64 oracle:
+two light flavours (u u~ > t t~ d d~ in both beam orders, u d > t t~ u d, u d~ > t t~ u d~,
+u~ d~ > t t~ u~ d~) and one light flavour (u u > t t~ u u, u~ u~ > t t~ u~ u~,
+u u~ > t t~ u u~ in both beam orders, both pairings of the light quarks).  FP64 within
+1e-12 on every event, FP32 within 1e-5; selections equal except at running-sum
+boundaries."""
 import numpy as np
 import pytest
 
@@ -13,9 +15,10 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 FOURQ = ("u u~ > t t~ d d~", "u~ u > t t~ d d~", "u d > t t~ u d", "u d~ > t t~ u d~", "u~ d~ > t t~ u~ d~")
+SAME = ("u u > t t~ u u", "u~ u~ > t t~ u~ u~", "u u~ > t t~ u u~", "u~ u > t t~ u u~")
 
 
-@pytest.mark.parametrize("process", FOURQ)
+@pytest.mark.parametrize("process", FOURQ + SAME)
 @pytest.mark.parametrize("precision,bound", [("fp64", 1e-12), ("fp32", 1e-5)])
 def test_parity(process, precision, bound):
     n = 555
@@ -30,11 +33,13 @@ def test_parity(process, precision, bound):
     assert boundary_ok(sc, ref["sel_col"], ref["colw"], rc, tol)
 
 
-@pytest.mark.parametrize("process", FOURQ)
+@pytest.mark.parametrize("process", FOURQ + SAME)
 def test_info_and_helicity_filter(process):
     m = mk(process)
-    assert (m.npar, m.ncomb, m.ncol, m.ndiag) == (6, 64, 6, 7)
-    assert m.ngood == 16
+    assert (m.npar, m.ncomb, m.ncol, m.ndiag) == (6, 64, 6, 14 if process in SAME else 7)
+    # massless quark lines keep their helicity: 4 light patterns per pairing, and the two
+    # pairings of identical quarks share the 2 where all four agree (6 x 4 top helicities)
+    assert m.ngood == (24 if process in SAME else 16)
     mom, _, _, _ = ps.make_batch(process, 12, seed=97)
     ref = oracle.me(process, mom, want_hel=True)
     contributing = set(np.nonzero((ref["me_hel"] != 0).any(axis=0))[0].tolist())
@@ -49,7 +54,7 @@ def test_zero_width_tchannel():
     assert np.max(np.abs(me / ref - 1)) <= 1e-12
 
 
-@pytest.mark.parametrize("process,slot", [("u d > t t~ u d", 4), ("u d~ > t t~ u d~", 4)])
+@pytest.mark.parametrize("process,slot", [("u d > t t~ u d", 4), ("u d~ > t t~ u d~", 4), ("u u > t t~ u u", 4)])
 def test_nearly_collinear_quark(process, slot):
     """the final quark 1-10 mrad from the beam of its own flavour (a nearly on-shell
     t-channel gluon): FP64 within 1e-12, FP32 rescued to the FP64 bits"""

@@ -1,7 +1,7 @@
 """GPU parity of the two-jet channels with one light-quark line (q qbar -> t tbar g g,
 q g -> t tbar q g, qbar g -> t tbar qbar g in both beam orders, g g -> t tbar q qbar)
 against the FP64 oracle, and the per-event dispatch of a p p -> t tbar + 2 jets batch over
-these channels, g g -> t tbar g g and the four-quark channels with two light flavours.
+these channels, g g -> t tbar g g and the four-quark channels.
 
 Bars as for the other processes: FP64 within 1e-12 of the oracle on every event, FP32
 within 1e-5 (with the FP64 rescue of ill-conditioned events); selections equal except
@@ -19,7 +19,8 @@ pytestmark = pytest.mark.gpu
 JET2 = ("u u~ > t t~ g g", "u~ u > t t~ g g", "u g > t t~ u g", "g u > t t~ u g", "u~ g > t t~ u~ g",
         "g u~ > t t~ u~ g", "g g > t t~ u u~")
 FOURQ = ("u u~ > t t~ d d~", "u~ u > t t~ d d~", "u d > t t~ u d", "u d~ > t t~ u d~", "u~ d~ > t t~ u~ d~")
-PP_TT2J = ("g g > t t~ g g",) + JET2 + FOURQ
+SAME = ("u u > t t~ u u", "u~ u~ > t t~ u~ u~", "u u~ > t t~ u u~", "u~ u > t t~ u u~")
+PP_TT2J = ("g g > t t~ g g",) + JET2 + FOURQ + SAME
 
 
 def mk(process, precision="fp64", **kw):
@@ -124,13 +125,14 @@ def test_nearly_collinear_parton(process, slot):
 
 @pytest.mark.parametrize("precision,bound", [("fp64", 1e-12), ("fp32", 1e-5)])
 def test_pp_ttbar_2jet_dispatch(precision, bound):
-    """one batch of p p -> t tbar + 2 jets events over g g -> t tbar g g, the seven
-    one-light-line channels and the five four-quark channels with two light flavours:
-    every event gets its channel's single-call bits and the oracle's value"""
+    """one batch of p p -> t tbar + 2 jets events over all 17 channels (g g -> t tbar g g,
+    seven with one light-quark line, five four-quark channels with two light flavours and
+    four with one): every event gets its channel's single-call bits and the oracle's
+    value"""
     from paper_2312_02898_b300.binding import compute_channels
     n = 2053
     mom, a, rh, rc = ps.make_batch(PP_TT2J[0], n, seed=75, alphas="uniform")
-    w = np.array([0.4, 0.07, 0.07, 0.07, 0.07, 0.05, 0.05, 0.05, 0.04, 0.03, 0.04, 0.03, 0.03])
+    w = np.array([0.36, 0.06, 0.06, 0.06, 0.06, 0.05, 0.05, 0.05, 0.04, 0.03, 0.04, 0.03, 0.03, 0.02, 0.02, 0.02, 0.02])
     ch = np.random.default_rng(76).choice(len(PP_TT2J), size=n, p=w / w.sum()).astype(np.int32)
     hs = [mk(p, precision) for p in PP_TT2J]
     d = dev(mom, a, rh, rc)
