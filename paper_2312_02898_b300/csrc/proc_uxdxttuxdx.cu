@@ -9,11 +9,11 @@ namespace {
 using P = proc_uxdxttuxdx;
 template <int PREC, int C> struct Cfg;
 // The first layout of each precision is the default, the others alternatives for sweeps
-// (me_set_config): FP64 with everything in registers or with the denominators, J and
-// colour weights in shared memory; FP32 capped at 168 registers (measured 4.0e8 ME/s),
-// at 128 (3.4e8) or uncapped (3.7e8)
-template <> struct Cfg<0, 0> { using R = double; using L = Layout<0, 128, 0, 0, 0, 0, 1>; };
-template <> struct Cfg<0, 1> { using R = double; using L = Layout<0, 128, 1, 1, 1, 0, 1>; };
+// (me_set_config).  Measured on u d > t t~ u d at 262144 events: FP64 with the
+// denominators, J and colour weights in shared memory 1.89e7 ME/s, everything in
+// registers 1.86e7; FP32 capped at 168 registers 4.0e8, at 128 3.4e8, uncapped 3.7e8
+template <> struct Cfg<0, 0> { using R = double; using L = Layout<0, 128, 1, 1, 1, 0, 1>; };
+template <> struct Cfg<0, 1> { using R = double; using L = Layout<0, 128, 0, 0, 0, 0, 1>; };
 template <> struct Cfg<1, 0> { using R = float; using L = Layout<0, 128, 0, 0, 0, 0, 1, 0, 3>; };
 template <> struct Cfg<1, 1> { using R = float; using L = Layout<0, 128, 0, 0, 0, 0, 1, 0, 4>; };
 template <> struct Cfg<1, 2> { using R = float; using L = Layout<0, 128, 0, 0, 0, 0, 1>; };
