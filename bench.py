@@ -49,11 +49,11 @@ ERR_BOUND = {"fp64": 1e-12, "fp32": 1e-5, "mixed": 1e-5, "dfloat": 1e-10}
 # changed default reports no traffic; an entry is removed when its kernel's code changes
 # and comes back with a new capture.
 DRAM_BYTES_PER_EVENT = {
-    ("fp64", "Layout<3, 64, 1, 1, 1, 2, 2, 3, 1>"): 1.459e11 / 655360,
-    ("fp32", "Layout<1, 64, 1, 0, 1, 1, 2, 3, 1>"): 1.257e9 / 655360,
+    ("fp64", "Layout<9, 64, 1, 1, 1, 2, 2, 3, 1>"): (6.136e10 + 8.949e10) / 655360,
+    ("fp32", "Layout<10, 64, 1, 0, 1, 1, 2, 3, 1>"): (1.482e8 + 9.32e7) / 655360,
 }
-DEFAULT_LAYOUT = {"fp64": "Layout<3, 64, 1, 1, 1, 2, 2, 3, 1>", "fp32": "Layout<1, 64, 1, 0, 1, 1, 2, 3, 1>",
-                  "mixed": "pipelined Layout<1, 128, 1, 0, 1, 2, 2, 3, 1>"}
+DEFAULT_LAYOUT = {"fp64": "Layout<9, 64, 1, 1, 1, 2, 2, 3, 1>", "fp32": "Layout<10, 64, 1, 0, 1, 1, 2, 3, 1>",
+                  "mixed": "pipelined Layout<7, 128, 1, 0, 1, 2, 2, 3, 1>"}
 
 
 def dist_env():

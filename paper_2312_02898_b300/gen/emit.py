@@ -72,15 +72,19 @@ QUARK_JET2_TAGS = ("qqttgg", "qxqttgg", "qgttqg", "gqttqg", "qxgttqxg", "gqxttqx
                    "uuxttddx", "uxuttddx", "udttud", "udxttudx", "uxdxttuxdx", "uuttuu", "uxuxttuxux", "uuxttuux",
                    "uxuttuux")
 
-# jamps variants per process: (register budget, diagram-group size).  The budget is the
-# number of currents kept in registers (None: all); a group size splits the emission
-# sequence into out-of-line functions of that many steps (diagram groups), with every
-# value that crosses a group boundary passed through the slot buffer.
+# jamps variants per process: (register budget, diagram-group size[, pending colour
+# accumulators]).  The budget is the number of currents kept in registers (None: all); a
+# group size splits the emission sequence into out-of-line functions of that many steps
+# (diagram groups), with every value that crosses a group boundary passed through the slot
+# buffer.  With P pending accumulators, amplitudes whose colour vectors agree up to a
+# factor 1, i, -1 or -i are summed in registers before they are added into J (see
+# _pending_plan).
 VARIANTS = {
     "ggtt": ((None, None),),
     "ggttg": ((None, None), (6, None)),
-    "ggttgg": ((None, None), (20, None), (10, None), (6, None), (3, None), (10, 160)),
-    "ggttggg": ((12, 160), (6, 160)),
+    "ggttgg": ((None, None), (20, None), (10, None), (6, None), (3, None), (10, 160), (6, None, 4), (20, None, 4),
+               (6, None, 8), (6, None, 12), (20, None, 12)),
+    "ggttggg": ((12, 160), (6, 160), (12, 160, 4), (12, 160, 8), (12, 160, 16)),
 }
 
 # real-flop counts of the helas.cuh routines (complex multiply 6, complex add 2,
@@ -97,6 +101,85 @@ FLOPS = {
     "v4": 4 * 30 + 2 * 6 + 2 + 2,                           # 136
     "add": 2,
 }
+
+
+_PHASES = (1, 1j, -1, -1j)
+
+
+def colour_class(col):
+    """(base, ph) with base the colour vector col scaled by ph so that its entry of
+    lowest flow index is 1: amplitude a then adds sum_c base[c] * (a / ph) into J"""
+    items = sorted(col.items())
+    for ph in _PHASES:
+        if abs(complex(items[0][1]) * ph - 1) < 1e-9:
+            base = []
+            for c, v in items:
+                w = complex(v) * ph
+                q = next((u for u in _PHASES if abs(w - u) < 1e-9), None)
+                if q is None:
+                    raise ValueError(f"unexpected colour coefficient {v}")
+                base.append((c, q))
+            return tuple(base), ph
+    raise ValueError(f"unexpected colour coefficient {items[0][1]}")
+
+
+def _pending_plan(keys, segs, npend):
+    """Accumulation plan for the closings in emission order.  keys[j] is closing j's
+    colour class, segs[j] the out-of-line function it is emitted in.  A class with a
+    later member in the same function may take one of npend pending accumulators: its
+    members are summed there and the sum is distributed over J once, after the last
+    member or when the slot is taken by a class whose next member comes sooner (the
+    pending class with the farthest next member is the one given up).  Returns, per
+    closing, (action, slot, flushes): action 'direct' (add into J now), 'open', 'merge'
+    or 'last' (merge, then distribute); flushes lists (slot, class) distributed before
+    the closing."""
+    nxt, last = [None] * len(keys), {}
+    for j in reversed(range(len(keys))):
+        k = (keys[j], segs[j])
+        nxt[j] = last.get(k)
+        last[k] = j
+    pend, free, plan = {}, list(reversed(range(npend))), []
+    for j, key in enumerate(keys):
+        flushes = []
+        if key in pend:
+            slot = pend[key][0]
+            if nxt[j] is None:
+                del pend[key]
+                free.append(slot)
+                plan.append(("last", slot, flushes))
+            else:
+                pend[key][1] = nxt[j]
+                plan.append(("merge", slot, flushes))
+            continue
+        if nxt[j] is None or npend == 0:
+            plan.append(("direct", None, flushes))
+            continue
+        if not free:
+            far = max(pend, key=lambda q: pend[q][1])
+            if pend[far][1] > nxt[j]:
+                flushes.append((pend[far][0], far))
+                free.append(pend.pop(far)[0])
+        if free:
+            slot = free.pop()
+            pend[key] = [slot, nxt[j]]
+            plan.append(("open", slot, flushes))
+        else:
+            plan.append(("direct", None, flushes))
+    assert not pend
+    return plan
+
+
+def _add_into(target, src, coef):
+    """target += coef * src for coef in (1, i, -1, -i)"""
+    if coef == 1:
+        return f"{target} += {src};"
+    if coef == -1:
+        return f"{target} -= {src};"
+    if coef == 1j:
+        return f"acc_pi({target}, {src});"
+    if coef == -1j:
+        return f"acc_mi({target}, {src});"
+    raise ValueError(f"unexpected colour coefficient {coef}")
 
 
 def _exact(cf, bits):
@@ -302,9 +385,12 @@ class Emitter:
 
         pair_count = 0
 
-        def emit_amp(a):
+        def emit_amp(a, act=None):
             nonlocal pair_count
             nm = [name[x] for x in a.inputs]
+            if act is not None:
+                for slot, base in act[2]:
+                    body.append("  " + " ".join(_add_into(f"J[{c}]", f"pc{slot}", q) for c, q in base))
             if a.kind == "DOT":
                 body.append(f"  {{ const cx<R> a = close_dot<R>({nm[0]}, {nm[1]});")
                 flop("dot")
@@ -319,21 +405,23 @@ class Emitter:
                     body.append(f"  {{ const cx<R> a = close_v4<{a.struct}, R>({nm[0]}, {nm[1]}, {nm[2]}, "
                                 f"{nm[3]}, dg[{ig}]);")
                     flop("v4")
-            ops = []
-            for c, v in sorted(a.colour.items()):
-                v = complex(v)
-                if abs(v - 1) < 1e-12:
-                    ops.append(f"J[{c}] += a;")
-                elif abs(v + 1) < 1e-12:
-                    ops.append(f"J[{c}] -= a;")
-                elif abs(v - 1j) < 1e-12:
-                    ops.append(f"acc_pi(J[{c}], a);")
-                elif abs(v + 1j) < 1e-12:
-                    ops.append(f"acc_mi(J[{c}], a);")
-                else:
-                    raise ValueError(f"unexpected colour coefficient {v}")
+            # the algorithmic count is the accumulation as written, J_c += colour_c * a,
+            # whether or not the closing's amplitude is first summed in a pending slot
+            for _ in a.colour:
                 flop("add")
                 pair_count += 1
+            base, ph = colour_class(a.colour)
+            kind = "direct" if act is None else act[0]
+            if kind == "direct":
+                ops = [_add_into(f"J[{c}]", "a", q / ph) for c, q in base]
+            elif kind == "open":
+                # pc = a / ph
+                init = {1: "a", -1: "mk<R>(-a.r, -a.i)", 1j: "mk<R>(a.i, -a.r)", -1j: "mk<R>(-a.i, a.r)"}[ph]
+                ops = [f"pc{act[1]} = {init};"]
+            else:
+                ops = [_add_into(f"pc{act[1]}", "a", 1 / ph)]
+                if kind == "last":
+                    ops += [_add_into(f"J[{c}]", f"pc{act[1]}", q) for c, q in base]
             body.append("    " + " ".join(ops) + " }")
 
         def emit_node(node, loc):
@@ -378,8 +466,14 @@ class Emitter:
         externals = [("EXT", i) for i in range(self.npar)]
         ext_lines = list(body)
         variants = []
-        for vi, (budget, group) in enumerate(budgets):
+        for vi, vdef in enumerate(budgets):
+            budget, group = vdef[0], vdef[1]
+            npend = vdef[2] if len(vdef) > 2 else 0
             bounds = list(range(group, len(sched.seq), group)) if group else []
+            amp_steps = [k for k, (t, _) in enumerate(sched.seq) if t == "A"]
+            aplan = _pending_plan([colour_class(sched.amps[sched.seq[k][1]].colour)[0] for k in amp_steps],
+                                  [sum(1 for b in bounds if b <= k) for k in amp_steps], npend)
+            aplan = dict(zip(amp_steps, aplan))
             plan, nslot = allocate_storage(sched.seq, deps_of, externals, budget, bounds)
             body[:] = list(ext_lines)
             name.clear()
@@ -401,9 +495,9 @@ class Emitter:
                 if t == "N":
                     emit_node(x, loc)
                 else:
-                    emit_amp(sched.amps[x])
+                    emit_amp(sched.amps[x], aplan[k])
             groups.append(list(body))
-            variants.append((budget, group, nslot, groups))
+            variants.append((budget, group, nslot, groups, npend))
 
         den = ["  using DD = dd_for<R>;", "  DD q[4];"]
 
@@ -504,21 +598,22 @@ class Emitter:
         out.append(f"template <int V> static HD constexpr bool grouped() {{ return {chain_g}; }}")
         lam = (f"  int lam[{self.npar}];\n  for (int i = 0; i < {self.npar}; ++i) "
                f"lam[i] = ((h >> ({self.npar - 1} - i)) & 1) ? 1 : -1;")
-        for vi, (budget, group, nslot, groups) in enumerate(variants):
+        for vi, (budget, group, nslot, groups, npend) in enumerate(variants):
+            pdecl = [f"  cx<R> {', '.join(f'pc{i}' for i in range(npend))};  // pending colour sums"] if npend else []
             # SYNC > 0: a block barrier every SYNC * SYNC_STEP steps and between diagram
             # groups, which keeps the warps of a block on the same stretch of code (all
             # threads of the block must then call the function together)
             if not group:
                 out += ["", "template <int S, class R, int SYNC = 0, class DG, class DT, class JA>",
                         f"static HD void jamps_v{vi}(int h, R mt, const DG& dg, const DT& dt, JA& J, cx<R>* ws,"
-                        " const R* kt) {", lam]
+                        " const R* kt) {", lam] + pdecl
                 out += groups[0]
                 out.append("}")
             else:
                 for gi, gbody in enumerate(groups):
                     out += ["", "template <int S, class R, int SYNC = 0, class DG, class DT, class JA>",
                             f"static NOINL void jamps_v{vi}_g{gi}(int h, R mt, DG dg, DT dt, JA J, cx<R>* ws, const R* kt) {{",
-                            lam]
+                            lam] + pdecl
                     out += gbody
                     out.append("}")
                 out += ["", "template <int S, class R, int SYNC = 0, class DG, class DT, class JA>",
@@ -545,7 +640,7 @@ class Emitter:
         stats = dict(ndiag=ndiag, namp=len(sched.amps), nnode=len(sched.nodes), ncol=ncol, pairs=pair_count,
                      flops_amp=fl["amp"], flops_col=csflops, nden_g=ngden, nden_t=ntden, col_den=cden,
                      max_live=sc.max_live(sched, it, itb), schedule=sc.summary(sched),
-                     variants=[(b, g, ns) for b, g, ns, _ in variants])
+                     variants=[(b, g, ns, npd) for b, g, ns, _, npd in variants])
         return "\n".join(out) + "\n", stats
 
     # ------------------------------------------------------------------ e+e- -> mu+mu-

@@ -2,7 +2,8 @@
 // GPU): reads nevt events [nevt][NPAR][4] FP64 from standard input and prints, per event,
 // g_s^(2 NGLUON) sum over all helicities of colour_sum(J_h) / (COL_DEN IDEN) -- the
 // matrix element the kernels accumulate -- from the header's own precompute, jamps and
-// colour_sum in FP64.  PROC_HEADER and PROC are given on the command line.
+// colour_sum in FP64.  PROC_HEADER and PROC are given on the command line, and VARIANT
+// (default 0) picks the jamps variant (its slot buffer is a host array).
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -12,6 +13,9 @@
 
 using namespace meb300;
 using P = PROC;
+#ifndef VARIANT
+#define VARIANT 0
+#endif
 
 int main(int argc, char** argv) {
   if (argc < 5) return 2;
@@ -19,6 +23,7 @@ int main(int argc, char** argv) {
   const double wt = atof(argv[2]), as = atof(argv[4]), mt = 173.0;
   const int zwt = atoi(argv[3]);
   std::vector<double> mom(size_t(n) * P::NPAR * 4);
+  std::vector<cx<double>> ws(4 * size_t(P::NSLOT[VARIANT] > 0 ? P::NSLOT[VARIANT] : 1));
   if (fread(mom.data(), sizeof(double), mom.size(), stdin) != mom.size()) return 3;
   for (int e = 0; e < n; ++e) {
     const double(*p)[4] = reinterpret_cast<const double(*)[4]>(mom.data() + size_t(e) * P::NPAR * 4);
@@ -30,7 +35,7 @@ int main(int argc, char** argv) {
     for (int h = 0; h < P::NCOMB; ++h) {
       cx<double> J[P::NCOL];
       for (int i = 0; i < P::NCOL; ++i) J[i] = mk<double>(0, 0);
-      P::jamps<0, 4, double>(h, mt, dg, dt, J, nullptr, kt);
+      P::jamps<VARIANT, 4, double>(h, mt, dg, dt, J, ws.data(), kt);
       s += P::colour_sum<double>(J);
     }
     double gp = 1, g2 = 4.0 * M_PI * as;
