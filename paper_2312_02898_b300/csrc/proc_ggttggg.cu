@@ -18,26 +18,30 @@ template <int PREC, int C> struct Cfg;
 // Each layout sums the amplitudes whose colour vectors agree up to a phase in registers
 // (jamps variant 3: eight pending colour sums, variant 4: sixteen) before they are added
 // into J, which removes 43% (eight) or 49% (sixteen) of the adds into J in global memory.
-// Measured at 131072 events: FP64 2.23e4 ME/s with sixteen, 2.19e4 with eight, 1.97e4 with
-// none (variant 0); FP32 1.49e5, 1.46e5 and 1.26e5; mixed 1.44e5, 1.40e5 and 1.13e5.  The
-// default of each precision takes sixteen.
+// Measured at 131072 events with diagram groups of 160 steps: FP64 2.23e4 ME/s with
+// sixteen, 2.19e4 with eight, 1.97e4 with none (variant 0); FP32 1.49e5, 1.46e5 and
+// 1.26e5; mixed 1.44e5, 1.40e5 and 1.13e5.  Larger groups merge more closings and pass
+// fewer values through the slot buffer: groups of 320 steps with sixteen pending sums
+// (jamps variant 5, the alternative layout of each precision) FP64 2.28e4, FP32 1.54e5,
+// mixed 1.52e5; groups of 480 with twenty-four (variant 6, the default of each precision)
+// FP64 2.33e4, FP32 1.58e5, mixed 1.59e5.  Larger groups lengthen this unit's build.
 // Measured alternatives (not compiled, to keep the build of this large translation unit
 // short): shared-memory denominators and J (176 KB, one block per SM) were 1.6-1.7x
 // slower; block barriers between diagram groups add 13% in FP64 and nothing in FP32; a
 // register budget of 20 currents instead of 12 changed nothing; FP32 with J in shared
 // memory and small blocks (64- or 32-thread blocks, six or seven warps per SM) ran at
 // 1.15e5 and 1.38e5 ME/s against 1.40e5 with J in global tiles.
-template <> struct Cfg<0, 0> { using R = double; using L = Layout<4, 64, 2, 2, 2, 2, 2, 3>; };
-template <> struct Cfg<0, 1> { using R = double; using L = Layout<3, 64, 2, 2, 2, 2, 2, 3>; };
-template <> struct Cfg<1, 0> { using R = float; using L = Layout<4, 128, 2, 2, 2, 2, 2>; };
-template <> struct Cfg<1, 1> { using R = float; using L = Layout<3, 128, 2, 2, 2, 2, 2>; };
+template <> struct Cfg<0, 0> { using R = double; using L = Layout<6, 64, 2, 2, 2, 2, 2, 3>; };
+template <> struct Cfg<0, 1> { using R = double; using L = Layout<5, 64, 2, 2, 2, 2, 2, 3>; };
+template <> struct Cfg<1, 0> { using R = float; using L = Layout<6, 128, 2, 2, 2, 2, 2>; };
+template <> struct Cfg<1, 1> { using R = float; using L = Layout<5, 128, 2, 2, 2, 2, 2>; };
 
 // mixed precision: every per-thread array in global tiles, so that the FP16 operand
 // tiles (120 flows padded to 128) and the colour matrix fit in shared memory beside two
 // blocks per SM; two FP16 terms (the colour matrix is exact in FP16, not in BF16)
 template <int C> struct MixedCfg;
-template <> struct MixedCfg<0> { using L = Layout<4, 128, 2, 2, 2, 2, 2>; static constexpr int NTERM = 2; static constexpr bool F16 = true; };
-template <> struct MixedCfg<1> { using L = Layout<3, 128, 2, 2, 2, 2, 2>; static constexpr int NTERM = 2; static constexpr bool F16 = true; };
+template <> struct MixedCfg<0> { using L = Layout<6, 128, 2, 2, 2, 2, 2>; static constexpr int NTERM = 2; static constexpr bool F16 = true; };
+template <> struct MixedCfg<1> { using L = Layout<5, 128, 2, 2, 2, 2, 2>; static constexpr int NTERM = 2; static constexpr bool F16 = true; };
 
 LaunchNeeds needs(int prec, int config) {
   switch (prec * 8 + config) {

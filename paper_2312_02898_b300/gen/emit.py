@@ -84,7 +84,7 @@ VARIANTS = {
     "ggttg": ((None, None), (6, None)),
     "ggttgg": ((None, None), (20, None), (10, None), (6, None), (3, None), (10, 160), (6, None, 4), (20, None, 4),
                (6, None, 8), (6, None, 12), (20, None, 12)),
-    "ggttggg": ((12, 160), (6, 160), (12, 160, 4), (12, 160, 8), (12, 160, 16)),
+    "ggttggg": ((12, 160), (6, 160), (12, 160, 4), (12, 160, 8), (12, 160, 16), (12, 320, 16), (12, 480, 24)),
 }
 
 # real-flop counts of the helas.cuh routines (complex multiply 6, complex add 2,
